@@ -1,0 +1,125 @@
+"""Pins for the oracle's CG solve (paper Sec. 1: CG with WAXPY, DOT, MATVEC and
+no preconditioner) and the whole path against the series solution the paper's
+verification module uses.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+import fe_inputs
+import oracle
+from oracle import analytic
+
+
+def csr(sysm):
+    m = sysm["b"].size
+    return sp.csr_matrix((sysm["vals"], sysm["cols"], sysm["row_ptr"]), shape=(m, m))
+
+
+@pytest.mark.parametrize("dims", [(1, 1, 1), (2, 2, 2), (3, 4, 2), (4, 4, 4)])
+def test_cg_matches_dense_direct(dims):
+    sysm = oracle.build_system(*dims)
+    A = oracle.dense(sysm["row_ptr"], sysm["cols"], sysm["vals"])
+    x_direct = np.linalg.solve(A, sysm["b"])
+    x, it, rel, st = oracle.cg(sysm["row_ptr"], sysm["cols"], sysm["vals"], sysm["b"],
+                               tol=1e-13, maxit=500)
+    assert st == oracle.CG_CONVERGED
+    assert rel <= 1e-13
+    assert np.linalg.norm(x - x_direct) <= 1e-11 * np.linalg.norm(x_direct)
+
+
+@pytest.mark.parametrize("n", [4, 8, 16])
+def test_cg_iterations_match_scipy(n):
+    sysm = oracle.build_system(n, n, n)
+    x, it, rel, st = oracle.cg(sysm["row_ptr"], sysm["cols"], sysm["vals"], sysm["b"],
+                               tol=1e-10, maxit=1000)
+    count = [0]
+
+    def cb(_):
+        count[0] += 1
+
+    xs, info = spla.cg(csr(sysm), sysm["b"], rtol=1e-10, atol=0.0, maxiter=1000, callback=cb)
+    assert info == 0 and st == oracle.CG_CONVERGED
+    assert abs(it - count[0]) <= 1
+    assert np.linalg.norm(x - xs) <= 1e-8 * np.linalg.norm(xs)
+
+
+def test_cg_n30_converges_and_true_residual():
+    sysm = oracle.build_system(30, 30, 30)
+    x, it, rel, st = oracle.cg(sysm["row_ptr"], sysm["cols"], sysm["vals"], sysm["b"],
+                               tol=1e-10, maxit=200)
+    assert st == oracle.CG_CONVERGED and rel <= 1e-10
+    assert 55 <= it <= 75                          # ~2.1 N iterations for this problem
+    tr = oracle.true_relres(sysm["row_ptr"], sysm["cols"], sysm["vals"], sysm["b"], x)
+    assert tr <= 1.5e-10
+    ref = spla.spsolve(csr(sysm).tocsc(), sysm["b"])
+    assert np.linalg.norm(x - ref) <= 1e-8 * np.linalg.norm(ref)
+
+
+def test_cg_degenerate_cases():
+    sysm = oracle.build_system(4, 4, 4)
+    rp, c, v = sysm["row_ptr"], sysm["cols"], sysm["vals"]
+    # b = 0: solution 0 at once, whatever the start
+    x, it, rel, st = oracle.cg(rp, c, v, np.zeros_like(sysm["b"]), x0=np.ones_like(sysm["b"]))
+    assert st == oracle.CG_CONVERGED and it == 0 and np.all(x == 0)
+    # maxit reached
+    x, it, rel, st = oracle.cg(rp, c, v, sysm["b"], maxit=2)
+    assert st == oracle.CG_MAXIT and it == 2 and rel > 1e-10
+    # a start that already meets the tolerance takes no step
+    A = oracle.dense(rp, c, v)
+    xe = np.linalg.solve(A, sysm["b"])
+    x, it, rel, st = oracle.cg(rp, c, v, sysm["b"], x0=xe, tol=1e-10)
+    assert st == oracle.CG_CONVERGED and it == 0
+    # an indefinite matrix (negated diagonal) breaks down
+    v2 = v.copy()
+    diag = np.array([k for i in range(rp.size - 1) for k in range(rp[i], rp[i + 1]) if c[k] == i])
+    v2[diag] *= -1.0
+    x, it, rel, st = oracle.cg(rp, c, v2, sysm["b"])
+    assert st == oracle.CG_BREAKDOWN
+
+
+def test_face_data_solve_matches_dense():
+    nx, ny, nz = 4, 3, 5
+    fv = fe_inputs.face_data(11, 3, nx, ny, nz)
+    sysm = oracle.build_system(nx, ny, nz, fv)
+    A = oracle.dense(sysm["row_ptr"], sysm["cols"], sysm["vals"])
+    x, it, rel, st = oracle.cg(sysm["row_ptr"], sysm["cols"], sysm["vals"], sysm["b"], tol=1e-13)
+    assert st == 0
+    assert np.allclose(x, np.linalg.solve(A, sysm["b"]), atol=1e-11)
+    # the maximum principle: the harmonic interpolant stays within the boundary data range
+    assert x.min() >= fv.min() - 1e-12 and x.max() <= fv.max() + 1e-12
+
+
+# --------------------------------------------------------------------------- series
+
+def test_series_centre_is_one_sixth():
+    # superposing the six face problems gives T = 1; by symmetry each face
+    # contributes equally at the centre
+    assert abs(analytic.series(0.5, 0.5, 0.5) - 1.0 / 6.0) < 1e-14
+
+
+def test_series_boundary_values():
+    y = np.linspace(0.1, 0.9, 9)
+    assert np.allclose(analytic.series(0.0, y, 0.37), 0.0, atol=1e-15)
+    assert np.allclose(analytic.series(0.6, 0.0, y), 0.0, atol=1e-15)
+    # on x = 1 the series converges slowly (a discontinuous face); away from edges it is 1
+    assert np.allclose(analytic.series(1.0, 0.5, 0.5, max_mode=2001), 1.0, atol=2e-3)
+
+
+@pytest.mark.parametrize("n_pair", [(8, 16)])
+def test_fe_solution_converges_to_series(n_pair):
+    errs_c, errs_w = [], []
+    for n in n_pair:
+        sysm, x, it, rel, st = oracle.solve(n, n, n, tol=1e-12)
+        assert st == 0
+        xyz = sysm["coords"]
+        centre = n // 2 + (n + 1) * (n // 2 + (n + 1) * (n // 2))
+        errs_c.append(abs(x[centre] - 1.0 / 6.0))
+        win = np.all((xyz >= 0.25) & (xyz <= 0.75), axis=1)
+        t = analytic.series(xyz[win, 0], xyz[win, 1], xyz[win, 2])
+        errs_w.append(np.abs(x[win] - t).max())
+    # second-order convergence: halving h divides the error by about 4
+    assert 3.0 < errs_c[0] / errs_c[1] < 5.0
+    assert 3.0 < errs_w[0] / errs_w[1] < 5.0
+    assert errs_c[1] < 2.5e-3
