@@ -1,0 +1,230 @@
+/*
+ * fe.h -- C ABI of libfe, a GB300 (sm_103a) implementation of the MiniFE
+ * steady heat-conduction path studied in "The Research and Optimization of
+ * Parallel Finite Element Algorithm based on MiniFE" (arXiv 1505.08023).
+ *
+ * The problem (paper Sec. 1): the unit cube 0 <= x,y,z <= 1 split into
+ * nx x ny x nz trilinear hexahedra, T = 1 on the plane x = 1 and T = 0 on the
+ * other faces; the FE system A T = b is solved by unpreconditioned CG.
+ *
+ * Conventions shared by every call
+ *   - Nodes: n_x = nx+1 per x-line, node id i = ix + n_x*(iy + n_y*iz).
+ *     Rows of A are nodes; m = n_x n_y n_z.
+ *   - Elements: id e = ex + nx*(ey + ny*ez); local node order
+ *     (0,0,0),(1,0,0),(1,1,0),(0,1,0),(0,0,1),(1,0,1),(1,1,1),(0,1,1).
+ *   - Every pointer argument named d_* is DEVICE memory owned by the caller
+ *     (the library allocates nothing, frees nothing and keeps no pointer
+ *     after a call returns); h_* are host pointers.  Arrays are dense, C
+ *     order, with the lengths stated at each call.
+ *   - Work is enqueued on `stream` (a cudaStream_t; NULL = legacy default
+ *     stream) and runs asynchronously unless the call says it synchronises.
+ *   - Every call returns an fe_status.  Nothing prints, aborts or traps.
+ *     Arguments are checked before anything is enqueued; a CUDA launch or
+ *     copy failure returns FE_ERR_CUDA (fe_last_cuda_error() gives the code).
+ */
+#ifndef FE_H
+#define FE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *fe_stream_t; /* same type as cudaStream_t */
+
+typedef enum fe_status {
+    FE_OK = 0,
+    FE_ERR_ARG = -1,        /* bad size, NULL pointer, unknown enum, misaligned buffer */
+    FE_ERR_OVERFLOW = -2,   /* nnz or an index does not fit int32 (N >= 430 on a cube) */
+    FE_ERR_CUDA = -3,       /* a CUDA runtime call failed */
+    FE_ERR_BREAKDOWN = -4,  /* CG: p.Ap <= 0 or not finite (matrix not SPD, NaN input) */
+    FE_ERR_MAXIT = -5,      /* CG: tolerance not met in maxit steps; x holds the iterate */
+    FE_ERR_TIMEOUT = -6,    /* CG: a grid barrier waited past its time limit */
+    FE_ERR_WORKSPACE = -7   /* workspace smaller than the size query returned */
+} fe_status;
+
+/* Storage formats of the assembled matrix. */
+typedef enum fe_format {
+    FE_FMT_CSR = 0,   /* compressed rows (paper Sec. 3.1, "CRS"): row_ptr, cols, vals */
+    FE_FMT_SELL = 1,  /* sliced ELL, 32-row slices, column-major inside a slice */
+    FE_FMT_BCRS3 = 2  /* 1x3 blocked rows (the paper's BCRS, Sec. 3.1, with every
+                         segment padded to length 3), 32-row slices */
+} fe_format;
+
+/* Storage type of matrix values. */
+typedef enum fe_value_type { FE_VAL_F64 = 0, FE_VAL_F32 = 1, FE_VAL_BF16 = 2 } fe_value_type;
+
+#define FE_SLICE_ROWS 32
+
+/*
+ * A matrix on the device, described by plain pointers (all caller-owned).
+ *   FE_FMT_CSR   row_ptr[n_rows+1] (int32, row_ptr[n_rows] = nnz), cols[nnz],
+ *                vals[nnz]; slice_ptr unused.  n_stored = nnz.
+ *   FE_FMT_SELL  slice s holds rows 32s..32s+31 in slots slice_ptr[s] ..
+ *                slice_ptr[s+1]-1 (int64, multiples of 32); slot
+ *                slice_ptr[s] + 32k + r is entry k of row 32s+r.  cols[] and
+ *                vals[] are indexed by slot; padding slots have val 0 and a
+ *                valid column.  n_stored = slice_ptr[n_slices].
+ *   FE_FMT_BCRS3 like SELL but a slot is a 1x3 segment: cols[slot] is the
+ *                first column c of the segment (0 <= c <= n_cols-3) and the
+ *                three values multiply x[c], x[c+1], x[c+2].  Values of slot
+ *                group g = slice_ptr[s]/32 + k sit at vals[96g + 32t + r],
+ *                t = 0, 1, 2 (component), r = row in slice.
+ * vals has the element type value_type.  n_slices = ceil(n_rows / 32).
+ */
+typedef struct fe_matrix {
+    int32_t format;           /* fe_format */
+    int32_t value_type;       /* fe_value_type */
+    int64_t n_rows;
+    int64_t n_cols;
+    int64_t n_slices;
+    int64_t n_stored;         /* nnz (CSR) or slots (SELL, BCRS3) */
+    const int32_t *d_row_ptr; /* CSR only */
+    const int64_t *d_slice_ptr; /* SELL, BCRS3 */
+    const int32_t *d_cols;
+    const void *d_vals;
+} fe_matrix;
+
+/* Sizes of the problem nx x ny x nz (all >= 1). */
+typedef struct fe_sizes {
+    int64_t n_rows;     /* m = (nx+1)(ny+1)(nz+1) */
+    int64_t n_elems;    /* nx ny nz */
+    int64_t nnz;        /* (3nx+1)(3ny+1)(3nz+1): full 27-point pattern */
+    int64_t n_faces;    /* length of a face-value array (x0,x1,y0,y1,z0,z1) */
+    int64_t n_slices;   /* ceil(m / 32) */
+} fe_sizes;
+
+/* Sizes for a mesh; FE_ERR_ARG if a dimension is < 1, FE_ERR_OVERFLOW if
+ * nnz > INT32_MAX (the int32 row pointer of the CSR form cannot hold it). */
+fe_status fe_problem_sizes(int nx, int ny, int nz, fe_sizes *h_out);
+
+/*
+ * Mesh processing (paper Sec. 1, mesh module): node coordinates
+ * (ix/nx, iy/ny, iz/nz), boundary flag (1 on any face) and prescribed
+ * boundary value per node.
+ *   d_face_vals  NULL: the paper's data -- 1 on the closed plane x = 1
+ *                (edges and corners included), 0 elsewhere.  Otherwise
+ *                n_faces values, faces x0, x1, y0, y1, z0, z1 in that order;
+ *                an x face is indexed iy + (ny+1) iz, a y face ix + (nx+1) iz,
+ *                a z face ix + (nx+1) iy; a later face overwrites an earlier
+ *                one on a shared edge.
+ *   d_coords     [m][3] double;  d_bc_flag [m] uint8;  d_bc_val [m] double.
+ *   d_conn       optional [n_elems][8] int32 element node ids, or NULL.
+ */
+fe_status fe_generate_mesh(int nx, int ny, int nz, const double *d_face_vals,
+                           double *d_coords, uint8_t *d_bc_flag, double *d_bc_val,
+                           int32_t *d_conn, fe_stream_t stream);
+
+/* Workspace of fe_assemble_csr: 36 doubles per element (upper triangles of
+ * the element matrices). */
+fe_status fe_assemble_workspace(int nx, int ny, int nz, size_t *h_bytes);
+
+/*
+ * Matrix generation and FE assembly (paper Sec. 1; Fig 3.6, Fig 3.7) plus the
+ * Dirichlet rows:
+ *   - pattern: row i lists its 3x3x3 neighbours that exist (per-axis bounds),
+ *     ascending; d_row_ptr[m+1], d_cols[nnz];
+ *   - element matrices by 2x2x2 Gauss quadrature from the node coordinates,
+ *     summed per row over the incident elements in element-id order
+ *     (deterministic; no atomics); zero source, so the load vector is zero;
+ *   - Dirichlet rows by symmetric elimination: a boundary row becomes the
+ *     identity row with b_i = g_i; elsewhere b_i -= a_ij g_j and a_ij = 0 for
+ *     every boundary column j.  The pattern keeps all (3nx+1)(3ny+1)(3nz+1)
+ *     entries, zeros included.
+ *   d_vals[nnz], d_b[m] double.  d_work: fe_assemble_workspace() bytes,
+ *   8-byte aligned; its contents are scratch.
+ */
+fe_status fe_assemble_csr(int nx, int ny, int nz, const double *d_coords,
+                          const uint8_t *d_bc_flag, const double *d_bc_val,
+                          int32_t *d_row_ptr, int32_t *d_cols, double *d_vals, double *d_b,
+                          void *d_work, size_t work_bytes, fe_stream_t stream);
+
+/*
+ * Format conversion at the start of CG (paper Sec. 3.1: CRS is kept for
+ * generation and assembly and converted just before the solve).
+ *
+ * fe_sliced_plan: slot offsets of the 32-row slices for a SELL or BCRS3 copy
+ * of the CSR matrix; writes d_slice_ptr[n_slices+1] and *h_n_stored (the
+ * call synchronises `stream` to return it).  BCRS3 segments are formed
+ * greedily along each row: a segment starts at the first column not yet
+ * covered and covers that column and the next two.
+ */
+fe_status fe_sliced_plan(int32_t format, int64_t n_rows, int64_t n_cols,
+                         const int32_t *d_row_ptr, const int32_t *d_cols,
+                         int64_t *d_slice_ptr, int64_t *h_n_stored, fe_stream_t stream);
+
+/* Fill a SELL or BCRS3 matrix (format, value_type, sizes and d_slice_ptr set
+ * in *dst; d_cols / d_vals point to caller buffers of n_stored entries, with
+ * 3 n_stored values for BCRS3) from an FP64 CSR matrix.  Values are rounded
+ * to value_type (round to nearest even). */
+fe_status fe_convert(const fe_matrix *src_csr, const fe_matrix *dst, fe_stream_t stream);
+
+/* Round an FP64 array to value_type (FE_VAL_F32 or FE_VAL_BF16), nearest even:
+ * a CSR copy of the matrix with lower-precision values. */
+fe_status fe_round_values(int64_t n, const double *d_src, int32_t value_type, void *d_dst,
+                          fe_stream_t stream);
+
+/* SpMV y = A x (paper Fig 3.1 / Fig 3.2) in any format and value type,
+ * FP64 vectors and FP64 accumulation.  d_x[n_cols], d_y[n_rows]. */
+fe_status fe_spmv(const fe_matrix *A, const double *d_x, double *d_y, fe_stream_t stream);
+
+/* The same with FP32 vectors and FP32 accumulation (inner solve of the
+ * mixed-precision form). */
+fe_status fe_spmv_f32(const fe_matrix *A, const float *d_x, float *d_y, fe_stream_t stream);
+
+/* Result of a CG solve. */
+typedef struct fe_cg_result {
+    int32_t status;      /* fe_status of the solve */
+    int32_t iterations;  /* CG steps taken */
+    double relres;       /* ||r_k|| / ||b|| of the recursive residual */
+    double bnorm;        /* ||b|| */
+} fe_cg_result;
+
+/* Workspace of fe_cg_solve for matrix A: three vectors (r, p, w) of
+ * 32 * n_slices doubles plus the reduction and barrier block (about 64 KiB). */
+fe_status fe_cg_workspace(const fe_matrix *A, size_t *h_bytes);
+
+/*
+ * Unpreconditioned CG on A x = b (paper Sec. 1: MATVEC, DOT, WAXPY), textbook
+ * form, the whole loop in one persistent cooperative kernel: each step makes
+ * one pass over the matrix (w = A p with p.w fused into the SpMV epilogue),
+ * then x += alpha p, r -= alpha w with r.r fused, then p = r + beta p; dot
+ * products are reduced in a fixed order, so a rerun gives identical bits.
+ *   Stop when ||r_k|| <= tol ||b|| (checked before the first step and after
+ *   each update) or after maxit steps; b = 0 returns x = 0.
+ *   d_x[m]: start vector in, iterate out.  d_work: fe_cg_workspace() bytes,
+ *   256-byte aligned, scratch.  timeout_s: limit on any one grid-barrier
+ *   wait (<= 0: 2 s); past it every block exits and the status is
+ *   FE_ERR_TIMEOUT.
+ *   Synchronises `stream` and fills *h_result (required); returns its status.
+ */
+fe_status fe_cg_solve(const fe_matrix *A, const double *d_b, double *d_x, double tol, int maxit,
+                      double timeout_s, void *d_work, size_t work_bytes,
+                      fe_cg_result *h_result, fe_stream_t stream);
+
+/* Fault injection for tests of the barrier time limit: the next fe_cg_solve
+ * on the calling thread has block 0 skip its arrival at grid barrier number
+ * barrier_index (0 = the barrier after the initial residual), so every
+ * block's bounded wait runs out and the solve returns FE_ERR_TIMEOUT with
+ * the GPU context intact.  -1 clears it.  Nothing faults, traps or hangs. */
+fe_status fe_inject_barrier_stall(int barrier_index);
+
+/* True relative residual ||b - A x|| / ||b|| (||b - A x|| if b = 0), FP64,
+ * with A's stored values.  d_work: at least FE_RESID_WORK_BYTES, 8-byte
+ * aligned (per-block partial sums).  Synchronises `stream`. */
+#define FE_RESID_WORK_BYTES (65536 + 64)
+fe_status fe_true_relres(const fe_matrix *A, const double *d_b, const double *d_x,
+                         void *d_work, size_t work_bytes, double *h_relres, fe_stream_t stream);
+
+/* CUDA error code of the last FE_ERR_CUDA on this thread (0 if none). */
+int fe_last_cuda_error(void);
+
+/* Version string of the library. */
+const char *fe_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FE_H */

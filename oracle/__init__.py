@@ -252,3 +252,28 @@ def dense(row_ptr, cols, vals) -> np.ndarray:
         for k in range(row_ptr[i], row_ptr[i + 1]):
             A[i, cols[k]] += vals[k]
     return A
+
+
+# ----------------------------------------------------------------------------
+# value rounding of the mixed-precision form (IEEE round to nearest, ties to
+# even, directly from FP64); used to build the matrices the oracle multiplies
+# when a GPU kernel stores its values in FP32 or BF16.
+# ----------------------------------------------------------------------------
+
+def round_to_f32(v: np.ndarray) -> np.ndarray:
+    """FP64 values rounded to FP32 (nearest even), returned as FP64."""
+    return np.asarray(v, dtype=np.float64).astype(np.float32).astype(np.float64)
+
+
+def round_to_bf16(v: np.ndarray) -> np.ndarray:
+    """FP64 values rounded to bfloat16 (8-bit significand, nearest even), as FP64.
+
+    Drops the low 45 of the 52 stored significand bits with round-half-even on
+    the bit pattern; valid for finite values inside the bfloat16 normal range
+    (every matrix value here is)."""
+    bits = np.asarray(v, dtype=np.float64).view(np.uint64)
+    drop = np.uint64(45)
+    half = np.uint64((1 << 44) - 1)
+    lsb = (bits >> drop) & np.uint64(1)
+    rounded = (bits + half + lsb) & ~np.uint64((1 << 45) - 1)
+    return rounded.view(np.float64)

@@ -1,0 +1,261 @@
+// fe_assemble.cu -- matrix generation (paper Fig 3.6), element operator and
+// FE assembly (paper Sec. 1, Fig 3.7) with the Dirichlet rows, on the GPU.
+//
+// Design (GB300): the paper's assembly loops over elements and scatters into
+// the CRS arrays inside an OpenMP critical section.  Here
+//   1. k_element_matrices: one thread per element computes its 8x8 matrix by
+//      2x2x2 Gauss quadrature from the node coordinates and stores the 36
+//      entries of the upper triangle (SoA, coalesced) in the workspace;
+//   2. k_assemble_rows: one thread per node gathers the rows of its (up to 8)
+//      incident elements in element-id order, so each entry is summed in a
+//      fixed order with no atomics, applies the Dirichlet elimination, and
+//      writes its CSR row.  The row pointer is the closed-form prefix sum of
+//      the per-axis neighbour counts (2 at an end of an axis, 3 inside).
+#include "fe_common.cuh"
+
+namespace fe {
+
+// Local hex8 corner order (0,0,0),(1,0,0),(1,1,0),(0,1,0),(0,0,1),(1,0,1),(1,1,1),(0,1,1).
+__host__ __device__ constexpr int corner_x(int a) { return (a & 3) == 1 || (a & 3) == 2; }
+__host__ __device__ constexpr int corner_y(int a) { return (a & 3) >= 2; }
+__host__ __device__ constexpr int corner_z(int a) { return a >= 4; }
+__host__ __device__ constexpr int corner_of(int ox, int oy, int oz) {
+    return 4 * oz + (oy ? (ox ? 2 : 3) : (ox ? 1 : 0));
+}
+// Index of (a, b), a <= b, in the packed upper triangle (36 entries).
+__host__ __device__ constexpr int tri_index(int a, int b) {
+    return a <= b ? a * 8 - a * (a - 1) / 2 + (b - a) : b * 8 - b * (b - 1) / 2 + (a - b);
+}
+
+// Reference-cell derivative of the trilinear shape function of corner a in
+// direction j at the Gauss point (q & 1, (q >> 1) & 1, q >> 2), points +-1/sqrt(3).
+__host__ __device__ constexpr double ref_grad(int q, int a, int j) {
+    constexpr double g = 0.57735026918962576451;  // 1/sqrt(3)
+    const double pt[3] = {(q & 1) ? g : -g, ((q >> 1) & 1) ? g : -g, (q >> 2) ? g : -g};
+    const double sgn[3] = {corner_x(a) ? 1.0 : -1.0, corner_y(a) ? 1.0 : -1.0,
+                           corner_z(a) ? 1.0 : -1.0};
+    double v = 0.125;
+    for (int i = 0; i < 3; ++i) v *= (i == j) ? sgn[i] : (1.0 + sgn[i] * pt[i]);
+    return v;
+}
+
+struct RefGradTable {
+    double v[8][8][3];  // [Gauss point][corner][direction]
+};
+__host__ __device__ constexpr RefGradTable make_ref_grad_table() {
+    RefGradTable t{};
+    for (int q = 0; q < 8; ++q)
+        for (int a = 0; a < 8; ++a)
+            for (int j = 0; j < 3; ++j) t.v[q][a][j] = ref_grad(q, a, j);
+    return t;
+}
+__constant__ RefGradTable kRefGrad = make_ref_grad_table();
+
+__global__ void __launch_bounds__(128)
+k_element_matrices(int nx, int ny, int nz, const double *__restrict__ coords,
+                   double *__restrict__ work) {
+    const int64_t ne = (int64_t)nx * ny * nz;
+    const int64_t nxn = nx + 1, plane = nxn * (ny + 1);
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ne;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int ex = (int)(e % nx);
+        const int64_t q0 = e / nx;
+        const int ey = (int)(q0 % ny);
+        const int ez = (int)(q0 / ny);
+        const int64_t n0 = ex + nxn * (ey + (int64_t)(ny + 1) * ez);
+        double X[8][3];
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
+            const int64_t node = n0 + corner_x(a) + nxn * corner_y(a) + plane * corner_z(a);
+#pragma unroll
+            for (int i = 0; i < 3; ++i) X[a][i] = coords[3 * node + i];
+        }
+        double K[36];
+#pragma unroll
+        for (int k = 0; k < 36; ++k) K[k] = 0.0;
+
+#pragma unroll 1
+        for (int q = 0; q < 8; ++q) {
+            // J[i][j] = d x_i / d xi_j
+            double J[3][3];
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    double s = 0.0;
+#pragma unroll
+                    for (int a = 0; a < 8; ++a) s = fma(X[a][i], kRefGrad.v[q][a][j], s);
+                    J[i][j] = s;
+                }
+            const double c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+            const double c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+            const double c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+            const double det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
+            const double rdet = 1.0 / det;
+            // Jinv[i][j] = cofactor(J)[j][i] / det
+            double Ji[3][3];
+            Ji[0][0] = c00 * rdet;
+            Ji[1][0] = c01 * rdet;
+            Ji[2][0] = c02 * rdet;
+            Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) * rdet;
+            Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) * rdet;
+            Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) * rdet;
+            Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) * rdet;
+            Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) * rdet;
+            Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) * rdet;
+            // physical gradients G[a] = J^{-T} grad_xi N_a; weight 1 at every point
+            double G[8][3];
+#pragma unroll
+            for (int a = 0; a < 8; ++a)
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    double s = 0.0;
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) s = fma(Ji[j][i], kRefGrad.v[q][a][j], s);
+                    G[a][i] = s;
+                }
+            double H[8][3];
+#pragma unroll
+            for (int a = 0; a < 8; ++a)
+#pragma unroll
+                for (int i = 0; i < 3; ++i) H[a][i] = det * G[a][i];
+#pragma unroll
+            for (int a = 0; a < 8; ++a)
+#pragma unroll
+                for (int b = a; b < 8; ++b) {
+                    double d = H[a][0] * G[b][0];
+                    d = fma(H[a][1], G[b][1], d);
+                    d = fma(H[a][2], G[b][2], d);
+                    K[tri_index(a, b)] += d;
+                }
+        }
+#pragma unroll
+        for (int k = 0; k < 36; ++k) work[k * ne + e] = K[k];
+    }
+}
+
+// Closed-form CSR row start of node (ix, iy, iz): the prefix sum, in node
+// order, of the per-row neighbour counts cx(ix) cy(iy) cz(iz).
+__device__ __forceinline__ int64_t axis_count(int i, int n) {  // n = elements on the axis
+    return (i == 0 || i == n) ? 2 : 3;
+}
+__device__ __forceinline__ int64_t axis_prefix(int i) {  // sum of counts of indices < i
+    return i == 0 ? 0 : 3 * (int64_t)i - 1;
+}
+
+__global__ void __launch_bounds__(128)
+k_assemble_rows(int nx, int ny, int nz, const double *__restrict__ work,
+                const uint8_t *__restrict__ bc_flag, const double *__restrict__ bc_val,
+                int32_t *__restrict__ row_ptr, int32_t *__restrict__ cols,
+                double *__restrict__ vals, double *__restrict__ b) {
+    const int64_t nxn = nx + 1, nyn = ny + 1;
+    const int64_t m = nxn * nyn * (nz + 1);
+    const int64_t ne = (int64_t)nx * ny * nz;
+    const int64_t Cx = 3 * (int64_t)nx + 1, Cy = 3 * (int64_t)ny + 1;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int ix = (int)(i % nxn);
+        const int64_t q = i / nxn;
+        const int iy = (int)(q % nyn);
+        const int iz = (int)(q / nyn);
+
+        double acc[27];
+#pragma unroll
+        for (int k = 0; k < 27; ++k) acc[k] = 0.0;
+        // incident elements (ix+dx, iy+dy, iz+dz), dx,dy,dz in {-1,0}, in element-id order
+#pragma unroll
+        for (int dz = -1; dz <= 0; ++dz)
+#pragma unroll
+            for (int dy = -1; dy <= 0; ++dy)
+#pragma unroll
+                for (int dx = -1; dx <= 0; ++dx) {
+                    const int ex = ix + dx, ey = iy + dy, ez = iz + dz;
+                    if (ex < 0 || ex >= nx || ey < 0 || ey >= ny || ez < 0 || ez >= nz) continue;
+                    const int64_t e = ex + (int64_t)nx * (ey + (int64_t)ny * ez);
+                    const int a = corner_of(-dx, -dy, -dz);
+#pragma unroll
+                    for (int bb = 0; bb < 8; ++bb) {
+                        const int sx = dx + corner_x(bb), sy = dy + corner_y(bb), sz = dz + corner_z(bb);
+                        const int slot = (sz + 1) * 9 + (sy + 1) * 3 + (sx + 1);
+                        acc[slot] += work[(int64_t)tri_index(a, bb) * ne + e];
+                    }
+                }
+
+        const int64_t start = Cx * Cy * axis_prefix(iz) + Cx * axis_count(iz, nz) * axis_prefix(iy) +
+                              axis_count(iy, ny) * axis_count(iz, nz) * axis_prefix(ix);
+        row_ptr[i] = (int32_t)start;
+        if (i == m - 1) row_ptr[m] = (int32_t)(start + axis_count(ix, nx) * axis_count(iy, ny) *
+                                                           axis_count(iz, nz));
+        const bool brow = bc_flag[i] != 0;
+        double bi = 0.0;
+        int64_t pos = start;
+#pragma unroll
+        for (int sz = -1; sz <= 1; ++sz)
+#pragma unroll
+            for (int sy = -1; sy <= 1; ++sy)
+#pragma unroll
+                for (int sx = -1; sx <= 1; ++sx) {
+                    const int jx = ix + sx, jy = iy + sy, jz = iz + sz;
+                    if (jx < 0 || jx > nx || jy < 0 || jy > ny || jz < 0 || jz > nz) continue;
+                    const int64_t j = i + sx + nxn * (sy + nyn * sz);
+                    double v = acc[(sz + 1) * 9 + (sy + 1) * 3 + (sx + 1)];
+                    if (brow) {
+                        v = (j == i) ? 1.0 : 0.0;
+                    } else if (bc_flag[j]) {
+                        bi = fma(-v, bc_val[j], bi);
+                        v = 0.0;
+                    }
+                    cols[pos] = (int32_t)j;
+                    vals[pos] = v;
+                    ++pos;
+                }
+        b[i] = brow ? bc_val[i] : bi;
+    }
+}
+
+static int grid_cap(int64_t n, int threads, int per_sm) {
+    int64_t blocks = (n + threads - 1) / threads;
+    int64_t cap = (int64_t)sm_count() * per_sm;
+    if (cap < 1) cap = 1024;
+    return (int)(blocks < 1 ? 1 : (blocks > cap ? cap : blocks));
+}
+
+}  // namespace fe
+
+using namespace fe;
+
+extern "C" {
+
+fe_status fe_assemble_workspace(int nx, int ny, int nz, size_t *h_bytes) {
+    fe_sizes sz;
+    fe_status st = fe_problem_sizes(nx, ny, nz, &sz);
+    if (st != FE_OK) return st;
+    if (h_bytes == nullptr) return FE_ERR_ARG;
+    *h_bytes = (size_t)sz.n_elems * 36 * sizeof(double);
+    return FE_OK;
+}
+
+fe_status fe_assemble_csr(int nx, int ny, int nz, const double *d_coords,
+                          const uint8_t *d_bc_flag, const double *d_bc_val, int32_t *d_row_ptr,
+                          int32_t *d_cols, double *d_vals, double *d_b, void *d_work,
+                          size_t work_bytes, fe_stream_t stream) {
+    fe_sizes sz;
+    fe_status st = fe_problem_sizes(nx, ny, nz, &sz);
+    if (st != FE_OK) return st;
+    if (!d_coords || !d_bc_flag || !d_bc_val || !d_row_ptr || !d_cols || !d_vals || !d_b || !d_work)
+        return FE_ERR_ARG;
+    if (!aligned(d_coords, 8) || !aligned(d_bc_val, 8) || !aligned(d_vals, 8) || !aligned(d_b, 8) ||
+        !aligned(d_work, 8) || !aligned(d_row_ptr, 4) || !aligned(d_cols, 4))
+        return FE_ERR_ARG;
+    if (work_bytes < (size_t)sz.n_elems * 36 * sizeof(double)) return FE_ERR_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    k_element_matrices<<<grid_cap(sz.n_elems, 128, 32), 128, 0, s>>>(nx, ny, nz, d_coords,
+                                                                     (double *)d_work);
+    FE_TRY_LAUNCH();
+    k_assemble_rows<<<grid_cap(sz.n_rows, 128, 32), 128, 0, s>>>(
+        nx, ny, nz, (const double *)d_work, d_bc_flag, d_bc_val, d_row_ptr, d_cols, d_vals, d_b);
+    FE_TRY_LAUNCH();
+    return FE_OK;
+}
+
+}  // extern "C"

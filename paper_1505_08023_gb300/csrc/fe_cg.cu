@@ -1,0 +1,438 @@
+// fe_cg.cu -- unpreconditioned CG (paper Sec. 1: MATVEC + DOT + WAXPY) as
+// one persistent cooperative kernel per solve, and the true-residual check.
+//
+// Each CG step is three phases separated by grid barriers:
+//   A  w = A p over the block's slices, p.w accumulated in the SpMV epilogue
+//   B  x += alpha p, r -= alpha w, r.r accumulated in the same pass
+//   C  p = r + beta p
+// A dot product is reduced warp (xor butterfly) -> block (fixed warp order)
+// -> one partial per block in global memory -> after the barrier every warp
+// of every block sums the partials in block order, so all blocks hold the
+// same bits and take the same branch, and a rerun reproduces every bit.
+// Two partial buffers alternate, so a block that races ahead into the next
+// reduction never overwrites partials another block is still reading.
+//
+// The grid barrier counts arrivals on a 64-bit counter (release add, acquire
+// poll).  Every wait is bounded: past `timeout_ns` (or a poll cap) the block
+// raises the abort flag and leaves; the others see the flag at their next
+// wait and leave too, and the host reports FE_ERR_TIMEOUT.  Nothing traps.
+#include <math.h>
+
+#include "fe_common.cuh"
+
+namespace fe {
+
+constexpr int kCgWarps = 8;
+constexpr int kCgThreads = kCgWarps * 32;
+constexpr int kCgMaxBlocks = 4096;
+constexpr unsigned kMaxPolls = 1u << 28;
+
+struct CgCtrl {
+    unsigned long long bar;  // barrier arrivals
+    int abort;               // set by a block whose wait timed out
+    int status;              // fe_status of the solve
+    int iterations;
+    int pad;
+    double rr;
+    double bb;
+};
+
+struct CgArgs {
+    fe_matrix A;
+    const double *b;
+    double *x, *r, *p, *w;
+    double *part;            // [2][2 * kCgMaxBlocks]
+    CgCtrl *ctrl;
+    double tol2;
+    int maxit;
+    long long timeout_ns;
+    long long stall_barrier;  // fault injection: block 0 skips this arrival (-1: none)
+};
+
+__device__ __forceinline__ long long global_ns() {
+    long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void red_release_add(unsigned long long *p, unsigned long long v) {
+    asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Grid barrier with a bounded wait.  Returns true (uniformly in the block) if
+// all blocks arrived and nobody aborted.
+__device__ __forceinline__ bool grid_barrier(CgCtrl *ctrl, unsigned long long &target,
+                                             long long timeout_ns, long long stall_barrier,
+                                             int *s_ok) {
+    __syncthreads();
+    const long long index = (long long)(target / gridDim.x);  // barriers passed so far
+    target += gridDim.x;
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        if (!(blockIdx.x == 0 && index == stall_barrier)) red_release_add(&ctrl->bar, 1ull);
+        const long long t0 = global_ns();
+        unsigned polls = 0;
+        while (ld_acquire(&ctrl->bar) < target) {
+            if (*(volatile int *)&ctrl->abort) { ok = 0; break; }
+            if (((++polls) & 7u) == 0 &&
+                (global_ns() - t0 > timeout_ns || polls > kMaxPolls)) {
+                atomicExch(&ctrl->abort, 1);
+                ok = 0;
+                break;
+            }
+            __nanosleep(32);
+        }
+        if (ok && *(volatile int *)&ctrl->abort) ok = 0;
+        __threadfence();
+        *s_ok = ok;
+    }
+    __syncthreads();
+    return *s_ok != 0;
+}
+
+// Sum (v0, v1) over the whole grid; see the file comment for the order.
+__device__ __forceinline__ bool grid_sum2(const CgArgs &a, double v0, double v1, double &o0,
+                                          double &o1, int &round, unsigned long long &target,
+                                          double (*red)[2], int *s_ok) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    v0 = warp_sum(v0);
+    v1 = warp_sum(v1);
+    if (lane == 0) {
+        red[warp][0] = v0;
+        red[warp][1] = v1;
+    }
+    __syncthreads();
+    double *part = a.part + (size_t)(round & 1) * 2 * kCgMaxBlocks;
+    if (threadIdx.x == 0) {
+        double t0 = 0.0, t1 = 0.0;
+#pragma unroll
+        for (int k = 0; k < kCgWarps; ++k) {
+            t0 += red[k][0];
+            t1 += red[k][1];
+        }
+        __stcg(part + 2 * blockIdx.x, t0);
+        __stcg(part + 2 * blockIdx.x + 1, t1);
+    }
+    if (!grid_barrier(a.ctrl, target, a.timeout_ns, a.stall_barrier, s_ok)) return false;
+    double t0 = 0.0, t1 = 0.0;
+    for (unsigned i = lane; i < gridDim.x; i += 32) {
+        t0 += __ldcg(part + 2 * i);
+        t1 += __ldcg(part + 2 * i + 1);
+    }
+    o0 = warp_sum(t0);
+    o1 = warp_sum(t1);
+    ++round;
+    return true;
+}
+
+template <int FMT, class VT>
+__global__ void __launch_bounds__(kCgThreads, 2) k_cg(const CgArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[kCgWarps][2];
+    __shared__ int s_ok;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double *sv = reinterpret_cast<double *>(smem_raw) + (size_t)warp * 2 * kCsrStage;
+    double *sx = sv + kCsrStage;
+    const int64_t m = a.A.n_rows, ns = a.A.n_slices;
+    const int64_t gw = (int64_t)blockIdx.x * kCgWarps + warp;
+    const int64_t tw = (int64_t)gridDim.x * kCgWarps;
+    unsigned long long target = 0;
+    int round = 0;
+    int status = FE_ERR_MAXIT;
+    int k = 0;
+    double rr = 0.0, bb = 0.0;
+    bool alive = true;
+
+    // r = b - A x, p = r; r.r and b.b
+    {
+        double s0 = 0.0, s1 = 0.0;
+        for (int64_t s = gw; s < ns; s += tw) {
+            const double ax = slice_spmv<FMT, VT, double, double, false>(a.A, s, lane, a.x, sv, sx);
+            const int64_t row = s * kSlice + lane;
+            if (row < m) {
+                const double bi = a.b[row];
+                const double ri = bi - ax;
+                a.r[row] = ri;
+                a.p[row] = ri;
+                s0 = fma(ri, ri, s0);
+                s1 = fma(bi, bi, s1);
+            }
+        }
+        alive = grid_sum2(a, s0, s1, rr, bb, round, target, red, &s_ok);
+    }
+    if (alive && bb == 0.0) {  // b = 0: the solution is 0
+        for (int64_t s = gw; s < ns; s += tw) {
+            const int64_t row = s * kSlice + lane;
+            if (row < m) a.x[row] = 0.0;
+        }
+        rr = 0.0;
+        status = FE_OK;
+    } else {
+        while (alive) {
+            if (rr <= a.tol2 * bb) { status = FE_OK; break; }
+            if (k >= a.maxit) { status = FE_ERR_MAXIT; break; }
+            // A: w = A p, p.w
+            double pw_part = 0.0;
+            for (int64_t s = gw; s < ns; s += tw) {
+                const double y = slice_spmv<FMT, VT, double, double, false>(a.A, s, lane, a.p, sv, sx);
+                const int64_t row = s * kSlice + lane;
+                if (row < m) {
+                    a.w[row] = y;
+                    pw_part = fma(a.p[row], y, pw_part);
+                }
+            }
+            double pw, unused;
+            if (!(alive = grid_sum2(a, pw_part, 0.0, pw, unused, round, target, red, &s_ok))) break;
+            if (!(pw > 0.0) || !(pw < INFINITY)) { status = FE_ERR_BREAKDOWN; break; }
+            const double alpha = rr / pw;
+            // B: x += alpha p, r -= alpha w, r.r
+            double rr_part = 0.0;
+            for (int64_t s = gw; s < ns; s += tw) {
+                const int64_t row = s * kSlice + lane;
+                if (row < m) {
+                    const double pi = a.p[row], wi = a.w[row];
+                    a.x[row] = fma(alpha, pi, a.x[row]);
+                    const double ri = fma(-alpha, wi, a.r[row]);
+                    a.r[row] = ri;
+                    rr_part = fma(ri, ri, rr_part);
+                }
+            }
+            double rr_new;
+            if (!(alive = grid_sum2(a, rr_part, 0.0, rr_new, unused, round, target, red, &s_ok))) break;
+            const double beta = rr_new / rr;
+            rr = rr_new;
+            ++k;
+            if (rr <= a.tol2 * bb) { status = FE_OK; break; }
+            if (k >= a.maxit) { status = FE_ERR_MAXIT; break; }
+            // C: p = r + beta p
+            for (int64_t s = gw; s < ns; s += tw) {
+                const int64_t row = s * kSlice + lane;
+                if (row < m) a.p[row] = fma(beta, a.p[row], a.r[row]);
+            }
+            if (!(alive = grid_barrier(a.ctrl, target, a.timeout_ns, a.stall_barrier, &s_ok))) break;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.ctrl->status = alive ? status : FE_ERR_TIMEOUT;
+        a.ctrl->iterations = k;
+        a.ctrl->rr = rr;
+        a.ctrl->bb = bb;
+    }
+}
+
+// r = b - A x over the block's slices; r.r and b.b partials per block.
+template <int FMT, class VT>
+__global__ void __launch_bounds__(kCgThreads) k_resid(const fe_matrix A, const double *__restrict__ b,
+                                                      const double *__restrict__ x,
+                                                      double *__restrict__ part) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[kCgWarps][2];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double *sv = reinterpret_cast<double *>(smem_raw) + (size_t)warp * 2 * kCsrStage;
+    double *sx = sv + kCsrStage;
+    double s0 = 0.0, s1 = 0.0;
+    const int64_t tw = (int64_t)gridDim.x * kCgWarps;
+    for (int64_t s = (int64_t)blockIdx.x * kCgWarps + warp; s < A.n_slices; s += tw) {
+        const double ax = slice_spmv<FMT, VT, double, double, true>(A, s, lane, x, sv, sx);
+        const int64_t row = s * kSlice + lane;
+        if (row < A.n_rows) {
+            const double bi = b[row], ri = bi - ax;
+            s0 = fma(ri, ri, s0);
+            s1 = fma(bi, bi, s1);
+        }
+    }
+    s0 = warp_sum(s0);
+    s1 = warp_sum(s1);
+    if (lane == 0) {
+        red[warp][0] = s0;
+        red[warp][1] = s1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t0 = 0.0, t1 = 0.0;
+        for (int k = 0; k < kCgWarps; ++k) {
+            t0 += red[k][0];
+            t1 += red[k][1];
+        }
+        part[2 * blockIdx.x] = t0;
+        part[2 * blockIdx.x + 1] = t1;
+    }
+}
+
+__global__ void k_resid_final(int nblocks, const double *__restrict__ part, double *__restrict__ out) {
+    const int lane = threadIdx.x;
+    double t0 = 0.0, t1 = 0.0;
+    for (int i = lane; i < nblocks; i += 32) {
+        t0 += part[2 * i];
+        t1 += part[2 * i + 1];
+    }
+    t0 = warp_sum(t0);
+    t1 = warp_sum(t1);
+    if (lane == 0) {
+        out[0] = t0;
+        out[1] = t1;
+    }
+}
+
+static thread_local long long g_stall_barrier = -1;
+
+static size_t align256(size_t n) { return (n + 255) & ~(size_t)255; }
+
+static size_t cg_workspace_bytes(const fe_matrix &A) {
+    const size_t vec = align256((size_t)A.n_slices * kSlice * sizeof(double));
+    return 256 + align256(2 * 2 * (size_t)kCgMaxBlocks * sizeof(double)) + 3 * vec;
+}
+
+template <int FMT, class VT>
+static fe_status launch_cg(const CgArgs &args, cudaStream_t s) {
+    auto kern = k_cg<FMT, VT>;
+    const size_t smem = spmv_smem_bytes<FMT, double>(kCgWarps);
+    if (smem > 48 * 1024)
+        FE_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    FE_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kCgThreads, smem));
+    if (per_sm < 1) return FE_ERR_CUDA;
+    int64_t blocks = (int64_t)sm_count() * per_sm;
+    const int64_t need = (args.A.n_slices + kCgWarps - 1) / kCgWarps;
+    if (blocks > need) blocks = need;
+    if (blocks > kCgMaxBlocks) blocks = kCgMaxBlocks;
+    if (blocks < 1) blocks = 1;
+    void *params[] = {(void *)&args};
+    FE_TRY_CUDA(cudaLaunchCooperativeKernel((const void *)kern, dim3((unsigned)blocks), dim3(kCgThreads),
+                                            params, smem, s));
+    return FE_OK;
+}
+
+template <int FMT, class VT>
+static fe_status launch_resid(const fe_matrix &A, const double *b, const double *x, double *part,
+                              int *nblocks, cudaStream_t s) {
+    auto kern = k_resid<FMT, VT>;
+    const size_t smem = spmv_smem_bytes<FMT, double>(kCgWarps);
+    if (smem > 48 * 1024)
+        FE_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    FE_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kCgThreads, smem));
+    if (per_sm < 1) per_sm = 1;
+    int64_t blocks = (int64_t)sm_count() * per_sm;
+    const int64_t need = (A.n_slices + kCgWarps - 1) / kCgWarps;
+    if (blocks > need) blocks = need;
+    if (blocks > kCgMaxBlocks) blocks = kCgMaxBlocks;
+    if (blocks < 1) blocks = 1;
+    kern<<<(int)blocks, kCgThreads, smem, s>>>(A, b, x, part);
+    FE_TRY_LAUNCH();
+    *nblocks = (int)blocks;
+    return FE_OK;
+}
+
+#define FE_DISPATCH_FMT_VT(A, FN, ...)                                                     \
+    switch ((A).format * 3 + (A).value_type) {                                             \
+        case FE_FMT_CSR * 3 + FE_VAL_F64: return FN<FE_FMT_CSR, double>(__VA_ARGS__);       \
+        case FE_FMT_CSR * 3 + FE_VAL_F32: return FN<FE_FMT_CSR, float>(__VA_ARGS__);        \
+        case FE_FMT_CSR * 3 + FE_VAL_BF16: return FN<FE_FMT_CSR, __nv_bfloat16>(__VA_ARGS__); \
+        case FE_FMT_SELL * 3 + FE_VAL_F64: return FN<FE_FMT_SELL, double>(__VA_ARGS__);     \
+        case FE_FMT_SELL * 3 + FE_VAL_F32: return FN<FE_FMT_SELL, float>(__VA_ARGS__);      \
+        case FE_FMT_SELL * 3 + FE_VAL_BF16: return FN<FE_FMT_SELL, __nv_bfloat16>(__VA_ARGS__); \
+        case FE_FMT_BCRS3 * 3 + FE_VAL_F64: return FN<FE_FMT_BCRS3, double>(__VA_ARGS__);   \
+        case FE_FMT_BCRS3 * 3 + FE_VAL_F32: return FN<FE_FMT_BCRS3, float>(__VA_ARGS__);    \
+        case FE_FMT_BCRS3 * 3 + FE_VAL_BF16: return FN<FE_FMT_BCRS3, __nv_bfloat16>(__VA_ARGS__); \
+        default: return FE_ERR_ARG;                                                        \
+    }
+
+static fe_status dispatch_cg(const CgArgs &args, cudaStream_t s) {
+    FE_DISPATCH_FMT_VT(args.A, launch_cg, args, s)
+}
+
+static fe_status dispatch_resid(const fe_matrix &A, const double *b, const double *x, double *part,
+                                int *nblocks, cudaStream_t s) {
+    FE_DISPATCH_FMT_VT(A, launch_resid, A, b, x, part, nblocks, s)
+}
+
+}  // namespace fe
+
+using namespace fe;
+
+extern "C" {
+
+fe_status fe_inject_barrier_stall(int barrier_index) {
+    if (barrier_index < -1) return FE_ERR_ARG;
+    g_stall_barrier = barrier_index;
+    return FE_OK;
+}
+
+fe_status fe_cg_workspace(const fe_matrix *A, size_t *h_bytes) {
+    fe_status st = check_matrix(A);
+    if (st != FE_OK) return st;
+    if (h_bytes == nullptr) return FE_ERR_ARG;
+    *h_bytes = cg_workspace_bytes(*A);
+    return FE_OK;
+}
+
+fe_status fe_cg_solve(const fe_matrix *A, const double *d_b, double *d_x, double tol, int maxit,
+                      double timeout_s, void *d_work, size_t work_bytes, fe_cg_result *h_result,
+                      fe_stream_t stream) {
+    fe_status st = check_matrix(A);
+    if (st != FE_OK) return st;
+    if (!d_b || !d_x || !d_work || !h_result || maxit < 0 || !(tol >= 0.0)) return FE_ERR_ARG;
+    if (A->n_rows != A->n_cols) return FE_ERR_ARG;
+    if (!aligned(d_b, 8) || !aligned(d_x, 8) || !aligned(d_work, 256)) return FE_ERR_ARG;
+    if (work_bytes < cg_workspace_bytes(*A)) return FE_ERR_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+
+    char *ws = (char *)d_work;
+    CgArgs args;
+    args.A = *A;
+    args.b = d_b;
+    args.x = d_x;
+    args.ctrl = (CgCtrl *)ws;
+    args.part = (double *)(ws + 256);
+    const size_t vec = align256((size_t)A->n_slices * kSlice * sizeof(double));
+    char *v0 = ws + 256 + align256(2 * 2 * (size_t)kCgMaxBlocks * sizeof(double));
+    args.r = (double *)v0;
+    args.p = (double *)(v0 + vec);
+    args.w = (double *)(v0 + 2 * vec);
+    args.tol2 = tol * tol;
+    args.maxit = maxit;
+    const double tmo = timeout_s > 0.0 ? timeout_s : 2.0;
+    args.timeout_ns = (long long)(tmo * 1e9);
+    args.stall_barrier = g_stall_barrier;
+    g_stall_barrier = -1;
+
+    FE_TRY_CUDA(cudaMemsetAsync(args.ctrl, 0, sizeof(CgCtrl), s));
+    st = dispatch_cg(args, s);
+    if (st != FE_OK) return st;
+    CgCtrl ctrl;
+    FE_TRY_CUDA(cudaMemcpyAsync(&ctrl, args.ctrl, sizeof(CgCtrl), cudaMemcpyDeviceToHost, s));
+    FE_TRY_CUDA(cudaStreamSynchronize(s));
+    h_result->status = ctrl.status;
+    h_result->iterations = ctrl.iterations;
+    h_result->bnorm = sqrt(ctrl.bb);
+    h_result->relres = ctrl.bb > 0.0 ? sqrt(ctrl.rr / ctrl.bb) : 0.0;
+    return (fe_status)ctrl.status;
+}
+
+fe_status fe_true_relres(const fe_matrix *A, const double *d_b, const double *d_x, void *d_work,
+                         size_t work_bytes, double *h_relres, fe_stream_t stream) {
+    fe_status st = check_matrix(A);
+    if (st != FE_OK) return st;
+    if (!d_b || !d_x || !d_work || !h_relres || !aligned(d_work, 8)) return FE_ERR_ARG;
+    if (work_bytes < FE_RESID_WORK_BYTES) return FE_ERR_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    double *part = (double *)d_work;
+    double *out = part + 2 * kCgMaxBlocks;
+    int nblocks = 0;
+    st = dispatch_resid(*A, d_b, d_x, part, &nblocks, s);
+    if (st != FE_OK) return st;
+    k_resid_final<<<1, 32, 0, s>>>(nblocks, part, out);
+    FE_TRY_LAUNCH();
+    double h[2];
+    FE_TRY_CUDA(cudaMemcpyAsync(h, out, sizeof(h), cudaMemcpyDeviceToHost, s));
+    FE_TRY_CUDA(cudaStreamSynchronize(s));
+    *h_relres = h[1] > 0.0 ? sqrt(h[0] / h[1]) : sqrt(h[0]);
+    return FE_OK;
+}
+
+}  // extern "C"

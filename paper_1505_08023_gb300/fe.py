@@ -1,0 +1,333 @@
+"""Thin Python binding of libfe (include/fe.h).
+
+Every ``fe_*`` function here has the name and arguments of the C entry point
+and only marshals arguments: torch CUDA tensors become device pointers, the
+current torch stream becomes the ``stream`` argument, and a non-zero status
+raises :class:`FeError`.  All computation happens in the CUDA library; there is
+no CPU path.  If ``libfe.so`` has not been built the import fails loudly.
+
+``System`` strings the calls together for one mesh (buffers allocated with
+torch) and is what the tests and the benchmark use.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+from .build import LIB
+
+FE_OK, FE_ERR_ARG, FE_ERR_OVERFLOW, FE_ERR_CUDA = 0, -1, -2, -3
+FE_ERR_BREAKDOWN, FE_ERR_MAXIT, FE_ERR_TIMEOUT, FE_ERR_WORKSPACE = -4, -5, -6, -7
+STATUS_NAMES = {0: "FE_OK", -1: "FE_ERR_ARG", -2: "FE_ERR_OVERFLOW", -3: "FE_ERR_CUDA",
+                -4: "FE_ERR_BREAKDOWN", -5: "FE_ERR_MAXIT", -6: "FE_ERR_TIMEOUT",
+                -7: "FE_ERR_WORKSPACE"}
+
+FE_FMT_CSR, FE_FMT_SELL, FE_FMT_BCRS3 = 0, 1, 2
+FORMATS = {"csr": FE_FMT_CSR, "sell": FE_FMT_SELL, "bcrs3": FE_FMT_BCRS3}
+FE_VAL_F64, FE_VAL_F32, FE_VAL_BF16 = 0, 1, 2
+VALUE_TYPES = {"f64": FE_VAL_F64, "f32": FE_VAL_F32, "bf16": FE_VAL_BF16}
+TORCH_VALUE = {FE_VAL_F64: torch.float64, FE_VAL_F32: torch.float32, FE_VAL_BF16: torch.bfloat16}
+SLICE_ROWS = 32
+RESID_WORK_BYTES = 65536 + 64
+
+
+class FeError(RuntimeError):
+    def __init__(self, call: str, status: int):
+        self.status = status
+        extra = ""
+        if status == FE_ERR_CUDA and _lib is not None:
+            extra = f" (cuda error {_lib.fe_last_cuda_error()})"
+        super().__init__(f"{call} returned {STATUS_NAMES.get(status, status)}{extra}")
+
+
+class fe_sizes(ctypes.Structure):
+    _fields_ = [("n_rows", ctypes.c_int64), ("n_elems", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("n_faces", ctypes.c_int64), ("n_slices", ctypes.c_int64)]
+
+
+class fe_matrix(ctypes.Structure):
+    _fields_ = [("format", ctypes.c_int32), ("value_type", ctypes.c_int32),
+                ("n_rows", ctypes.c_int64), ("n_cols", ctypes.c_int64),
+                ("n_slices", ctypes.c_int64), ("n_stored", ctypes.c_int64),
+                ("d_row_ptr", ctypes.c_void_p), ("d_slice_ptr", ctypes.c_void_p),
+                ("d_cols", ctypes.c_void_p), ("d_vals", ctypes.c_void_p)]
+
+
+class fe_cg_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("iterations", ctypes.c_int32),
+                ("relres", ctypes.c_double), ("bnorm", ctypes.c_double)]
+
+
+# Exported entry points: name -> (restype, argtypes).  Tests check that the
+# shared library exports exactly these names and that include/fe.h declares them.
+_VP, _I32, _I64, _D, _SZ = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_size_t
+SIGNATURES = {
+    "fe_problem_sizes": (_I32, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(fe_sizes)]),
+    "fe_generate_mesh": (_I32, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "fe_assemble_workspace": (_I32, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_SZ)]),
+    "fe_assemble_csr": (_I32, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, _VP, _VP, _VP, _VP,
+                               _VP, _VP, _VP, _SZ, _VP]),
+    "fe_sliced_plan": (_I32, [_I32, _I64, _I64, _VP, _VP, _VP, ctypes.POINTER(_I64), _VP]),
+    "fe_convert": (_I32, [ctypes.POINTER(fe_matrix), ctypes.POINTER(fe_matrix), _VP]),
+    "fe_round_values": (_I32, [_I64, _VP, _I32, _VP, _VP]),
+    "fe_spmv": (_I32, [ctypes.POINTER(fe_matrix), _VP, _VP, _VP]),
+    "fe_spmv_f32": (_I32, [ctypes.POINTER(fe_matrix), _VP, _VP, _VP]),
+    "fe_cg_workspace": (_I32, [ctypes.POINTER(fe_matrix), ctypes.POINTER(_SZ)]),
+    "fe_cg_solve": (_I32, [ctypes.POINTER(fe_matrix), _VP, _VP, _D, ctypes.c_int, _D, _VP, _SZ,
+                           ctypes.POINTER(fe_cg_result), _VP]),
+    "fe_true_relres": (_I32, [ctypes.POINTER(fe_matrix), _VP, _VP, _VP, _SZ,
+                              ctypes.POINTER(_D), _VP]),
+    "fe_inject_barrier_stall": (_I32, [ctypes.c_int]),
+    "fe_last_cuda_error": (ctypes.c_int, []),
+    "fe_version": (ctypes.c_char_p, []),
+}
+
+_lib = None
+
+
+def load() -> ctypes.CDLL:
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB):
+        raise ImportError(f"libfe.so is missing ({LIB}); build it with "
+                          "`python -m paper_1505_08023_gb300.build` -- there is no CPU fallback")
+    lib = ctypes.CDLL(LIB)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(call: str, st: int) -> int:
+    if st != FE_OK:
+        raise FeError(call, st)
+    return st
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("expected a torch tensor")
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("device arrays must be contiguous CUDA tensors")
+    return t.data_ptr()
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+# ---------------------------------------------------------------- raw calls
+
+def fe_problem_sizes(nx: int, ny: int, nz: int) -> fe_sizes:
+    out = fe_sizes()
+    _check("fe_problem_sizes", load().fe_problem_sizes(nx, ny, nz, ctypes.byref(out)))
+    return out
+
+
+def fe_generate_mesh(nx, ny, nz, face_vals, coords, bc_flag, bc_val, conn=None, stream=None):
+    return _check("fe_generate_mesh", load().fe_generate_mesh(
+        nx, ny, nz, _ptr(face_vals), _ptr(coords), _ptr(bc_flag), _ptr(bc_val), _ptr(conn),
+        _stream(stream)))
+
+
+def fe_assemble_workspace(nx, ny, nz) -> int:
+    n = ctypes.c_size_t(0)
+    _check("fe_assemble_workspace", load().fe_assemble_workspace(nx, ny, nz, ctypes.byref(n)))
+    return n.value
+
+
+def fe_assemble_csr(nx, ny, nz, coords, bc_flag, bc_val, row_ptr, cols, vals, b, work,
+                    stream=None):
+    return _check("fe_assemble_csr", load().fe_assemble_csr(
+        nx, ny, nz, _ptr(coords), _ptr(bc_flag), _ptr(bc_val), _ptr(row_ptr), _ptr(cols),
+        _ptr(vals), _ptr(b), _ptr(work), work.numel() * work.element_size(), _stream(stream)))
+
+
+def fe_sliced_plan(fmt, n_rows, n_cols, row_ptr, cols, slice_ptr, stream=None) -> int:
+    n = ctypes.c_int64(0)
+    _check("fe_sliced_plan", load().fe_sliced_plan(
+        fmt, n_rows, n_cols, _ptr(row_ptr), _ptr(cols), _ptr(slice_ptr), ctypes.byref(n),
+        _stream(stream)))
+    return n.value
+
+
+def fe_convert(src: fe_matrix, dst: fe_matrix, stream=None):
+    return _check("fe_convert", load().fe_convert(ctypes.byref(src), ctypes.byref(dst),
+                                                  _stream(stream)))
+
+
+def fe_round_values(n, src, value_type, dst, stream=None):
+    return _check("fe_round_values", load().fe_round_values(n, _ptr(src), value_type, _ptr(dst),
+                                                            _stream(stream)))
+
+
+def fe_spmv(A: fe_matrix, x, y, stream=None):
+    return _check("fe_spmv", load().fe_spmv(ctypes.byref(A), _ptr(x), _ptr(y), _stream(stream)))
+
+
+def fe_spmv_f32(A: fe_matrix, x, y, stream=None):
+    return _check("fe_spmv_f32", load().fe_spmv_f32(ctypes.byref(A), _ptr(x), _ptr(y),
+                                                    _stream(stream)))
+
+
+def fe_cg_workspace(A: fe_matrix) -> int:
+    n = ctypes.c_size_t(0)
+    _check("fe_cg_workspace", load().fe_cg_workspace(ctypes.byref(A), ctypes.byref(n)))
+    return n.value
+
+
+def fe_cg_solve(A: fe_matrix, b, x, tol, maxit, work, timeout_s=0.0, stream=None,
+                check=True) -> fe_cg_result:
+    res = fe_cg_result()
+    st = load().fe_cg_solve(ctypes.byref(A), _ptr(b), _ptr(x), float(tol), int(maxit),
+                            float(timeout_s), _ptr(work), work.numel() * work.element_size(),
+                            ctypes.byref(res), _stream(stream))
+    if check and st not in (FE_OK,):
+        raise FeError("fe_cg_solve", st)
+    return res
+
+
+def fe_true_relres(A: fe_matrix, b, x, work, stream=None) -> float:
+    out = ctypes.c_double(0.0)
+    _check("fe_true_relres", load().fe_true_relres(
+        ctypes.byref(A), _ptr(b), _ptr(x), _ptr(work), work.numel() * work.element_size(),
+        ctypes.byref(out), _stream(stream)))
+    return out.value
+
+
+def fe_inject_barrier_stall(barrier_index: int):
+    return _check("fe_inject_barrier_stall", load().fe_inject_barrier_stall(barrier_index))
+
+
+def fe_version() -> str:
+    return load().fe_version().decode()
+
+
+# ---------------------------------------------------------------- one mesh, end to end
+
+def _alloc_bytes(n: int, device) -> torch.Tensor:
+    # 256-byte alignment comes with the caching allocator (512-byte blocks)
+    return torch.empty(max(n, 1), dtype=torch.uint8, device=device)
+
+
+@dataclass
+class DeviceMatrix:
+    """A matrix in one format plus the tensors that own its memory."""
+    desc: fe_matrix
+    tensors: dict
+
+    @property
+    def format(self) -> int:
+        return self.desc.format
+
+    def stored_bytes(self) -> int:
+        return sum(t.numel() * t.element_size() for t in self.tensors.values())
+
+
+class System:
+    """Mesh, assembled CSR system and solver buffers for one nx x ny x nz problem."""
+
+    def __init__(self, nx: int, ny: int | None = None, nz: int | None = None, device="cuda",
+                 face_vals: torch.Tensor | None = None, keep_conn: bool = False):
+        ny = nx if ny is None else ny
+        nz = nx if nz is None else nz
+        self.dims = (nx, ny, nz)
+        self.device = torch.device(device)
+        self.sizes = fe_problem_sizes(nx, ny, nz)
+        m, nnz = self.sizes.n_rows, self.sizes.nnz
+        dev = self.device
+        self.coords = torch.empty((m, 3), dtype=torch.float64, device=dev)
+        self.bc_flag = torch.empty(m, dtype=torch.uint8, device=dev)
+        self.bc_val = torch.empty(m, dtype=torch.float64, device=dev)
+        self.conn = (torch.empty((self.sizes.n_elems, 8), dtype=torch.int32, device=dev)
+                     if keep_conn else None)
+        self.row_ptr = torch.empty(m + 1, dtype=torch.int32, device=dev)
+        self.cols = torch.empty(nnz, dtype=torch.int32, device=dev)
+        self.vals = torch.empty(nnz, dtype=torch.float64, device=dev)
+        self.b = torch.empty(m, dtype=torch.float64, device=dev)
+        self.face_vals = face_vals
+        self._asm_work = None
+        self._formats: dict = {}
+
+    # -- pipeline steps
+    def generate_mesh(self, stream=None):
+        fe_generate_mesh(*self.dims, self.face_vals, self.coords, self.bc_flag, self.bc_val,
+                         self.conn, stream)
+
+    def assemble(self, stream=None, keep_workspace: bool = False):
+        if self._asm_work is None:
+            self._asm_work = _alloc_bytes(fe_assemble_workspace(*self.dims), self.device)
+        fe_assemble_csr(*self.dims, self.coords, self.bc_flag, self.bc_val, self.row_ptr,
+                        self.cols, self.vals, self.b, self._asm_work, stream)
+        if not keep_workspace:
+            # the caching allocator reuses the block only after work already
+            # queued on the stream that used it
+            if stream is not None:
+                self._asm_work.record_stream(stream)
+            self._asm_work = None
+
+    def build(self, stream=None):
+        self.generate_mesh(stream)
+        self.assemble(stream)
+        return self
+
+    @property
+    def m(self) -> int:
+        return self.sizes.n_rows
+
+    def csr(self) -> DeviceMatrix:
+        d = fe_matrix(FE_FMT_CSR, FE_VAL_F64, self.m, self.m, self.sizes.n_slices,
+                      self.sizes.nnz, self.row_ptr.data_ptr(), None, self.cols.data_ptr(),
+                      self.vals.data_ptr())
+        return DeviceMatrix(d, {"row_ptr": self.row_ptr, "cols": self.cols, "vals": self.vals})
+
+    def matrix(self, fmt: str = "csr", value: str = "f64", stream=None) -> DeviceMatrix:
+        """The assembled matrix in a storage format (converted and cached on first use)."""
+        key = (fmt, value)
+        if key in self._formats:
+            return self._formats[key]
+        f, vt = FORMATS[fmt], VALUE_TYPES[value]
+        src = self.csr()
+        if f == FE_FMT_CSR:
+            if vt == FE_VAL_F64:
+                return src
+            v = torch.empty(self.sizes.nnz, dtype=TORCH_VALUE[vt], device=self.device)
+            fe_round_values(self.sizes.nnz, self.vals, vt, v, stream)
+            d = fe_matrix(f, vt, self.m, self.m, self.sizes.n_slices, self.sizes.nnz,
+                          self.row_ptr.data_ptr(), None, self.cols.data_ptr(), v.data_ptr())
+            dm = DeviceMatrix(d, {"row_ptr": self.row_ptr, "cols": self.cols, "vals": v})
+        else:
+            ns = self.sizes.n_slices
+            sp = torch.empty(ns + 1, dtype=torch.int64, device=self.device)
+            n_stored = fe_sliced_plan(f, self.m, self.m, self.row_ptr, self.cols, sp, stream)
+            cols = torch.empty(n_stored, dtype=torch.int32, device=self.device)
+            nv = n_stored * (3 if f == FE_FMT_BCRS3 else 1)
+            v = torch.empty(nv, dtype=TORCH_VALUE[vt], device=self.device)
+            d = fe_matrix(f, vt, self.m, self.m, ns, n_stored, None, sp.data_ptr(),
+                          cols.data_ptr(), v.data_ptr())
+            fe_convert(src.desc, d, stream)
+            dm = DeviceMatrix(d, {"slice_ptr": sp, "cols": cols, "vals": v})
+        self._formats[key] = dm
+        return dm
+
+    def drop_formats(self):
+        self._formats.clear()
+
+
+def cg_workspace(A: DeviceMatrix, device="cuda") -> torch.Tensor:
+    return _alloc_bytes(fe_cg_workspace(A.desc), device)
+
+
+def resid_workspace(device="cuda") -> torch.Tensor:
+    return _alloc_bytes(RESID_WORK_BYTES, device)
