@@ -108,9 +108,18 @@ void orc_element_nodes(int nx, int ny, int nz, int64_t e, int64_t nodes[8])
 /* the hexahedron, trilinear shape functions, 2x2x2 Gauss-Legendre rule      */
 /* (points +-1/sqrt(3), weights 1), Jacobian taken from the node coords.     */
 /* X[3*a + i] = coordinate i of local node a; K is row-major 8x8.            */
+/* The operator depends on the element's shape only, so the Jacobian is      */
+/* built from corner offsets X_a - X_0: the same integral without the        */
+/* cancellation of summing absolute coordinates of size 1 into entries of    */
+/* size h.                                                                   */
 /* ------------------------------------------------------------------------ */
-void orc_element_matrix(const double *X, double *K)
+void orc_element_matrix(const double *Xabs, double *K)
 {
+    double X[24];
+    for (int a = 0; a < 8; ++a)
+        for (int i = 0; i < 3; ++i)
+            X[3 * a + i] = Xabs[3 * a + i] - Xabs[i];
+
     const double g = 1.0 / sqrt(3.0);
     const double gauss_pt[2] = {-g, g};
     for (int k = 0; k < 64; ++k)

@@ -63,6 +63,8 @@ k_element_matrices(int nx, int ny, int nz, const double *__restrict__ coords,
         const int ey = (int)(q0 % ny);
         const int ez = (int)(q0 / ny);
         const int64_t n0 = ex + nxn * (ey + (int64_t)(ny + 1) * ez);
+        // corner offsets from corner 0: the operator is translation invariant,
+        // and offsets of size h keep the Jacobian free of cancellation
         double X[8][3];
 #pragma unroll
         for (int a = 0; a < 8; ++a) {
@@ -70,6 +72,10 @@ k_element_matrices(int nx, int ny, int nz, const double *__restrict__ coords,
 #pragma unroll
             for (int i = 0; i < 3; ++i) X[a][i] = coords[3 * node + i];
         }
+#pragma unroll
+        for (int a = 7; a >= 0; --a)
+#pragma unroll
+            for (int i = 0; i < 3; ++i) X[a][i] -= X[0][i];
         double K[36];
 #pragma unroll
         for (int k = 0; k < 36; ++k) K[k] = 0.0;
