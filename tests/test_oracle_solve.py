@@ -123,3 +123,38 @@ def test_fe_solution_converges_to_series(n_pair):
     assert 3.0 < errs_c[0] / errs_c[1] < 5.0
     assert 3.0 < errs_w[0] / errs_w[1] < 5.0
     assert errs_c[1] < 2.5e-3
+
+
+def test_summation_order_changes_iterates():
+    """CG amplifies rounding: the same iteration with pairwise instead of
+    sequential dot products stops within a step of the oracle, but after the
+    same number of steps its iterate differs from the oracle's by more than
+    1e-10 (one step near the stop moves x by ~1e-9), while both solved to 1e-12
+    agree to 1e-10.  This fixes the form of the GPU solution criteria."""
+    sysm = oracle.build_system(30, 30, 30)
+    A = csr(sysm)
+    b = sysm["b"]
+
+    def cg_pairwise(tol):
+        x = np.zeros_like(b)
+        r = b.copy()
+        p = r.copy()
+        rr, bb, k = np.dot(r, r), np.dot(b, b), 0
+        while rr > tol * tol * bb:
+            w = A @ p
+            a = rr / np.dot(p, w)
+            x += a * p
+            r -= a * w
+            rn = np.dot(r, r)
+            p = r + (rn / rr) * p
+            rr, k = rn, k + 1
+        return x, k
+
+    x10, k10 = cg_pairwise(1e-10)
+    xo10, ko10, _, _ = oracle.cg(sysm["row_ptr"], sysm["cols"], sysm["vals"], b, tol=1e-10)
+    assert abs(k10 - ko10) <= 1
+    xo_k, _, _, _ = oracle.cg(sysm["row_ptr"], sysm["cols"], sysm["vals"], b, tol=0.0, maxit=k10)
+    assert np.linalg.norm(x10 - xo_k) > 1e-10 * np.linalg.norm(xo_k)
+    x12, _ = cg_pairwise(1e-12)
+    xo12, _, _, _ = oracle.cg(sysm["row_ptr"], sysm["cols"], sysm["vals"], b, tol=1e-12)
+    assert np.linalg.norm(x12 - xo12) <= 1e-10 * np.linalg.norm(xo12)
