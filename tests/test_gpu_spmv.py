@@ -5,9 +5,11 @@ Tolerances come from the forward error bound of a length-k dot product
 (Higham, Thm 3.5): |fl(sum) - sum| <= gamma_k sum |a_ij x_j|, gamma_k ~ k u.
 Both sides round, so the bar is 2 k u sum |a_ij x_j| with k = 27 (longest
 row) and u = 2^-53 for FP64 accumulation, 2^-24 for FP32 accumulation.
-Values stored in FP32/BF16 are compared against the oracle applied to the
-same rounded values (rounded by the oracle, and the GPU's rounded arrays
-must equal them bit for bit).
+Values stored in FP32/BF16: the oracle rounds its own FP64 values; the GPU
+rounds its own.  Wherever the two FP64 inputs agree bit for bit the rounded
+values must too, elsewhere they may differ by one unit of the stored type
+(the FP64 values themselves agree to 1e-14 of the row scale).  The SpMV bar
+adds the measured effect of those value differences, sum |dv_ij| |x_j|.
 """
 import numpy as np
 import pytest
@@ -44,6 +46,16 @@ def rounded(ref_vals, value):
             "bf16": oracle.round_to_bf16(ref_vals)}[value]
 
 
+def gpu_values(s, value):
+    """The GPU's stored values (every format rounds the same FP64 array elementwise)."""
+    return s.matrix("csr", value).tensors["vals"].double().cpu().numpy()
+
+
+def value_slack(s, ref, value, x):
+    dv = np.abs(gpu_values(s, value) - rounded(ref["vals"], value))
+    return oracle.spmv_csr(ref["row_ptr"], ref["cols"], dv, np.abs(x))
+
+
 DIMS = [(1, 1, 1), (2, 2, 2), (5, 4, 3), (30, 30, 30), (31, 7, 13)]
 
 
@@ -61,7 +73,8 @@ def test_spmv_f64_vectors(fe, dims, fmt, value):
     got = y.cpu().numpy()
     want = oracle.spmv_csr(ref["row_ptr"], ref["cols"], v, x)
     absum = oracle.spmv_csr(ref["row_ptr"], ref["cols"], np.abs(v), np.abs(x))
-    assert np.all(np.abs(got - want) <= 2 * K * U64 * absum + 1e-300)
+    slack = value_slack(s, ref, value, x)
+    assert np.all(np.abs(got - want) <= 2 * K * U64 * absum + slack + 1e-300)
 
 
 @pytest.mark.parametrize("dims", [(5, 4, 3), (30, 30, 30)])
@@ -79,15 +92,22 @@ def test_spmv_f32_vectors(fe, dims, fmt, value):
     # FP64 values enter the FP32 product rounded to FP32: one more u per term
     want = oracle.spmv_csr(ref["row_ptr"], ref["cols"], v, x)
     absum = oracle.spmv_csr(ref["row_ptr"], ref["cols"], np.abs(v), np.abs(x))
-    assert np.all(np.abs(got - want) <= 2 * (K + 2) * U32 * absum + 1e-38)
+    slack = value_slack(s, ref, value, x)
+    assert np.all(np.abs(got - want) <= 2 * (K + 2) * U32 * absum + slack + 1e-38)
 
 
 @pytest.mark.parametrize("value", ["f32", "bf16"])
-def test_rounded_values_bit_exact(fe, value):
-    s, ref = system(fe, (30, 30, 30))
-    A = s.matrix("csr", value)
-    got = A.tensors["vals"].double().cpu().numpy()
-    assert np.array_equal(got, rounded(ref["vals"], value))
+@pytest.mark.parametrize("dims", [(30, 30, 30), (31, 7, 13)])
+def test_rounded_values(fe, value, dims):
+    s, ref = system(fe, dims)
+    got = gpu_values(s, value)
+    want = rounded(ref["vals"], value)
+    same_input = s.vals.cpu().numpy() == ref["vals"]
+    assert np.array_equal(got[same_input], want[same_input])
+    # elsewhere: at most one unit in the last place of the stored type
+    bits = 8 if value == "bf16" else 24
+    ulp = np.ldexp(1.0, np.frexp(np.maximum(np.abs(want), np.abs(got)))[1] - bits)
+    assert np.all(np.abs(got - want)[~same_input] <= ulp[~same_input])
 
 
 @pytest.mark.parametrize("fmt", ["sell", "bcrs3"])
