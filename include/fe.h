@@ -204,6 +204,40 @@ fe_status fe_cg_solve(const fe_matrix *A, const double *d_b, double *d_x, double
                       double timeout_s, void *d_work, size_t work_bytes,
                       fe_cg_result *h_result, fe_stream_t stream);
 
+/* Result of a mixed-precision solve. */
+typedef struct fe_mixed_result {
+    int32_t status;            /* fe_status of the solve */
+    int32_t outer_iterations;  /* refinement steps (inner solves) */
+    int32_t inner_iterations;  /* FP32 CG steps over all inner solves */
+    int32_t reserved;
+    double relres;             /* true FP64 ||b - A64 x|| / ||b|| at exit */
+    double bnorm;              /* ||b|| */
+} fe_mixed_result;
+
+/* Workspace of fe_cg_solve_mixed for the low-precision matrix A_lo: five FP32
+ * vectors of 32 * n_slices entries plus reduction blocks. */
+fe_status fe_cg_mixed_workspace(const fe_matrix *A_lo, size_t *h_bytes);
+
+/*
+ * Mixed-precision form of the solve (not in the paper; the FP64 path is its
+ * judge): iterative refinement around an FP32 inner CG.
+ *   repeat: r = b - A64 x       (FP64 matrix, FP64 accumulation, FP64 ||r||)
+ *           stop if ||r|| <= tol ||b|| or after max_outer inner solves
+ *           solve A_lo d = r    (the persistent CG kernel with FP32 vectors and
+ *                                FP32 accumulation; dot products reduced over
+ *                                the grid in FP64) to ||r_in|| <= inner_tol ||r||
+ *                                or max_inner steps
+ *           x += d              (FP64)
+ *   A64: value_type FE_VAL_F64, any format; A_lo: the same matrix with FP32 or
+ *   BF16 (or FP64) values, any format.  The stopping test uses the true FP64
+ *   residual.  d_x: start in, solution out.  d_work: fe_cg_mixed_workspace()
+ *   bytes, 256-byte aligned.  Synchronises `stream` once per outer step.
+ */
+fe_status fe_cg_solve_mixed(const fe_matrix *A64, const fe_matrix *A_lo, const double *d_b,
+                            double *d_x, double tol, int max_outer, double inner_tol,
+                            int max_inner, double timeout_s, void *d_work, size_t work_bytes,
+                            fe_mixed_result *h_result, fe_stream_t stream);
+
 /* Fault injection for tests of the barrier time limit: the next fe_cg_solve
  * on the calling thread has block 0 skip its arrival at grid barrier number
  * barrier_index (0 = the barrier after the initial residual), so every

@@ -12,6 +12,10 @@
 // Two partial buffers alternate, so a block that races ahead into the next
 // reduction never overwrites partials another block is still reading.
 //
+// The same kernel, instantiated with FP32 vectors, is the inner solver of the
+// mixed-precision form: SpMV and per-thread dot partials in FP32, the grid
+// reduction of every dot product in FP64, alpha and beta in FP64.
+//
 // The grid barrier counts arrivals on a 64-bit counter (release add, acquire
 // poll).  Every wait is bounded: past `timeout_ns` (or a poll cap) the block
 // raises the abort flag and leaves; the others see the flag at their next
@@ -37,16 +41,18 @@ struct CgCtrl {
     double bb;
 };
 
-struct CgArgs {
+template <class XT> struct CgArgs {
     fe_matrix A;
-    const double *b;
-    double *x, *r, *p, *w;
+    const XT *b;
+    XT *x, *r, *p, *w;
     double *part;            // [2][2 * kCgMaxBlocks]
     CgCtrl *ctrl;
     double tol2;
     int maxit;
+    int x0_zero;             // start from x = 0 without reading x (skips one SpMV)
     long long timeout_ns;
     long long stall_barrier;  // fault injection: block 0 skips this arrival (-1: none)
+    double *x64;             // if set: x64 += x on exit (mixed-precision refinement step)
 };
 
 __device__ __forceinline__ long long global_ns() {
@@ -95,7 +101,8 @@ __device__ __forceinline__ bool grid_barrier(CgCtrl *ctrl, unsigned long long &t
 }
 
 // Sum (v0, v1) over the whole grid; see the file comment for the order.
-__device__ __forceinline__ bool grid_sum2(const CgArgs &a, double v0, double v1, double &o0,
+template <class XT>
+__device__ __forceinline__ bool grid_sum2(const CgArgs<XT> &a, double v0, double v1, double &o0,
                                           double &o1, int &round, unsigned long long &target,
                                           double (*red)[2], int *s_ok) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -129,14 +136,14 @@ __device__ __forceinline__ bool grid_sum2(const CgArgs &a, double v0, double v1,
     return true;
 }
 
-template <int FMT, class VT>
-__global__ void __launch_bounds__(kCgThreads, 2) k_cg(const CgArgs a) {
+template <int FMT, class VT, class XT>
+__global__ void __launch_bounds__(kCgThreads, 2) k_cg(const CgArgs<XT> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[kCgWarps][2];
     __shared__ int s_ok;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    double *sv = reinterpret_cast<double *>(smem_raw) + (size_t)warp * 2 * kCsrStage;
-    double *sx = sv + kCsrStage;
+    XT *sv = reinterpret_cast<XT *>(smem_raw) + (size_t)warp * 2 * kCsrStage;
+    XT *sx = sv + kCsrStage;
     const int64_t m = a.A.n_rows, ns = a.A.n_slices;
     const int64_t gw = (int64_t)blockIdx.x * kCgWarps + warp;
     const int64_t tw = (int64_t)gridDim.x * kCgWarps;
@@ -149,25 +156,27 @@ __global__ void __launch_bounds__(kCgThreads, 2) k_cg(const CgArgs a) {
 
     // r = b - A x, p = r; r.r and b.b
     {
-        double s0 = 0.0, s1 = 0.0;
+        XT s0 = XT(0), s1 = XT(0);
         for (int64_t s = gw; s < ns; s += tw) {
-            const double ax = slice_spmv<FMT, VT, double, double, false>(a.A, s, lane, a.x, sv, sx);
+            XT ax = XT(0);
+            if (!a.x0_zero) ax = slice_spmv<FMT, VT, XT, XT, false>(a.A, s, lane, a.x, sv, sx);
             const int64_t row = s * kSlice + lane;
             if (row < m) {
-                const double bi = a.b[row];
-                const double ri = bi - ax;
+                const XT bi = a.b[row];
+                const XT ri = bi - ax;
+                if (a.x0_zero) a.x[row] = XT(0);
                 a.r[row] = ri;
                 a.p[row] = ri;
                 s0 = fma(ri, ri, s0);
                 s1 = fma(bi, bi, s1);
             }
         }
-        alive = grid_sum2(a, s0, s1, rr, bb, round, target, red, &s_ok);
+        alive = grid_sum2(a, (double)s0, (double)s1, rr, bb, round, target, red, &s_ok);
     }
     if (alive && bb == 0.0) {  // b = 0: the solution is 0
         for (int64_t s = gw; s < ns; s += tw) {
             const int64_t row = s * kSlice + lane;
-            if (row < m) a.x[row] = 0.0;
+            if (row < m) a.x[row] = XT(0);
         }
         rr = 0.0;
         status = FE_OK;
@@ -176,9 +185,9 @@ __global__ void __launch_bounds__(kCgThreads, 2) k_cg(const CgArgs a) {
             if (rr <= a.tol2 * bb) { status = FE_OK; break; }
             if (k >= a.maxit) { status = FE_ERR_MAXIT; break; }
             // A: w = A p, p.w
-            double pw_part = 0.0;
+            XT pw_part = XT(0);
             for (int64_t s = gw; s < ns; s += tw) {
-                const double y = slice_spmv<FMT, VT, double, double, false>(a.A, s, lane, a.p, sv, sx);
+                const XT y = slice_spmv<FMT, VT, XT, XT, false>(a.A, s, lane, a.p, sv, sx);
                 const int64_t row = s * kSlice + lane;
                 if (row < m) {
                     a.w[row] = y;
@@ -186,34 +195,43 @@ __global__ void __launch_bounds__(kCgThreads, 2) k_cg(const CgArgs a) {
                 }
             }
             double pw, unused;
-            if (!(alive = grid_sum2(a, pw_part, 0.0, pw, unused, round, target, red, &s_ok))) break;
+            if (!(alive = grid_sum2(a, (double)pw_part, 0.0, pw, unused, round, target, red, &s_ok))) break;
             if (!(pw > 0.0) || !(pw < INFINITY)) { status = FE_ERR_BREAKDOWN; break; }
             const double alpha = rr / pw;
+            const XT alpha_x = (XT)alpha;
             // B: x += alpha p, r -= alpha w, r.r
-            double rr_part = 0.0;
+            XT rr_part = XT(0);
             for (int64_t s = gw; s < ns; s += tw) {
                 const int64_t row = s * kSlice + lane;
                 if (row < m) {
-                    const double pi = a.p[row], wi = a.w[row];
-                    a.x[row] = fma(alpha, pi, a.x[row]);
-                    const double ri = fma(-alpha, wi, a.r[row]);
+                    const XT pi = a.p[row], wi = a.w[row];
+                    a.x[row] = fma(alpha_x, pi, a.x[row]);
+                    const XT ri = fma(-alpha_x, wi, a.r[row]);
                     a.r[row] = ri;
                     rr_part = fma(ri, ri, rr_part);
                 }
             }
             double rr_new;
-            if (!(alive = grid_sum2(a, rr_part, 0.0, rr_new, unused, round, target, red, &s_ok))) break;
+            if (!(alive = grid_sum2(a, (double)rr_part, 0.0, rr_new, unused, round, target, red, &s_ok))) break;
             const double beta = rr_new / rr;
             rr = rr_new;
             ++k;
             if (rr <= a.tol2 * bb) { status = FE_OK; break; }
             if (k >= a.maxit) { status = FE_ERR_MAXIT; break; }
             // C: p = r + beta p
+            const XT beta_x = (XT)beta;
             for (int64_t s = gw; s < ns; s += tw) {
                 const int64_t row = s * kSlice + lane;
-                if (row < m) a.p[row] = fma(beta, a.p[row], a.r[row]);
+                if (row < m) a.p[row] = fma(beta_x, a.p[row], a.r[row]);
             }
             if (!(alive = grid_barrier(a.ctrl, target, a.timeout_ns, a.stall_barrier, &s_ok))) break;
+        }
+    }
+    // refinement step of the mixed-precision form: x64 += x (own rows only)
+    if (a.x64 != nullptr && alive && (status == FE_OK || status == FE_ERR_MAXIT)) {
+        for (int64_t s = gw; s < ns; s += tw) {
+            const int64_t row = s * kSlice + lane;
+            if (row < m) a.x64[row] += (double)a.x[row];
         }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -225,10 +243,13 @@ __global__ void __launch_bounds__(kCgThreads, 2) k_cg(const CgArgs a) {
 }
 
 // r = b - A x over the block's slices; r.r and b.b partials per block.
+// With r32 set, also stores r in FP32 (the right-hand side of the inner solve
+// of the mixed-precision form).
 template <int FMT, class VT>
 __global__ void __launch_bounds__(kCgThreads) k_resid(const fe_matrix A, const double *__restrict__ b,
                                                       const double *__restrict__ x,
-                                                      double *__restrict__ part) {
+                                                      double *__restrict__ part,
+                                                      float *__restrict__ r32) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[kCgWarps][2];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -241,6 +262,7 @@ __global__ void __launch_bounds__(kCgThreads) k_resid(const fe_matrix A, const d
         const int64_t row = s * kSlice + lane;
         if (row < A.n_rows) {
             const double bi = b[row], ri = bi - ax;
+            if (r32 != nullptr) r32[row] = (float)ri;
             s0 = fma(ri, ri, s0);
             s1 = fma(bi, bi, s1);
         }
@@ -287,10 +309,10 @@ static size_t cg_workspace_bytes(const fe_matrix &A) {
     return 256 + align256(2 * 2 * (size_t)kCgMaxBlocks * sizeof(double)) + 3 * vec;
 }
 
-template <int FMT, class VT>
-static fe_status launch_cg(const CgArgs &args, cudaStream_t s) {
-    auto kern = k_cg<FMT, VT>;
-    const size_t smem = spmv_smem_bytes<FMT, double>(kCgWarps);
+template <int FMT, class VT, class XT>
+static fe_status launch_cg(const CgArgs<XT> &args, cudaStream_t s) {
+    auto kern = k_cg<FMT, VT, XT>;
+    const size_t smem = spmv_smem_bytes<FMT, XT>(kCgWarps);
     if (smem > 48 * 1024)
         FE_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
@@ -309,7 +331,7 @@ static fe_status launch_cg(const CgArgs &args, cudaStream_t s) {
 
 template <int FMT, class VT>
 static fe_status launch_resid(const fe_matrix &A, const double *b, const double *x, double *part,
-                              int *nblocks, cudaStream_t s) {
+                              float *r32, int *nblocks, cudaStream_t s) {
     auto kern = k_resid<FMT, VT>;
     const size_t smem = spmv_smem_bytes<FMT, double>(kCgWarps);
     if (smem > 48 * 1024)
@@ -322,7 +344,7 @@ static fe_status launch_resid(const fe_matrix &A, const double *b, const double 
     if (blocks > need) blocks = need;
     if (blocks > kCgMaxBlocks) blocks = kCgMaxBlocks;
     if (blocks < 1) blocks = 1;
-    kern<<<(int)blocks, kCgThreads, smem, s>>>(A, b, x, part);
+    kern<<<(int)blocks, kCgThreads, smem, s>>>(A, b, x, part, r32);
     FE_TRY_LAUNCH();
     *nblocks = (int)blocks;
     return FE_OK;
@@ -342,13 +364,24 @@ static fe_status launch_resid(const fe_matrix &A, const double *b, const double 
         default: return FE_ERR_ARG;                                                        \
     }
 
-static fe_status dispatch_cg(const CgArgs &args, cudaStream_t s) {
-    FE_DISPATCH_FMT_VT(args.A, launch_cg, args, s)
+template <int FMT, class VT> static fe_status launch_cg64(const CgArgs<double> &a, cudaStream_t s) {
+    return launch_cg<FMT, VT, double>(a, s);
+}
+template <int FMT, class VT> static fe_status launch_cg32(const CgArgs<float> &a, cudaStream_t s) {
+    return launch_cg<FMT, VT, float>(a, s);
+}
+
+static fe_status dispatch_cg(const CgArgs<double> &args, cudaStream_t s) {
+    FE_DISPATCH_FMT_VT(args.A, launch_cg64, args, s)
+}
+
+static fe_status dispatch_cg(const CgArgs<float> &args, cudaStream_t s) {
+    FE_DISPATCH_FMT_VT(args.A, launch_cg32, args, s)
 }
 
 static fe_status dispatch_resid(const fe_matrix &A, const double *b, const double *x, double *part,
-                                int *nblocks, cudaStream_t s) {
-    FE_DISPATCH_FMT_VT(A, launch_resid, A, b, x, part, nblocks, s)
+                                float *r32, int *nblocks, cudaStream_t s) {
+    FE_DISPATCH_FMT_VT(A, launch_resid, A, b, x, part, r32, nblocks, s)
 }
 
 }  // namespace fe
@@ -383,7 +416,7 @@ fe_status fe_cg_solve(const fe_matrix *A, const double *d_b, double *d_x, double
     cudaStream_t s = (cudaStream_t)stream;
 
     char *ws = (char *)d_work;
-    CgArgs args;
+    CgArgs<double> args;
     args.A = *A;
     args.b = d_b;
     args.x = d_x;
@@ -399,6 +432,8 @@ fe_status fe_cg_solve(const fe_matrix *A, const double *d_b, double *d_x, double
     const double tmo = timeout_s > 0.0 ? timeout_s : 2.0;
     args.timeout_ns = (long long)(tmo * 1e9);
     args.stall_barrier = g_stall_barrier;
+    args.x0_zero = 0;
+    args.x64 = nullptr;
     g_stall_barrier = -1;
 
     FE_TRY_CUDA(cudaMemsetAsync(args.ctrl, 0, sizeof(CgCtrl), s));
@@ -424,7 +459,7 @@ fe_status fe_true_relres(const fe_matrix *A, const double *d_b, const double *d_
     double *part = (double *)d_work;
     double *out = part + 2 * kCgMaxBlocks;
     int nblocks = 0;
-    st = dispatch_resid(*A, d_b, d_x, part, &nblocks, s);
+    st = dispatch_resid(*A, d_b, d_x, part, nullptr, &nblocks, s);
     if (st != FE_OK) return st;
     k_resid_final<<<1, 32, 0, s>>>(nblocks, part, out);
     FE_TRY_LAUNCH();
@@ -433,6 +468,118 @@ fe_status fe_true_relres(const fe_matrix *A, const double *d_b, const double *d_
     FE_TRY_CUDA(cudaStreamSynchronize(s));
     *h_relres = h[1] > 0.0 ? sqrt(h[0] / h[1]) : sqrt(h[0]);
     return FE_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- mixed precision
+
+namespace fe {
+
+static size_t mixed_workspace_bytes(const fe_matrix &lo) {
+    const size_t vec = align256((size_t)lo.n_slices * kSlice * sizeof(float));
+    return 256 + align256(2 * 2 * (size_t)kCgMaxBlocks * sizeof(double)) +
+           align256(FE_RESID_WORK_BYTES) + 5 * vec;
+}
+
+}  // namespace fe
+
+extern "C" {
+
+fe_status fe_cg_mixed_workspace(const fe_matrix *A_lo, size_t *h_bytes) {
+    fe_status st = check_matrix(A_lo);
+    if (st != FE_OK) return st;
+    if (h_bytes == nullptr) return FE_ERR_ARG;
+    *h_bytes = mixed_workspace_bytes(*A_lo);
+    return FE_OK;
+}
+
+fe_status fe_cg_solve_mixed(const fe_matrix *A64, const fe_matrix *A_lo, const double *d_b,
+                            double *d_x, double tol, int max_outer, double inner_tol,
+                            int max_inner, double timeout_s, void *d_work, size_t work_bytes,
+                            fe_mixed_result *h_result, fe_stream_t stream) {
+    fe_status st = check_matrix(A64);
+    if (st != FE_OK) return st;
+    st = check_matrix(A_lo);
+    if (st != FE_OK) return st;
+    if (A64->value_type != FE_VAL_F64 || A64->n_rows != A64->n_cols ||
+        A_lo->n_rows != A64->n_rows || A_lo->n_cols != A64->n_cols)
+        return FE_ERR_ARG;
+    if (!d_b || !d_x || !d_work || !h_result || max_outer < 0 || max_inner < 0 || !(tol >= 0.0) ||
+        !(inner_tol > 0.0 && inner_tol < 1.0))
+        return FE_ERR_ARG;
+    if (!aligned(d_b, 8) || !aligned(d_x, 8) || !aligned(d_work, 256)) return FE_ERR_ARG;
+    if (work_bytes < mixed_workspace_bytes(*A_lo)) return FE_ERR_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+
+    char *ws = (char *)d_work;
+    CgCtrl *ctrl = (CgCtrl *)ws;
+    double *cg_part = (double *)(ws + 256);
+    char *q = ws + 256 + align256(2 * 2 * (size_t)kCgMaxBlocks * sizeof(double));
+    double *res_part = (double *)q;
+    double *res_out = res_part + 2 * kCgMaxBlocks;
+    q += align256(FE_RESID_WORK_BYTES);
+    const size_t vec = align256((size_t)A_lo->n_slices * kSlice * sizeof(float));
+    float *r32 = (float *)q, *d32 = (float *)(q + vec), *ri = (float *)(q + 2 * vec),
+          *pi = (float *)(q + 3 * vec), *wi = (float *)(q + 4 * vec);
+
+    CgArgs<float> in;
+    in.A = *A_lo;
+    in.b = r32;
+    in.x = d32;
+    in.r = ri;
+    in.p = pi;
+    in.w = wi;
+    in.part = cg_part;
+    in.ctrl = ctrl;
+    in.tol2 = inner_tol * inner_tol;
+    in.maxit = max_inner;
+    in.x0_zero = 1;
+    in.timeout_ns = (long long)((timeout_s > 0.0 ? timeout_s : 2.0) * 1e9);
+    in.stall_barrier = -1;
+    in.x64 = d_x;
+
+    int outer = 0, inner_total = 0, status = FE_ERR_MAXIT;
+    double relres = 0.0, bnorm = 0.0;
+    while (true) {
+        // r = b - A64 x in FP64 (stored in FP32 for the inner solve), ||r||, ||b||
+        int nb = 0;
+        st = dispatch_resid(*A64, d_b, d_x, res_part, r32, &nb, s);
+        if (st != FE_OK) return st;
+        k_resid_final<<<1, 32, 0, s>>>(nb, res_part, res_out);
+        FE_TRY_LAUNCH();
+        double h[2];
+        FE_TRY_CUDA(cudaMemcpyAsync(h, res_out, sizeof(h), cudaMemcpyDeviceToHost, s));
+        FE_TRY_CUDA(cudaStreamSynchronize(s));
+        bnorm = sqrt(h[1]);
+        if (h[1] == 0.0) {  // b = 0: the solution is 0
+            FE_TRY_CUDA(cudaMemsetAsync(d_x, 0, (size_t)A64->n_rows * sizeof(double), s));
+            FE_TRY_CUDA(cudaStreamSynchronize(s));
+            relres = 0.0;
+            status = FE_OK;
+            break;
+        }
+        relres = sqrt(h[0] / h[1]);
+        if (!(relres == relres)) { status = FE_ERR_BREAKDOWN; break; }
+        if (relres <= tol) { status = FE_OK; break; }
+        if (outer >= max_outer) { status = FE_ERR_MAXIT; break; }
+        // inner FP32 CG on A_lo d = r, then x += d (inside the kernel)
+        FE_TRY_CUDA(cudaMemsetAsync(ctrl, 0, sizeof(CgCtrl), s));
+        st = dispatch_cg(in, s);
+        if (st != FE_OK) return st;
+        CgCtrl c;
+        FE_TRY_CUDA(cudaMemcpyAsync(&c, ctrl, sizeof(CgCtrl), cudaMemcpyDeviceToHost, s));
+        FE_TRY_CUDA(cudaStreamSynchronize(s));
+        inner_total += c.iterations;
+        ++outer;
+        if (c.status == FE_ERR_TIMEOUT || c.status == FE_ERR_BREAKDOWN) { status = c.status; break; }
+    }
+    h_result->status = status;
+    h_result->outer_iterations = outer;
+    h_result->inner_iterations = inner_total;
+    h_result->relres = relres;
+    h_result->bnorm = bnorm;
+    return (fe_status)status;
 }
 
 }  // extern "C"

@@ -61,6 +61,12 @@ class fe_cg_result(ctypes.Structure):
                 ("relres", ctypes.c_double), ("bnorm", ctypes.c_double)]
 
 
+class fe_mixed_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("outer_iterations", ctypes.c_int32),
+                ("inner_iterations", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("relres", ctypes.c_double), ("bnorm", ctypes.c_double)]
+
+
 # Exported entry points: name -> (restype, argtypes).  Tests check that the
 # shared library exports exactly these names and that include/fe.h declares them.
 _VP, _I32, _I64, _D, _SZ = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_size_t
@@ -80,6 +86,10 @@ SIGNATURES = {
                            ctypes.POINTER(fe_cg_result), _VP]),
     "fe_true_relres": (_I32, [ctypes.POINTER(fe_matrix), _VP, _VP, _VP, _SZ,
                               ctypes.POINTER(_D), _VP]),
+    "fe_cg_mixed_workspace": (_I32, [ctypes.POINTER(fe_matrix), ctypes.POINTER(_SZ)]),
+    "fe_cg_solve_mixed": (_I32, [ctypes.POINTER(fe_matrix), ctypes.POINTER(fe_matrix), _VP, _VP,
+                                 _D, ctypes.c_int, _D, ctypes.c_int, _D, _VP, _SZ,
+                                 ctypes.POINTER(fe_mixed_result), _VP]),
     "fe_inject_barrier_stall": (_I32, [ctypes.c_int]),
     "fe_last_cuda_error": (ctypes.c_int, []),
     "fe_version": (ctypes.c_char_p, []),
@@ -195,6 +205,24 @@ def fe_cg_solve(A: fe_matrix, b, x, tol, maxit, work, timeout_s=0.0, stream=None
                             ctypes.byref(res), _stream(stream))
     if check and st not in (FE_OK,):
         raise FeError("fe_cg_solve", st)
+    return res
+
+
+def fe_cg_mixed_workspace(A_lo: fe_matrix) -> int:
+    n = ctypes.c_size_t(0)
+    _check("fe_cg_mixed_workspace", load().fe_cg_mixed_workspace(ctypes.byref(A_lo), ctypes.byref(n)))
+    return n.value
+
+
+def fe_cg_solve_mixed(A64: fe_matrix, A_lo: fe_matrix, b, x, tol, max_outer, inner_tol, max_inner,
+                      work, timeout_s=0.0, stream=None, check=True) -> fe_mixed_result:
+    res = fe_mixed_result()
+    st = load().fe_cg_solve_mixed(ctypes.byref(A64), ctypes.byref(A_lo), _ptr(b), _ptr(x),
+                                  float(tol), int(max_outer), float(inner_tol), int(max_inner),
+                                  float(timeout_s), _ptr(work), work.numel() * work.element_size(),
+                                  ctypes.byref(res), _stream(stream))
+    if check and st != FE_OK:
+        raise FeError("fe_cg_solve_mixed", st)
     return res
 
 
@@ -345,6 +373,10 @@ class System:
 
 def cg_workspace(A: DeviceMatrix, device="cuda") -> torch.Tensor:
     return _alloc_bytes(fe_cg_workspace(A.desc), device)
+
+
+def mixed_workspace(A_lo: DeviceMatrix, device="cuda") -> torch.Tensor:
+    return _alloc_bytes(fe_cg_mixed_workspace(A_lo.desc), device)
 
 
 def resid_workspace(device="cuda") -> torch.Tensor:
