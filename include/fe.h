@@ -238,6 +238,29 @@ fe_status fe_cg_solve_mixed(const fe_matrix *A64, const fe_matrix *A_lo, const d
                             int max_inner, double timeout_s, void *d_work, size_t work_bytes,
                             fe_mixed_result *h_result, fe_stream_t stream);
 
+/*
+ * fe_cg_solve without a workspace argument, for callers that cannot allocate
+ * device memory when they solve (a latency-critical loop where cudaMalloc's
+ * implicit device synchronisation is unacceptable, or a plugin whose host
+ * framework owns all device memory).  The paper has no counterpart: this is
+ * a packaging variant of the same solve.
+ *   The solver's scratch comes from a fixed array inside the library (about
+ *   6.4 MB, held on every GPU that loads the library until the process
+ *   exits), so A may have at most FE_NOALLOC_MAX_ROWS rows (32 * n_slices <=
+ *   FE_NOALLOC_MAX_ROWS, e.g. meshes up to 63 x 63 x 63 elements); larger A
+ *   returns FE_ERR_WORKSPACE before anything is enqueued.
+ *   The first call on a device looks up that array's device address (with the
+ *   device current); make that first call before any stream capture.
+ *   All calls share the one array: calls whose work overlaps on the GPU (two
+ *   streams, two host threads) race and give undefined results; serialise
+ *   them.  Each call re-initialises the part that must start at zero.
+ *   Arguments, results and synchronisation are those of fe_cg_solve.
+ */
+#define FE_NOALLOC_MAX_ROWS 262144
+fe_status fe_cg_solve_noalloc(const fe_matrix *A, const double *d_b, double *d_x, double tol,
+                              int maxit, double timeout_s, fe_cg_result *h_result,
+                              fe_stream_t stream);
+
 /* Fault injection for tests of the barrier time limit: the next fe_cg_solve
  * on the calling thread has block 0 skip its arrival at grid barrier number
  * barrier_index (0 = the barrier after the initial residual), so every

@@ -22,6 +22,8 @@
 // wait and leave too, and the host reports FE_ERR_TIMEOUT.  Nothing traps.
 #include <math.h>
 
+#include <mutex>
+
 #include "fe_common.cuh"
 
 namespace fe {
@@ -580,6 +582,65 @@ fe_status fe_cg_solve_mixed(const fe_matrix *A64, const fe_matrix *A_lo, const d
     h_result->relres = relres;
     h_result->bnorm = bnorm;
     return (fe_status)status;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- solve without allocation
+//
+// fe_cg_solve_noalloc serves callers that cannot allocate device memory when
+// they solve: code inside a latency-critical loop, where cudaMalloc's implicit
+// device-wide synchronisation is not acceptable, or a plugin whose host
+// framework owns every device buffer and forbids driver allocations.  They
+// still pass A, b and x; the solver's own scratch (barrier/result block,
+// reduction partials and the r, p, w vectors) lives in the file-scope array
+// below, which every GPU that loads this library holds until the process
+// exits.  Host code cannot use the array's name as a device address, so the
+// first call on each device looks the address up with cudaGetSymbolAddress
+// (with that device current) and caches it.
+
+namespace fe {
+
+constexpr size_t kNoallocVecBytes = ((size_t)FE_NOALLOC_MAX_ROWS * sizeof(double) + 255) & ~(size_t)255;
+constexpr size_t kNoallocBytes =
+    256 + ((2 * 2 * (size_t)kCgMaxBlocks * sizeof(double) + 255) & ~(size_t)255) + 3 * kNoallocVecBytes;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
+
+static std::mutex g_noalloc_mu;
+static void *g_noalloc_addr[64];
+
+// Device address of g_noalloc_scratch on the current device (looked up once).
+static fe_status noalloc_scratch(void **out) {
+    int dev = 0;
+    FE_TRY_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return FE_ERR_ARG;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (g_noalloc_addr[dev] == nullptr) {
+        void *p = nullptr;
+        FE_TRY_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return FE_OK;
+}
+
+}  // namespace fe
+
+extern "C" {
+
+fe_status fe_cg_solve_noalloc(const fe_matrix *A, const double *d_b, double *d_x, double tol,
+                              int maxit, double timeout_s, fe_cg_result *h_result,
+                              fe_stream_t stream) {
+    fe_status st = check_matrix(A);
+    if (st != FE_OK) return st;
+    if (A->n_slices * (int64_t)kSlice > (int64_t)FE_NOALLOC_MAX_ROWS) return FE_ERR_WORKSPACE;
+    const size_t need = cg_workspace_bytes(*A);
+    if (need > kNoallocBytes) return FE_ERR_WORKSPACE;
+    void *ws = nullptr;
+    st = noalloc_scratch(&ws);
+    if (st != FE_OK) return st;
+    return fe_cg_solve(A, d_b, d_x, tol, maxit, timeout_s, ws, need, h_result, stream);
 }
 
 }  // extern "C"

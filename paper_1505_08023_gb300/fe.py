@@ -90,6 +90,8 @@ SIGNATURES = {
     "fe_cg_solve_mixed": (_I32, [ctypes.POINTER(fe_matrix), ctypes.POINTER(fe_matrix), _VP, _VP,
                                  _D, ctypes.c_int, _D, ctypes.c_int, _D, _VP, _SZ,
                                  ctypes.POINTER(fe_mixed_result), _VP]),
+    "fe_cg_solve_noalloc": (_I32, [ctypes.POINTER(fe_matrix), _VP, _VP, _D, ctypes.c_int, _D,
+                                   ctypes.POINTER(fe_cg_result), _VP]),
     "fe_inject_barrier_stall": (_I32, [ctypes.c_int]),
     "fe_last_cuda_error": (ctypes.c_int, []),
     "fe_version": (ctypes.c_char_p, []),
@@ -223,6 +225,20 @@ def fe_cg_solve_mixed(A64: fe_matrix, A_lo: fe_matrix, b, x, tol, max_outer, inn
                                   ctypes.byref(res), _stream(stream))
     if check and st != FE_OK:
         raise FeError("fe_cg_solve_mixed", st)
+    return res
+
+
+NOALLOC_MAX_ROWS = 262144
+
+
+def fe_cg_solve_noalloc(A: fe_matrix, b, x, tol, maxit, timeout_s=0.0, stream=None,
+                        check=True) -> fe_cg_result:
+    """fe_cg_solve with the library's built-in scratch (no workspace argument)."""
+    res = fe_cg_result()
+    st = load().fe_cg_solve_noalloc(ctypes.byref(A), _ptr(b), _ptr(x), float(tol), int(maxit),
+                                    float(timeout_s), ctypes.byref(res), _stream(stream))
+    if check and st != FE_OK:
+        raise FeError("fe_cg_solve_noalloc", st)
     return res
 
 
