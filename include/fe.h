@@ -194,7 +194,7 @@ fe_status fe_cg_workspace(const fe_matrix *A, size_t *h_bytes);
  * products are reduced in a fixed order, so a rerun gives identical bits.
  *   Stop when ||r_k|| <= tol ||b|| (checked before the first step and after
  *   each update) or after maxit steps; b = 0 returns x = 0.
- *   d_x[m]: start vector in, iterate out.  d_work: fe_cg_workspace() bytes,
+ *   d_x[m]: start vector in, iterate out (d_b, d_x 16-byte aligned).  d_work: fe_cg_workspace() bytes,
  *   256-byte aligned, scratch.  timeout_s: limit on any one grid-barrier
  *   wait (<= 0: 2 s); past it every block exits and the status is
  *   FE_ERR_TIMEOUT.

@@ -31,6 +31,7 @@ namespace fe {
 constexpr int kCgWarps = 8;
 constexpr int kCgThreads = kCgWarps * 32;
 constexpr int kCgMaxBlocks = 4096;
+constexpr int kCgBlocksPerSm = 3;
 constexpr unsigned kMaxPolls = 1u << 28;
 
 struct CgCtrl {
@@ -138,8 +139,90 @@ __device__ __forceinline__ bool grid_sum2(const CgArgs<XT> &a, double v0, double
     return true;
 }
 
+// 16-byte packs of the vector phases: the streaming passes (x, r update and
+// p update) are bracketed by grid barriers, so they need not follow the
+// SpMV's slice ownership; each thread moves two 16-byte packs per array per
+// trip, which keeps enough bytes in flight to stream at HBM rate.
+template <class XT> struct Pack16;
+template <> struct Pack16<double> { using T = double2; static constexpr int N = 2; };
+template <> struct Pack16<float> { using T = float4; static constexpr int N = 4; };
+
+template <class XT> __device__ __forceinline__ XT &lane_of(typename Pack16<XT>::T &v, int i) {
+    return reinterpret_cast<XT *>(&v)[i];
+}
+
+// B: x += alpha p, r -= alpha w; returns this thread's partial of r.r
+template <class XT>
+__device__ __forceinline__ XT update_xr(XT *__restrict__ x, XT *__restrict__ r,
+                                        const XT *__restrict__ p, const XT *__restrict__ w,
+                                        int64_t m, XT alpha) {
+    using P = typename Pack16<XT>::T;
+    constexpr int V = Pack16<XT>::N;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+    const int64_t npk = m / V;
+    P *x4 = reinterpret_cast<P *>(x), *r4 = reinterpret_cast<P *>(r);
+    const P *p4 = reinterpret_cast<const P *>(p), *w4 = reinterpret_cast<const P *>(w);
+    XT acc = XT(0);
+    for (int64_t q = tid; q < npk; q += 2 * nth) {
+        const int64_t q1 = q + nth;
+        const bool two = q1 < npk;
+        P xv[2], rv[2], pv[2], wv[2];
+        xv[0] = x4[q]; rv[0] = r4[q]; pv[0] = p4[q]; wv[0] = w4[q];
+        if (two) { xv[1] = x4[q1]; rv[1] = r4[q1]; pv[1] = p4[q1]; wv[1] = w4[q1]; }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            if (u == 1 && !two) break;
+#pragma unroll
+            for (int i = 0; i < V; ++i) {
+                lane_of<XT>(xv[u], i) = fma(alpha, lane_of<XT>(pv[u], i), lane_of<XT>(xv[u], i));
+                const XT ri = fma(-alpha, lane_of<XT>(wv[u], i), lane_of<XT>(rv[u], i));
+                lane_of<XT>(rv[u], i) = ri;
+                acc = fma(ri, ri, acc);
+            }
+        }
+        x4[q] = xv[0]; r4[q] = rv[0];
+        if (two) { x4[q1] = xv[1]; r4[q1] = rv[1]; }
+    }
+    for (int64_t row = npk * V + tid; row < m; row += nth) {
+        x[row] = fma(alpha, p[row], x[row]);
+        const XT ri = fma(-alpha, w[row], r[row]);
+        r[row] = ri;
+        acc = fma(ri, ri, acc);
+    }
+    return acc;
+}
+
+// C: p = r + beta p
+template <class XT>
+__device__ __forceinline__ void update_p(XT *__restrict__ p, const XT *__restrict__ r, int64_t m,
+                                         XT beta) {
+    using P = typename Pack16<XT>::T;
+    constexpr int V = Pack16<XT>::N;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+    const int64_t npk = m / V;
+    P *p4 = reinterpret_cast<P *>(p);
+    const P *r4 = reinterpret_cast<const P *>(r);
+    for (int64_t q = tid; q < npk; q += 2 * nth) {
+        const int64_t q1 = q + nth;
+        const bool two = q1 < npk;
+        P pv[2], rv[2];
+        pv[0] = p4[q]; rv[0] = r4[q];
+        if (two) { pv[1] = p4[q1]; rv[1] = r4[q1]; }
+#pragma unroll
+        for (int i = 0; i < V; ++i) {
+            lane_of<XT>(pv[0], i) = fma(beta, lane_of<XT>(pv[0], i), lane_of<XT>(rv[0], i));
+            lane_of<XT>(pv[1], i) = fma(beta, lane_of<XT>(pv[1], i), lane_of<XT>(rv[1], i));
+        }
+        p4[q] = pv[0];
+        if (two) p4[q1] = pv[1];
+    }
+    for (int64_t row = npk * V + tid; row < m; row += nth) p[row] = fma(beta, p[row], r[row]);
+}
+
 template <int FMT, class VT, class XT>
-__global__ void __launch_bounds__(kCgThreads, 2) k_cg(const CgArgs<XT> a) {
+__global__ void __launch_bounds__(kCgThreads, kCgBlocksPerSm) k_cg(const CgArgs<XT> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[kCgWarps][2];
     __shared__ int s_ok;
@@ -202,17 +285,7 @@ __global__ void __launch_bounds__(kCgThreads, 2) k_cg(const CgArgs<XT> a) {
             const double alpha = rr / pw;
             const XT alpha_x = (XT)alpha;
             // B: x += alpha p, r -= alpha w, r.r
-            XT rr_part = XT(0);
-            for (int64_t s = gw; s < ns; s += tw) {
-                const int64_t row = s * kSlice + lane;
-                if (row < m) {
-                    const XT pi = a.p[row], wi = a.w[row];
-                    a.x[row] = fma(alpha_x, pi, a.x[row]);
-                    const XT ri = fma(-alpha_x, wi, a.r[row]);
-                    a.r[row] = ri;
-                    rr_part = fma(ri, ri, rr_part);
-                }
-            }
+            const XT rr_part = update_xr<XT>(a.x, a.r, a.p, a.w, m, alpha_x);
             double rr_new;
             if (!(alive = grid_sum2(a, (double)rr_part, 0.0, rr_new, unused, round, target, red, &s_ok))) break;
             const double beta = rr_new / rr;
@@ -221,11 +294,7 @@ __global__ void __launch_bounds__(kCgThreads, 2) k_cg(const CgArgs<XT> a) {
             if (rr <= a.tol2 * bb) { status = FE_OK; break; }
             if (k >= a.maxit) { status = FE_ERR_MAXIT; break; }
             // C: p = r + beta p
-            const XT beta_x = (XT)beta;
-            for (int64_t s = gw; s < ns; s += tw) {
-                const int64_t row = s * kSlice + lane;
-                if (row < m) a.p[row] = fma(beta_x, a.p[row], a.r[row]);
-            }
+            update_p<XT>(a.p, a.r, m, (XT)beta);
             if (!(alive = grid_barrier(a.ctrl, target, a.timeout_ns, a.stall_barrier, &s_ok))) break;
         }
     }
@@ -413,7 +482,7 @@ fe_status fe_cg_solve(const fe_matrix *A, const double *d_b, double *d_x, double
     if (st != FE_OK) return st;
     if (!d_b || !d_x || !d_work || !h_result || maxit < 0 || !(tol >= 0.0)) return FE_ERR_ARG;
     if (A->n_rows != A->n_cols) return FE_ERR_ARG;
-    if (!aligned(d_b, 8) || !aligned(d_x, 8) || !aligned(d_work, 256)) return FE_ERR_ARG;
+    if (!aligned(d_b, 16) || !aligned(d_x, 16) || !aligned(d_work, 256)) return FE_ERR_ARG;
     if (work_bytes < cg_workspace_bytes(*A)) return FE_ERR_WORKSPACE;
     cudaStream_t s = (cudaStream_t)stream;
 
