@@ -31,7 +31,7 @@ namespace fe {
 constexpr int kCgWarps = 8;
 constexpr int kCgThreads = kCgWarps * 32;
 constexpr int kCgMaxBlocks = 4096;
-constexpr int kCgBlocksPerSm = 3;
+constexpr int kCgBlocksPerSm = 4;
 constexpr unsigned kMaxPolls = 1u << 28;
 
 struct CgCtrl {
@@ -72,15 +72,26 @@ __device__ __forceinline__ void red_release_add(unsigned long long *p, unsigned 
     asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
+// State every thread of a block shares (identical in all of them): kept in
+// shared memory so that the SpMV phase has the registers to itself.
+struct CgBlockState {
+    unsigned long long target;  // barrier arrivals this block waits for
+    double rr, bb;              // r.r of the current step, b.b
+    double red[kCgWarps][2];    // per-warp partials of the block reduction
+    int round;                  // reductions done (selects the partial buffer)
+    int k;                      // CG steps done
+    int ok;                     // 0 once a barrier wait gave up
+};
+
 // Grid barrier with a bounded wait.  Returns true (uniformly in the block) if
 // all blocks arrived and nobody aborted.
-__device__ __forceinline__ bool grid_barrier(CgCtrl *ctrl, unsigned long long &target,
-                                             long long timeout_ns, long long stall_barrier,
-                                             int *s_ok) {
+__device__ __forceinline__ bool grid_barrier(CgCtrl *ctrl, CgBlockState *st, long long timeout_ns,
+                                             long long stall_barrier) {
     __syncthreads();
-    const long long index = (long long)(target / gridDim.x);  // barriers passed so far
-    target += gridDim.x;
     if (threadIdx.x == 0) {
+        const long long index = (long long)(st->target / gridDim.x);  // barriers passed so far
+        const unsigned long long target = st->target + gridDim.x;
+        st->target = target;
         int ok = 1;
         if (!(blockIdx.x == 0 && index == stall_barrier)) red_release_add(&ctrl->bar, 1ull);
         const long long t0 = global_ns();
@@ -97,37 +108,36 @@ __device__ __forceinline__ bool grid_barrier(CgCtrl *ctrl, unsigned long long &t
         }
         if (ok && *(volatile int *)&ctrl->abort) ok = 0;
         __threadfence();
-        *s_ok = ok;
+        st->ok = ok;
     }
     __syncthreads();
-    return *s_ok != 0;
+    return st->ok != 0;
 }
 
 // Sum (v0, v1) over the whole grid; see the file comment for the order.
 template <class XT>
-__device__ __forceinline__ bool grid_sum2(const CgArgs<XT> &a, double v0, double v1, double &o0,
-                                          double &o1, int &round, unsigned long long &target,
-                                          double (*red)[2], int *s_ok) {
+__device__ __forceinline__ bool grid_sum2(const CgArgs<XT> &a, CgBlockState *st, double v0,
+                                          double v1, double &o0, double &o1) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     v0 = warp_sum(v0);
     v1 = warp_sum(v1);
     if (lane == 0) {
-        red[warp][0] = v0;
-        red[warp][1] = v1;
+        st->red[warp][0] = v0;
+        st->red[warp][1] = v1;
     }
     __syncthreads();
-    double *part = a.part + (size_t)(round & 1) * 2 * kCgMaxBlocks;
+    double *part = a.part + (size_t)(st->round & 1) * 2 * kCgMaxBlocks;
     if (threadIdx.x == 0) {
         double t0 = 0.0, t1 = 0.0;
 #pragma unroll
         for (int k = 0; k < kCgWarps; ++k) {
-            t0 += red[k][0];
-            t1 += red[k][1];
+            t0 += st->red[k][0];
+            t1 += st->red[k][1];
         }
         __stcg(part + 2 * blockIdx.x, t0);
         __stcg(part + 2 * blockIdx.x + 1, t1);
     }
-    if (!grid_barrier(a.ctrl, target, a.timeout_ns, a.stall_barrier, s_ok)) return false;
+    if (!grid_barrier(a.ctrl, st, a.timeout_ns, a.stall_barrier)) return false;
     double t0 = 0.0, t1 = 0.0;
     for (unsigned i = lane; i < gridDim.x; i += 32) {
         t0 += __ldcg(part + 2 * i);
@@ -135,7 +145,8 @@ __device__ __forceinline__ bool grid_sum2(const CgArgs<XT> &a, double v0, double
     }
     o0 = warp_sum(t0);
     o1 = warp_sum(t1);
-    ++round;
+    __syncthreads();                       // every warp has read st->round
+    if (threadIdx.x == 0) st->round += 1;
     return true;
 }
 
@@ -224,28 +235,30 @@ __device__ __forceinline__ void update_p(XT *__restrict__ p, const XT *__restric
 template <int FMT, class VT, class XT>
 __global__ void __launch_bounds__(kCgThreads, kCgBlocksPerSm) k_cg(const CgArgs<XT> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double red[kCgWarps][2];
-    __shared__ int s_ok;
+    __shared__ CgBlockState st;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     XT *sv = reinterpret_cast<XT *>(smem_raw) + (size_t)warp * 2 * kCsrStage;
     XT *sx = sv + kCsrStage;
-    const int64_t m = a.A.n_rows, ns = a.A.n_slices;
-    const int64_t gw = (int64_t)blockIdx.x * kCgWarps + warp;
-    const int64_t tw = (int64_t)gridDim.x * kCgWarps;
-    unsigned long long target = 0;
-    int round = 0;
+    // rows fit int32 (check_matrix); slices are walked in a grid-stride order
+    const int m = (int)a.A.n_rows, ns = (int)a.A.n_slices;
+    const int tw = gridDim.x * kCgWarps;
+    if (threadIdx.x == 0) {
+        st.target = 0;
+        st.round = 0;
+        st.k = 0;
+        st.ok = 1;
+    }
+    __syncthreads();
     int status = FE_ERR_MAXIT;
-    int k = 0;
-    double rr = 0.0, bb = 0.0;
     bool alive = true;
 
     // r = b - A x, p = r; r.r and b.b
     {
         XT s0 = XT(0), s1 = XT(0);
-        for (int64_t s = gw; s < ns; s += tw) {
+        for (int s = blockIdx.x * kCgWarps + warp; s < ns; s += tw) {
             XT ax = XT(0);
             if (!a.x0_zero) ax = slice_spmv<FMT, VT, XT, XT, false>(a.A, s, lane, a.x, sv, sx);
-            const int64_t row = s * kSlice + lane;
+            const int row = s * kSlice + lane;
             if (row < m) {
                 const XT bi = a.b[row];
                 const XT ri = bi - ax;
@@ -256,60 +269,66 @@ __global__ void __launch_bounds__(kCgThreads, kCgBlocksPerSm) k_cg(const CgArgs<
                 s1 = fma(bi, bi, s1);
             }
         }
-        alive = grid_sum2(a, (double)s0, (double)s1, rr, bb, round, target, red, &s_ok);
+        double rr0, bb0;
+        alive = grid_sum2(a, &st, (double)s0, (double)s1, rr0, bb0);
+        if (threadIdx.x == 0) {
+            st.rr = rr0;
+            st.bb = bb0;
+        }
+        __syncthreads();
     }
-    if (alive && bb == 0.0) {  // b = 0: the solution is 0
-        for (int64_t s = gw; s < ns; s += tw) {
-            const int64_t row = s * kSlice + lane;
+    if (alive && st.bb == 0.0) {  // b = 0: the solution is 0
+        for (int s = blockIdx.x * kCgWarps + warp; s < ns; s += tw) {
+            const int row = s * kSlice + lane;
             if (row < m) a.x[row] = XT(0);
         }
-        rr = 0.0;
+        if (threadIdx.x == 0) st.rr = 0.0;
         status = FE_OK;
     } else {
         while (alive) {
-            if (rr <= a.tol2 * bb) { status = FE_OK; break; }
-            if (k >= a.maxit) { status = FE_ERR_MAXIT; break; }
+            if (st.rr <= a.tol2 * st.bb) { status = FE_OK; break; }
+            if (st.k >= a.maxit) { status = FE_ERR_MAXIT; break; }
             // A: w = A p, p.w
             XT pw_part = XT(0);
-            for (int64_t s = gw; s < ns; s += tw) {
+            for (int s = blockIdx.x * kCgWarps + warp; s < ns; s += tw) {
                 const XT y = slice_spmv<FMT, VT, XT, XT, false>(a.A, s, lane, a.p, sv, sx);
-                const int64_t row = s * kSlice + lane;
+                const int row = s * kSlice + lane;
                 if (row < m) {
                     a.w[row] = y;
                     pw_part = fma(a.p[row], y, pw_part);
                 }
             }
             double pw, unused;
-            if (!(alive = grid_sum2(a, (double)pw_part, 0.0, pw, unused, round, target, red, &s_ok))) break;
+            if (!(alive = grid_sum2(a, &st, (double)pw_part, 0.0, pw, unused))) break;
             if (!(pw > 0.0) || !(pw < INFINITY)) { status = FE_ERR_BREAKDOWN; break; }
-            const double alpha = rr / pw;
-            const XT alpha_x = (XT)alpha;
             // B: x += alpha p, r -= alpha w, r.r
-            const XT rr_part = update_xr<XT>(a.x, a.r, a.p, a.w, m, alpha_x);
+            const XT rr_part = update_xr<XT>(a.x, a.r, a.p, a.w, m, (XT)(st.rr / pw));
             double rr_new;
-            if (!(alive = grid_sum2(a, (double)rr_part, 0.0, rr_new, unused, round, target, red, &s_ok))) break;
-            const double beta = rr_new / rr;
-            rr = rr_new;
-            ++k;
-            if (rr <= a.tol2 * bb) { status = FE_OK; break; }
-            if (k >= a.maxit) { status = FE_ERR_MAXIT; break; }
+            if (!(alive = grid_sum2(a, &st, (double)rr_part, 0.0, rr_new, unused))) break;
+            const double beta = rr_new / st.rr;
+            __syncthreads();                 // every thread has read st.rr
+            if (threadIdx.x == 0) {
+                st.rr = rr_new;
+                st.k += 1;
+            }
+            __syncthreads();
+            if (rr_new <= a.tol2 * st.bb) { status = FE_OK; break; }
+            if (st.k >= a.maxit) { status = FE_ERR_MAXIT; break; }
             // C: p = r + beta p
             update_p<XT>(a.p, a.r, m, (XT)beta);
-            if (!(alive = grid_barrier(a.ctrl, target, a.timeout_ns, a.stall_barrier, &s_ok))) break;
+            if (!(alive = grid_barrier(a.ctrl, &st, a.timeout_ns, a.stall_barrier))) break;
         }
     }
-    // refinement step of the mixed-precision form: x64 += x (own rows only)
+    // refinement step of the mixed-precision form: x64 += x
     if (a.x64 != nullptr && alive && (status == FE_OK || status == FE_ERR_MAXIT)) {
-        for (int64_t s = gw; s < ns; s += tw) {
-            const int64_t row = s * kSlice + lane;
-            if (row < m) a.x64[row] += (double)a.x[row];
-        }
+        const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+        for (int row = tid; row < m; row += nth) a.x64[row] += (double)a.x[row];
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         a.ctrl->status = alive ? status : FE_ERR_TIMEOUT;
-        a.ctrl->iterations = k;
-        a.ctrl->rr = rr;
-        a.ctrl->bb = bb;
+        a.ctrl->iterations = st.k;
+        a.ctrl->rr = st.rr;
+        a.ctrl->bb = st.bb;
     }
 }
 

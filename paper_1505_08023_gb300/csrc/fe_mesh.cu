@@ -31,7 +31,7 @@ fe_status check_matrix(const fe_matrix *A) {
         return FE_ERR_ARG;
     if (A->value_type < FE_VAL_F64 || A->value_type > FE_VAL_BF16) return FE_ERR_ARG;
     if (A->n_slices != (A->n_rows + kSlice - 1) / kSlice) return FE_ERR_ARG;
-    if (A->n_cols > INT32_MAX || A->n_rows > INT32_MAX) return FE_ERR_OVERFLOW;
+    if (A->n_cols > INT32_MAX - 64 || A->n_rows > INT32_MAX - 64) return FE_ERR_OVERFLOW;
     switch (A->format) {
         case FE_FMT_CSR:
             if (A->d_row_ptr == nullptr || A->n_stored > INT32_MAX) return FE_ERR_ARG;
