@@ -215,26 +215,41 @@ typedef struct fe_mixed_result {
 } fe_mixed_result;
 
 /* Workspace of fe_cg_solve_mixed for the low-precision matrix A_lo: five FP32
- * vectors of 32 * n_slices entries plus reduction blocks. */
+ * vectors of 32 * n_slices entries plus reduction blocks (either mode). */
 fe_status fe_cg_mixed_workspace(const fe_matrix *A_lo, size_t *h_bytes);
+
+/* Modes of the mixed-precision solve. */
+typedef enum fe_mixed_mode {
+    FE_MIXED_RELIABLE = 0,  /* one persistent kernel, refinement steps keep the search direction */
+    FE_MIXED_RESTART = 1    /* host loop of restarted inner solves */
+} fe_mixed_mode;
 
 /*
  * Mixed-precision form of the solve (not in the paper; the FP64 path is its
- * judge): iterative refinement around an FP32 inner CG.
- *   repeat: r = b - A64 x       (FP64 matrix, FP64 accumulation, FP64 ||r||)
- *           stop if ||r|| <= tol ||b|| or after max_outer inner solves
- *           solve A_lo d = r    (the persistent CG kernel with FP32 vectors and
- *                                FP32 accumulation; dot products reduced over
- *                                the grid in FP64) to ||r_in|| <= inner_tol ||r||
- *                                or max_inner steps
- *           x += d              (FP64)
- *   A64: value_type FE_VAL_F64, any format; A_lo: the same matrix with FP32 or
- *   BF16 (or FP64) values, any format.  The stopping test uses the true FP64
- *   residual.  d_x: start in, solution out.  d_work: fe_cg_mixed_workspace()
- *   bytes, 256-byte aligned.  Synchronises `stream` once per outer step.
+ * judge).  A_lo holds the matrix values in FP32 or BF16 (any format); the
+ * Krylov iteration runs in FP32 with FP32 accumulation on A_lo; the residual
+ * recompute r = b - A64 x (A64: FP64 values, any format), the refinement
+ * update x += d and every global dot product are FP64.  The stopping test is
+ * the true FP64 residual: ||b - A64 x|| <= tol ||b||.
+ *
+ *   FE_MIXED_RELIABLE: one persistent cooperative kernel.  The FP32 CG
+ *     accumulates a correction d; each time its residual has fallen by the
+ *     factor inner_tol since the last refinement step (or meets tol), the
+ *     kernel sets x += d (FP64), recomputes r = b - A64 x (FP64) as the FP32
+ *     residual and continues with the same search direction.  max_outer caps
+ *     the refinement steps, max_inner the FP32 CG steps.  A_lo must not be FP64.
+ *   FE_MIXED_RESTART: repeat { r = b - A64 x; solve A_lo d = r by the FP32
+ *     persistent CG from d = 0 to ||r_in|| <= inner_tol ||r|| or max_inner
+ *     steps; x += d } at most max_outer times.
+ *
+ *   d_b, d_x (16-byte aligned): right-hand side; start in, solution out.
+ *   d_work: fe_cg_mixed_workspace() bytes, 256-byte aligned.  Synchronises
+ *   `stream` (once per solve in RELIABLE mode, once per step in RESTART).
+ *   h_result->outer_iterations counts refinement steps, inner_iterations the
+ *   FP32 CG steps, relres is the last FP64 true residual.
  */
 fe_status fe_cg_solve_mixed(const fe_matrix *A64, const fe_matrix *A_lo, const double *d_b,
-                            double *d_x, double tol, int max_outer, double inner_tol,
+                            double *d_x, double tol, int mode, int max_outer, double inner_tol,
                             int max_inner, double timeout_s, void *d_work, size_t work_bytes,
                             fe_mixed_result *h_result, fe_stream_t stream);
 

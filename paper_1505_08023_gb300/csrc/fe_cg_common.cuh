@@ -1,0 +1,323 @@
+// fe_cg_common.cuh -- pieces shared by the persistent CG kernels: the bounded
+// grid barrier, the fixed-order grid reduction, the 16-byte streaming vector
+// updates, and the residual kernels.
+#pragma once
+
+#include <math.h>
+
+#include "fe_common.cuh"
+
+namespace fe {
+
+constexpr int kCgWarps = 8;
+constexpr int kCgThreads = kCgWarps * 32;
+constexpr int kCgMaxBlocks = 4096;
+constexpr int kCgBlocksPerSm = 4;
+constexpr unsigned kMaxPolls = 1u << 28;
+
+struct CgCtrl {
+    unsigned long long bar;  // barrier arrivals
+    int abort;               // set by a block whose wait timed out
+    int status;              // fe_status of the solve
+    int iterations;
+    int pad;
+    double rr;
+    double bb;
+};
+
+template <class XT> struct CgArgs {
+    fe_matrix A;
+    const XT *b;
+    XT *x, *r, *p, *w;
+    double *part;            // [2][2 * kCgMaxBlocks]
+    CgCtrl *ctrl;
+    double tol2;
+    int maxit;
+    int x0_zero;             // start from x = 0 without reading x (skips one SpMV)
+    long long timeout_ns;
+    long long stall_barrier;  // fault injection: block 0 skips this arrival (-1: none)
+    double *x64;             // if set: x64 += x on exit (mixed-precision refinement step)
+};
+
+__device__ __forceinline__ long long global_ns() {
+    long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void red_release_add(unsigned long long *p, unsigned long long v) {
+    asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// State every thread of a block shares (identical in all of them): kept in
+// shared memory so that the SpMV phase has the registers to itself.
+struct CgBlockState {
+    unsigned long long target;  // barrier arrivals this block waits for
+    double rr, bb;              // r.r of the current step, b.b
+    double red[kCgWarps][2];    // per-warp partials of the block reduction
+    int round;                  // reductions done (selects the partial buffer)
+    int k;                      // CG steps done
+    int ok;                     // 0 once a barrier wait gave up
+};
+
+// Grid barrier with a bounded wait.  Returns true (uniformly in the block) if
+// all blocks arrived and nobody aborted.
+__device__ __forceinline__ bool grid_barrier(CgCtrl *ctrl, CgBlockState *st, long long timeout_ns,
+                                             long long stall_barrier) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const long long index = (long long)(st->target / gridDim.x);  // barriers passed so far
+        const unsigned long long target = st->target + gridDim.x;
+        st->target = target;
+        int ok = 1;
+        if (!(blockIdx.x == 0 && index == stall_barrier)) red_release_add(&ctrl->bar, 1ull);
+        const long long t0 = global_ns();
+        unsigned polls = 0;
+        while (ld_acquire(&ctrl->bar) < target) {
+            if (*(volatile int *)&ctrl->abort) { ok = 0; break; }
+            if (((++polls) & 7u) == 0 &&
+                (global_ns() - t0 > timeout_ns || polls > kMaxPolls)) {
+                atomicExch(&ctrl->abort, 1);
+                ok = 0;
+                break;
+            }
+            __nanosleep(32);
+        }
+        if (ok && *(volatile int *)&ctrl->abort) ok = 0;
+        __threadfence();
+        st->ok = ok;
+    }
+    __syncthreads();
+    return st->ok != 0;
+}
+
+// Sum (v0, v1) over the whole grid (warp butterfly, fixed warp order, one
+// partial per block, then every warp sums the partials in block order).
+// `a` is any argument block with part, ctrl, timeout_ns and stall_barrier.
+template <class Args>
+__device__ __forceinline__ bool grid_sum2(const Args &a, CgBlockState *st, double v0,
+                                          double v1, double &o0, double &o1) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    v0 = warp_sum(v0);
+    v1 = warp_sum(v1);
+    if (lane == 0) {
+        st->red[warp][0] = v0;
+        st->red[warp][1] = v1;
+    }
+    __syncthreads();
+    double *part = a.part + (size_t)(st->round & 1) * 2 * kCgMaxBlocks;
+    if (threadIdx.x == 0) {
+        double t0 = 0.0, t1 = 0.0;
+#pragma unroll
+        for (int k = 0; k < kCgWarps; ++k) {
+            t0 += st->red[k][0];
+            t1 += st->red[k][1];
+        }
+        __stcg(part + 2 * blockIdx.x, t0);
+        __stcg(part + 2 * blockIdx.x + 1, t1);
+    }
+    if (!grid_barrier(a.ctrl, st, a.timeout_ns, a.stall_barrier)) return false;
+    double t0 = 0.0, t1 = 0.0;
+    for (unsigned i = lane; i < gridDim.x; i += 32) {
+        t0 += __ldcg(part + 2 * i);
+        t1 += __ldcg(part + 2 * i + 1);
+    }
+    o0 = warp_sum(t0);
+    o1 = warp_sum(t1);
+    __syncthreads();                       // every warp has read st->round
+    if (threadIdx.x == 0) st->round += 1;
+    return true;
+}
+
+// 16-byte packs of the vector phases: the streaming passes (x, r update and
+// p update) are bracketed by grid barriers, so they need not follow the
+// SpMV's slice ownership; each thread moves two 16-byte packs per array per
+// trip, which keeps enough bytes in flight to stream at HBM rate.
+template <class XT> struct Pack16;
+template <> struct Pack16<double> { using T = double2; static constexpr int N = 2; };
+template <> struct Pack16<float> { using T = float4; static constexpr int N = 4; };
+
+template <class XT> __device__ __forceinline__ XT &lane_of(typename Pack16<XT>::T &v, int i) {
+    return reinterpret_cast<XT *>(&v)[i];
+}
+
+// B: x += alpha p, r -= alpha w; returns this thread's partial of r.r
+template <class XT>
+__device__ __forceinline__ XT update_xr(XT *__restrict__ x, XT *__restrict__ r,
+                                        const XT *__restrict__ p, const XT *__restrict__ w,
+                                        int64_t m, XT alpha) {
+    using P = typename Pack16<XT>::T;
+    constexpr int V = Pack16<XT>::N;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+    const int64_t npk = m / V;
+    P *x4 = reinterpret_cast<P *>(x), *r4 = reinterpret_cast<P *>(r);
+    const P *p4 = reinterpret_cast<const P *>(p), *w4 = reinterpret_cast<const P *>(w);
+    XT acc = XT(0);
+    for (int64_t q = tid; q < npk; q += 2 * nth) {
+        const int64_t q1 = q + nth;
+        const bool two = q1 < npk;
+        P xv[2], rv[2], pv[2], wv[2];
+        xv[0] = x4[q]; rv[0] = r4[q]; pv[0] = p4[q]; wv[0] = w4[q];
+        if (two) { xv[1] = x4[q1]; rv[1] = r4[q1]; pv[1] = p4[q1]; wv[1] = w4[q1]; }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            if (u == 1 && !two) break;
+#pragma unroll
+            for (int i = 0; i < V; ++i) {
+                lane_of<XT>(xv[u], i) = fma(alpha, lane_of<XT>(pv[u], i), lane_of<XT>(xv[u], i));
+                const XT ri = fma(-alpha, lane_of<XT>(wv[u], i), lane_of<XT>(rv[u], i));
+                lane_of<XT>(rv[u], i) = ri;
+                acc = fma(ri, ri, acc);
+            }
+        }
+        x4[q] = xv[0]; r4[q] = rv[0];
+        if (two) { x4[q1] = xv[1]; r4[q1] = rv[1]; }
+    }
+    for (int64_t row = npk * V + tid; row < m; row += nth) {
+        x[row] = fma(alpha, p[row], x[row]);
+        const XT ri = fma(-alpha, w[row], r[row]);
+        r[row] = ri;
+        acc = fma(ri, ri, acc);
+    }
+    return acc;
+}
+
+// C: p = r + beta p
+template <class XT>
+__device__ __forceinline__ void update_p(XT *__restrict__ p, const XT *__restrict__ r, int64_t m,
+                                         XT beta) {
+    using P = typename Pack16<XT>::T;
+    constexpr int V = Pack16<XT>::N;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+    const int64_t npk = m / V;
+    P *p4 = reinterpret_cast<P *>(p);
+    const P *r4 = reinterpret_cast<const P *>(r);
+    for (int64_t q = tid; q < npk; q += 2 * nth) {
+        const int64_t q1 = q + nth;
+        const bool two = q1 < npk;
+        P pv[2], rv[2];
+        pv[0] = p4[q]; rv[0] = r4[q];
+        if (two) { pv[1] = p4[q1]; rv[1] = r4[q1]; }
+#pragma unroll
+        for (int i = 0; i < V; ++i) {
+            lane_of<XT>(pv[0], i) = fma(beta, lane_of<XT>(pv[0], i), lane_of<XT>(rv[0], i));
+            lane_of<XT>(pv[1], i) = fma(beta, lane_of<XT>(pv[1], i), lane_of<XT>(rv[1], i));
+        }
+        p4[q] = pv[0];
+        if (two) p4[q1] = pv[1];
+    }
+    for (int64_t row = npk * V + tid; row < m; row += nth) p[row] = fma(beta, p[row], r[row]);
+}
+
+// r = b - A x over the block's slices; r.r and b.b partials per block.
+// With r32 set, also stores r in FP32 (the right-hand side of the inner solve
+// of the mixed-precision form).
+template <int FMT, class VT>
+__global__ void __launch_bounds__(kCgThreads) k_resid(const fe_matrix A, const double *__restrict__ b,
+                                                      const double *__restrict__ x,
+                                                      double *__restrict__ part,
+                                                      float *__restrict__ r32) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[kCgWarps][2];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double *sv = reinterpret_cast<double *>(smem_raw) + (size_t)warp * 2 * kCsrStage;
+    double *sx = sv + kCsrStage;
+    double s0 = 0.0, s1 = 0.0;
+    const int64_t tw = (int64_t)gridDim.x * kCgWarps;
+    for (int64_t s = (int64_t)blockIdx.x * kCgWarps + warp; s < A.n_slices; s += tw) {
+        const double ax = slice_spmv<FMT, VT, double, double, true>(A, s, lane, x, sv, sx);
+        const int64_t row = s * kSlice + lane;
+        if (row < A.n_rows) {
+            const double bi = b[row], ri = bi - ax;
+            if (r32 != nullptr) r32[row] = (float)ri;
+            s0 = fma(ri, ri, s0);
+            s1 = fma(bi, bi, s1);
+        }
+    }
+    s0 = warp_sum(s0);
+    s1 = warp_sum(s1);
+    if (lane == 0) {
+        red[warp][0] = s0;
+        red[warp][1] = s1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t0 = 0.0, t1 = 0.0;
+        for (int k = 0; k < kCgWarps; ++k) {
+            t0 += red[k][0];
+            t1 += red[k][1];
+        }
+        part[2 * blockIdx.x] = t0;
+        part[2 * blockIdx.x + 1] = t1;
+    }
+}
+
+static __global__ void k_resid_final(int nblocks, const double *__restrict__ part, double *__restrict__ out) {
+    const int lane = threadIdx.x;
+    double t0 = 0.0, t1 = 0.0;
+    for (int i = lane; i < nblocks; i += 32) {
+        t0 += part[2 * i];
+        t1 += part[2 * i + 1];
+    }
+    t0 = warp_sum(t0);
+    t1 = warp_sum(t1);
+    if (lane == 0) {
+        out[0] = t0;
+        out[1] = t1;
+    }
+}
+
+static size_t align256(size_t n) { return (n + 255) & ~(size_t)255; }
+
+template <int FMT, class VT>
+static fe_status launch_resid(const fe_matrix &A, const double *b, const double *x, double *part,
+                              float *r32, int *nblocks, cudaStream_t s) {
+    auto kern = k_resid<FMT, VT>;
+    const size_t smem = spmv_smem_bytes<FMT, double>(kCgWarps);
+    if (smem > 48 * 1024)
+        FE_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    FE_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kCgThreads, smem));
+    if (per_sm < 1) per_sm = 1;
+    int64_t blocks = (int64_t)sm_count() * per_sm;
+    const int64_t need = (A.n_slices + kCgWarps - 1) / kCgWarps;
+    if (blocks > need) blocks = need;
+    if (blocks > kCgMaxBlocks) blocks = kCgMaxBlocks;
+    if (blocks < 1) blocks = 1;
+    kern<<<(int)blocks, kCgThreads, smem, s>>>(A, b, x, part, r32);
+    FE_TRY_LAUNCH();
+    *nblocks = (int)blocks;
+    return FE_OK;
+}
+
+#define FE_DISPATCH_FMT_VT(A, FN, ...)                                                     \
+    switch ((A).format * 3 + (A).value_type) {                                             \
+        case FE_FMT_CSR * 3 + FE_VAL_F64: return FN<FE_FMT_CSR, double>(__VA_ARGS__);       \
+        case FE_FMT_CSR * 3 + FE_VAL_F32: return FN<FE_FMT_CSR, float>(__VA_ARGS__);        \
+        case FE_FMT_CSR * 3 + FE_VAL_BF16: return FN<FE_FMT_CSR, __nv_bfloat16>(__VA_ARGS__); \
+        case FE_FMT_SELL * 3 + FE_VAL_F64: return FN<FE_FMT_SELL, double>(__VA_ARGS__);     \
+        case FE_FMT_SELL * 3 + FE_VAL_F32: return FN<FE_FMT_SELL, float>(__VA_ARGS__);      \
+        case FE_FMT_SELL * 3 + FE_VAL_BF16: return FN<FE_FMT_SELL, __nv_bfloat16>(__VA_ARGS__); \
+        case FE_FMT_BCRS3 * 3 + FE_VAL_F64: return FN<FE_FMT_BCRS3, double>(__VA_ARGS__);   \
+        case FE_FMT_BCRS3 * 3 + FE_VAL_F32: return FN<FE_FMT_BCRS3, float>(__VA_ARGS__);    \
+        case FE_FMT_BCRS3 * 3 + FE_VAL_BF16: return FN<FE_FMT_BCRS3, __nv_bfloat16>(__VA_ARGS__); \
+        default: return FE_ERR_ARG;                                                        \
+    }
+
+static inline fe_status dispatch_resid(const fe_matrix &A, const double *b, const double *x, double *part,
+                                float *r32, int *nblocks, cudaStream_t s) {
+    FE_DISPATCH_FMT_VT(A, launch_resid, A, b, x, part, r32, nblocks, s)
+}
+
+
+// Launch of the FP32-vector CG kernel (defined in fe_cg.cu): the inner solver
+// of the restarted mixed-precision mode.
+fe_status launch_cg_f32(const CgArgs<float> &args, cudaStream_t s);
+
+}  // namespace fe

@@ -1,0 +1,389 @@
+// fe_cg_mixed.cu -- mixed-precision form of the CG solve (not in the paper;
+// the FP64 path is its judge): matrix values stored in FP32 or BF16, the
+// Krylov iteration in FP32 with FP32 accumulation, and the residual
+// recompute, the refinement update and every global dot product in FP64.
+//
+// Two modes:
+//   FE_MIXED_RELIABLE (default)  one persistent cooperative kernel.  The FP32
+//       CG accumulates its correction in an FP32 vector; whenever its residual
+//       has dropped by `inner_tol` since the last refinement step (or looks
+//       converged), the kernel adds the correction to the FP64 x, recomputes
+//       r = b - A64 x with the FP64 matrix, stores it as the FP32 residual and
+//       continues with the same search direction ("reliable updates",
+//       Sleijpen & van der Vorst 1996).  The Krylov space is never thrown away,
+//       so the step count stays close to the FP64 solve's.
+//   FE_MIXED_RESTART  a host loop: FP64 residual, FP32 CG from zero to
+//       inner_tol, FP64 update; each inner solve starts a new Krylov space.
+#include "fe_cg_common.cuh"
+
+namespace fe {
+
+static size_t mixed_workspace_bytes(const fe_matrix &lo) {
+    const size_t vec = align256((size_t)lo.n_slices * kSlice * sizeof(float));
+    return 256 + align256(2 * 2 * (size_t)kCgMaxBlocks * sizeof(double)) +
+           align256(FE_RESID_WORK_BYTES) + 5 * vec;
+}
+
+struct MixArgs {
+    fe_matrix A_lo, A_hi;
+    const double *b;
+    double *x;                 // FP64 iterate (caller's)
+    float *r, *p, *w, *xs;     // FP32 residual, direction, A p, correction since the last update
+    double *part;
+    CgCtrl *ctrl;
+    double tol2, delta2;
+    int maxit, max_updates;
+    long long timeout_ns;
+    long long stall_barrier;
+};
+
+// r = b - A_hi x in FP64, stored as FP32 in r (and p when `set_p`); returns
+// this thread's partials of r.r and b.b in FP64.
+template <int FH>
+__device__ __forceinline__ void fp64_residual(const MixArgs &a, int m, int ns, bool set_p,
+                                              double *svd, double *sxd, double &s0, double &s1) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int tw = gridDim.x * kCgWarps;
+    s0 = 0.0;
+    s1 = 0.0;
+    for (int s = blockIdx.x * kCgWarps + warp; s < ns; s += tw) {
+        const double ax = slice_spmv<FH, double, double, double, false>(a.A_hi, s, lane, a.x, svd, sxd);
+        const int row = s * kSlice + lane;
+        if (row < m) {
+            const double bi = a.b[row], ri = bi - ax;
+            a.r[row] = (float)ri;
+            if (set_p) {
+                a.p[row] = (float)ri;
+                a.xs[row] = 0.0f;
+            }
+            s0 = fma(ri, ri, s0);
+            s1 = fma(bi, bi, s1);
+        }
+    }
+}
+
+// x += xs, xs = 0 (the FP64 refinement update)
+__device__ __forceinline__ void fold_correction(double *__restrict__ x, float *__restrict__ xs, int m) {
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+    const int npk = m / 4;
+    float4 *xs4 = reinterpret_cast<float4 *>(xs);
+    double2 *x2 = reinterpret_cast<double2 *>(x);
+    for (int q = tid; q < npk; q += nth) {
+        const float4 c = xs4[q];
+        double2 lo = x2[2 * q], hi = x2[2 * q + 1];
+        lo.x += (double)c.x;
+        lo.y += (double)c.y;
+        hi.x += (double)c.z;
+        hi.y += (double)c.w;
+        x2[2 * q] = lo;
+        x2[2 * q + 1] = hi;
+        xs4[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    for (int row = npk * 4 + tid; row < m; row += nth) {
+        x[row] += (double)xs[row];
+        xs[row] = 0.0f;
+    }
+}
+
+template <int FL, class VL, int FH>
+__global__ void __launch_bounds__(kCgThreads, kCgBlocksPerSm) k_cg_reliable(const MixArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ CgBlockState st;
+    __shared__ double s_rr_max;
+    __shared__ int s_updates;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // CSR staging: the FP64 residual needs double slots, the FP32 SpMV float slots
+    double *svd = reinterpret_cast<double *>(smem_raw) + (size_t)warp * 2 * kCsrStage;
+    double *sxd = svd + kCsrStage;
+    float *svf = reinterpret_cast<float *>(svd);
+    float *sxf = svf + kCsrStage;
+    const int m = (int)a.A_lo.n_rows, ns = (int)a.A_lo.n_slices;
+    const int tw = gridDim.x * kCgWarps;
+    if (threadIdx.x == 0) {
+        st.target = 0;
+        st.round = 0;
+        st.k = 0;
+        st.ok = 1;
+        s_updates = 0;
+    }
+    __syncthreads();
+    int status = FE_ERR_MAXIT;
+    bool alive = true;
+    double s0, s1, rr_true, bb;
+    fp64_residual<FH>(a, m, ns, true, svd, sxd, s0, s1);
+    alive = grid_sum2(a, &st, s0, s1, rr_true, bb);
+    if (threadIdx.x == 0) {
+        st.rr = rr_true;
+        st.bb = bb;
+        s_rr_max = rr_true;
+    }
+    __syncthreads();
+    if (alive && bb == 0.0) {  // b = 0: the solution is 0
+        const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+        for (int row = tid; row < m; row += nth) a.x[row] = 0.0;
+        if (threadIdx.x == 0) st.rr = 0.0;
+        status = FE_OK;
+    } else if (alive && rr_true <= a.tol2 * bb) {
+        status = FE_OK;
+    } else {
+        while (alive) {
+            // A: w = A_lo p (FP32), p.w
+            float pw_part = 0.0f;
+            for (int s = blockIdx.x * kCgWarps + warp; s < ns; s += tw) {
+                const float y = slice_spmv<FL, VL, float, float, false>(a.A_lo, s, lane, a.p, svf, sxf);
+                const int row = s * kSlice + lane;
+                if (row < m) {
+                    a.w[row] = y;
+                    pw_part = fmaf(a.p[row], y, pw_part);
+                }
+            }
+            double pw, unused;
+            if (!(alive = grid_sum2(a, &st, (double)pw_part, 0.0, pw, unused))) break;
+            if (!(pw > 0.0) || !(pw < INFINITY)) { status = FE_ERR_BREAKDOWN; break; }
+            // B: xs += alpha p, r -= alpha w, r.r
+            const float rr_part = update_xr<float>(a.xs, a.r, a.p, a.w, m, (float)(st.rr / pw));
+            double rr_new;
+            if (!(alive = grid_sum2(a, &st, (double)rr_part, 0.0, rr_new, unused))) break;
+            __syncthreads();
+            if (threadIdx.x == 0) st.k += 1;
+            __syncthreads();
+            const bool refine = rr_new <= a.delta2 * s_rr_max || rr_new <= a.tol2 * st.bb ||
+                                st.k >= a.maxit;
+            if (refine) {
+                // x += xs in FP64, then r = b - A64 x in FP64 (stored as the FP32 residual)
+                fold_correction(a.x, a.xs, m);
+                if (!(alive = grid_barrier(a.ctrl, &st, a.timeout_ns, a.stall_barrier))) break;
+                fp64_residual<FH>(a, m, ns, false, svd, sxd, s0, s1);
+                if (!(alive = grid_sum2(a, &st, s0, 0.0, rr_true, unused))) break;
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    s_updates += 1;
+                    s_rr_max = rr_true;
+                }
+                __syncthreads();
+                rr_new = rr_true;
+                if (rr_true <= a.tol2 * st.bb) { status = FE_OK; break; }
+                if (st.k >= a.maxit || s_updates >= a.max_updates) { status = FE_ERR_MAXIT; break; }
+            }
+            const double beta = rr_new / st.rr;
+            __syncthreads();
+            if (threadIdx.x == 0) st.rr = rr_new;
+            __syncthreads();
+            // C: p = r + beta p
+            update_p<float>(a.p, a.r, m, (float)beta);
+            if (!(alive = grid_barrier(a.ctrl, &st, a.timeout_ns, a.stall_barrier))) break;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.ctrl->status = alive ? status : FE_ERR_TIMEOUT;
+        a.ctrl->iterations = st.k;
+        a.ctrl->pad = s_updates;
+        a.ctrl->rr = st.rr;
+        a.ctrl->bb = st.bb;
+    }
+}
+
+template <int FL, class VL, int FH>
+static fe_status launch_reliable(const MixArgs &args, cudaStream_t s) {
+    auto kern = k_cg_reliable<FL, VL, FH>;
+    size_t smem = spmv_smem_bytes<FH, double>(kCgWarps);
+    const size_t smem_lo = spmv_smem_bytes<FL, float>(kCgWarps);
+    if (smem_lo > smem) smem = smem_lo;
+    if (smem > 48 * 1024)
+        FE_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    FE_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kCgThreads, smem));
+    if (per_sm < 1) return FE_ERR_CUDA;
+    int64_t blocks = (int64_t)sm_count() * per_sm;
+    const int64_t need = (args.A_lo.n_slices + kCgWarps - 1) / kCgWarps;
+    if (blocks > need) blocks = need;
+    if (blocks > kCgMaxBlocks) blocks = kCgMaxBlocks;
+    if (blocks < 1) blocks = 1;
+    void *params[] = {(void *)&args};
+    FE_TRY_CUDA(cudaLaunchCooperativeKernel((const void *)kern, dim3((unsigned)blocks), dim3(kCgThreads),
+                                            params, smem, s));
+    return FE_OK;
+}
+
+template <int FL, class VL>
+static fe_status dispatch_reliable_hi(const MixArgs &a, cudaStream_t s) {
+    switch (a.A_hi.format) {
+        case FE_FMT_CSR: return launch_reliable<FL, VL, FE_FMT_CSR>(a, s);
+        case FE_FMT_SELL: return launch_reliable<FL, VL, FE_FMT_SELL>(a, s);
+        case FE_FMT_BCRS3: return launch_reliable<FL, VL, FE_FMT_BCRS3>(a, s);
+        default: return FE_ERR_ARG;
+    }
+}
+
+static fe_status dispatch_reliable(const MixArgs &a, cudaStream_t s) {
+    switch (a.A_lo.format * 3 + a.A_lo.value_type) {
+        case FE_FMT_CSR * 3 + FE_VAL_F32: return dispatch_reliable_hi<FE_FMT_CSR, float>(a, s);
+        case FE_FMT_CSR * 3 + FE_VAL_BF16: return dispatch_reliable_hi<FE_FMT_CSR, __nv_bfloat16>(a, s);
+        case FE_FMT_SELL * 3 + FE_VAL_F32: return dispatch_reliable_hi<FE_FMT_SELL, float>(a, s);
+        case FE_FMT_SELL * 3 + FE_VAL_BF16: return dispatch_reliable_hi<FE_FMT_SELL, __nv_bfloat16>(a, s);
+        case FE_FMT_BCRS3 * 3 + FE_VAL_F32: return dispatch_reliable_hi<FE_FMT_BCRS3, float>(a, s);
+        case FE_FMT_BCRS3 * 3 + FE_VAL_BF16: return dispatch_reliable_hi<FE_FMT_BCRS3, __nv_bfloat16>(a, s);
+        default: return FE_ERR_ARG;  // FP64 inner values: use fe_cg_solve
+    }
+}
+
+static fe_status solve_mixed_reliable(const fe_matrix *A64, const fe_matrix *A_lo, const double *d_b,
+                                      double *d_x, double tol, int max_outer, double inner_tol,
+                                      int max_inner, double timeout_s, void *d_work,
+                                      fe_mixed_result *h_result, cudaStream_t s) {
+    char *ws = (char *)d_work;
+    MixArgs a;
+    a.A_lo = *A_lo;
+    a.A_hi = *A64;
+    a.b = d_b;
+    a.x = d_x;
+    a.ctrl = (CgCtrl *)ws;
+    a.part = (double *)(ws + 256);
+    char *q = ws + 256 + align256(2 * 2 * (size_t)kCgMaxBlocks * sizeof(double)) +
+              align256(FE_RESID_WORK_BYTES);
+    const size_t vec = align256((size_t)A_lo->n_slices * kSlice * sizeof(float));
+    a.r = (float *)q;
+    a.p = (float *)(q + vec);
+    a.w = (float *)(q + 2 * vec);
+    a.xs = (float *)(q + 3 * vec);
+    a.tol2 = tol * tol;
+    a.delta2 = inner_tol * inner_tol;
+    a.maxit = max_inner;
+    a.max_updates = max_outer;
+    a.timeout_ns = (long long)((timeout_s > 0.0 ? timeout_s : 2.0) * 1e9);
+    a.stall_barrier = -1;
+    FE_TRY_CUDA(cudaMemsetAsync(a.ctrl, 0, sizeof(CgCtrl), s));
+    fe_status st = dispatch_reliable(a, s);
+    if (st != FE_OK) return st;
+    CgCtrl c;
+    FE_TRY_CUDA(cudaMemcpyAsync(&c, a.ctrl, sizeof(CgCtrl), cudaMemcpyDeviceToHost, s));
+    FE_TRY_CUDA(cudaStreamSynchronize(s));
+    h_result->status = c.status;
+    h_result->outer_iterations = c.pad;
+    h_result->inner_iterations = c.iterations;
+    h_result->bnorm = sqrt(c.bb);
+    h_result->relres = c.bb > 0.0 ? sqrt(c.rr / c.bb) : 0.0;
+    return (fe_status)c.status;
+}
+
+
+// Restarted refinement: host loop of FP64 residual -> FP32 CG from zero ->
+// FP64 update.  Arguments already checked by the caller.
+static fe_status solve_mixed_restart(const fe_matrix *A64, const fe_matrix *A_lo, const double *d_b,
+                                     double *d_x, double tol, int max_outer, double inner_tol,
+                                     int max_inner, double timeout_s, void *d_work,
+                                     fe_mixed_result *h_result, cudaStream_t s) {
+    fe_status st = FE_OK;
+
+    char *ws = (char *)d_work;
+    CgCtrl *ctrl = (CgCtrl *)ws;
+    double *cg_part = (double *)(ws + 256);
+    char *q = ws + 256 + align256(2 * 2 * (size_t)kCgMaxBlocks * sizeof(double));
+    double *res_part = (double *)q;
+    double *res_out = res_part + 2 * kCgMaxBlocks;
+    q += align256(FE_RESID_WORK_BYTES);
+    const size_t vec = align256((size_t)A_lo->n_slices * kSlice * sizeof(float));
+    float *r32 = (float *)q, *d32 = (float *)(q + vec), *ri = (float *)(q + 2 * vec),
+          *pi = (float *)(q + 3 * vec), *wi = (float *)(q + 4 * vec);
+
+    CgArgs<float> in;
+    in.A = *A_lo;
+    in.b = r32;
+    in.x = d32;
+    in.r = ri;
+    in.p = pi;
+    in.w = wi;
+    in.part = cg_part;
+    in.ctrl = ctrl;
+    in.tol2 = inner_tol * inner_tol;
+    in.maxit = max_inner;
+    in.x0_zero = 1;
+    in.timeout_ns = (long long)((timeout_s > 0.0 ? timeout_s : 2.0) * 1e9);
+    in.stall_barrier = -1;
+    in.x64 = d_x;
+
+    int outer = 0, inner_total = 0, status = FE_ERR_MAXIT;
+    double relres = 0.0, bnorm = 0.0;
+    while (true) {
+        // r = b - A64 x in FP64 (stored in FP32 for the inner solve), ||r||, ||b||
+        int nb = 0;
+        st = dispatch_resid(*A64, d_b, d_x, res_part, r32, &nb, s);
+        if (st != FE_OK) return st;
+        k_resid_final<<<1, 32, 0, s>>>(nb, res_part, res_out);
+        FE_TRY_LAUNCH();
+        double h[2];
+        FE_TRY_CUDA(cudaMemcpyAsync(h, res_out, sizeof(h), cudaMemcpyDeviceToHost, s));
+        FE_TRY_CUDA(cudaStreamSynchronize(s));
+        bnorm = sqrt(h[1]);
+        if (h[1] == 0.0) {  // b = 0: the solution is 0
+            FE_TRY_CUDA(cudaMemsetAsync(d_x, 0, (size_t)A64->n_rows * sizeof(double), s));
+            FE_TRY_CUDA(cudaStreamSynchronize(s));
+            relres = 0.0;
+            status = FE_OK;
+            break;
+        }
+        relres = sqrt(h[0] / h[1]);
+        if (!(relres == relres)) { status = FE_ERR_BREAKDOWN; break; }
+        if (relres <= tol) { status = FE_OK; break; }
+        if (outer >= max_outer) { status = FE_ERR_MAXIT; break; }
+        // inner FP32 CG on A_lo d = r, then x += d (inside the kernel)
+        FE_TRY_CUDA(cudaMemsetAsync(ctrl, 0, sizeof(CgCtrl), s));
+        st = launch_cg_f32(in, s);
+        if (st != FE_OK) return st;
+        CgCtrl c;
+        FE_TRY_CUDA(cudaMemcpyAsync(&c, ctrl, sizeof(CgCtrl), cudaMemcpyDeviceToHost, s));
+        FE_TRY_CUDA(cudaStreamSynchronize(s));
+        inner_total += c.iterations;
+        ++outer;
+        if (c.status == FE_ERR_TIMEOUT || c.status == FE_ERR_BREAKDOWN) { status = c.status; break; }
+    }
+    h_result->status = status;
+    h_result->outer_iterations = outer;
+    h_result->inner_iterations = inner_total;
+    h_result->relres = relres;
+    h_result->bnorm = bnorm;
+    return (fe_status)status;
+}
+
+
+}  // namespace fe
+
+using namespace fe;
+
+extern "C" {
+
+fe_status fe_cg_mixed_workspace(const fe_matrix *A_lo, size_t *h_bytes) {
+    fe_status st = check_matrix(A_lo);
+    if (st != FE_OK) return st;
+    if (h_bytes == nullptr) return FE_ERR_ARG;
+    *h_bytes = mixed_workspace_bytes(*A_lo);
+    return FE_OK;
+}
+
+fe_status fe_cg_solve_mixed(const fe_matrix *A64, const fe_matrix *A_lo, const double *d_b,
+                            double *d_x, double tol, int mode, int max_outer, double inner_tol,
+                            int max_inner, double timeout_s, void *d_work, size_t work_bytes,
+                            fe_mixed_result *h_result, fe_stream_t stream) {
+    fe_status st = check_matrix(A64);
+    if (st != FE_OK) return st;
+    st = check_matrix(A_lo);
+    if (st != FE_OK) return st;
+    if (A64->value_type != FE_VAL_F64 || A64->n_rows != A64->n_cols ||
+        A_lo->n_rows != A64->n_rows || A_lo->n_cols != A64->n_cols)
+        return FE_ERR_ARG;
+    if (mode != FE_MIXED_RELIABLE && mode != FE_MIXED_RESTART) return FE_ERR_ARG;
+    if (mode == FE_MIXED_RELIABLE && A_lo->value_type == FE_VAL_F64) return FE_ERR_ARG;
+    if (!d_b || !d_x || !d_work || !h_result || max_outer < 0 || max_inner < 0 || !(tol >= 0.0) ||
+        !(inner_tol > 0.0 && inner_tol < 1.0))
+        return FE_ERR_ARG;
+    if (!aligned(d_b, 16) || !aligned(d_x, 16) || !aligned(d_work, 256)) return FE_ERR_ARG;
+    if (work_bytes < mixed_workspace_bytes(*A_lo)) return FE_ERR_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (mode == FE_MIXED_RELIABLE)
+        return solve_mixed_reliable(A64, A_lo, d_b, d_x, tol, max_outer, inner_tol, max_inner,
+                                    timeout_s, d_work, h_result, s);
+    return solve_mixed_restart(A64, A_lo, d_b, d_x, tol, max_outer, inner_tol, max_inner, timeout_s,
+                               d_work, h_result, s);
+}
+
+}  // extern "C"

@@ -88,7 +88,7 @@ SIGNATURES = {
                               ctypes.POINTER(_D), _VP]),
     "fe_cg_mixed_workspace": (_I32, [ctypes.POINTER(fe_matrix), ctypes.POINTER(_SZ)]),
     "fe_cg_solve_mixed": (_I32, [ctypes.POINTER(fe_matrix), ctypes.POINTER(fe_matrix), _VP, _VP,
-                                 _D, ctypes.c_int, _D, ctypes.c_int, _D, _VP, _SZ,
+                                 _D, ctypes.c_int, ctypes.c_int, _D, ctypes.c_int, _D, _VP, _SZ,
                                  ctypes.POINTER(fe_mixed_result), _VP]),
     "fe_cg_solve_noalloc": (_I32, [ctypes.POINTER(fe_matrix), _VP, _VP, _D, ctypes.c_int, _D,
                                    ctypes.POINTER(fe_cg_result), _VP]),
@@ -216,11 +216,15 @@ def fe_cg_mixed_workspace(A_lo: fe_matrix) -> int:
     return n.value
 
 
-def fe_cg_solve_mixed(A64: fe_matrix, A_lo: fe_matrix, b, x, tol, max_outer, inner_tol, max_inner,
-                      work, timeout_s=0.0, stream=None, check=True) -> fe_mixed_result:
+FE_MIXED_RELIABLE, FE_MIXED_RESTART = 0, 1
+
+
+def fe_cg_solve_mixed(A64: fe_matrix, A_lo: fe_matrix, b, x, tol, mode, max_outer, inner_tol,
+                      max_inner, work, timeout_s=0.0, stream=None, check=True) -> fe_mixed_result:
     res = fe_mixed_result()
     st = load().fe_cg_solve_mixed(ctypes.byref(A64), ctypes.byref(A_lo), _ptr(b), _ptr(x),
-                                  float(tol), int(max_outer), float(inner_tol), int(max_inner),
+                                  float(tol), int(mode), int(max_outer), float(inner_tol),
+                                  int(max_inner),
                                   float(timeout_s), _ptr(work), work.numel() * work.element_size(),
                                   ctypes.byref(res), _stream(stream))
     if check and st != FE_OK:

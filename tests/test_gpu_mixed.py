@@ -43,26 +43,31 @@ def rel(a, b):
     return np.linalg.norm(a - b) / np.linalg.norm(b)
 
 
-INNER_TOL = {"f32": 1e-5, "bf16": 1e-3}
+MODES = {"reliable": 0, "restart": 1}
+INNER_TOL = {("restart", "f32"): 1e-5, ("restart", "bf16"): 1e-3,
+             ("reliable", "f32"): 0.1, ("reliable", "bf16"): 0.1}
 
 
-def solve_mixed(fe, s, fmt, value, tol=1e-10, inner_tol=None, max_outer=30):
-    A64 = s.matrix("csr", "f64")
+def solve_mixed(fe, s, fmt, value, mode="reliable", tol=1e-10, inner_tol=None, max_outer=60,
+                max_inner=5000, hi="csr"):
+    A64 = s.matrix(hi, "f64")
     Alo = s.matrix(fmt, value)
     x = torch.zeros(s.m, dtype=torch.float64, device="cuda")
     work = fe.mixed_workspace(Alo)
-    res = fe.fe_cg_solve_mixed(A64.desc, Alo.desc, s.b, x, tol, max_outer,
-                               inner_tol or INNER_TOL[value], 5000, work, check=False)
+    res = fe.fe_cg_solve_mixed(A64.desc, Alo.desc, s.b, x, tol, MODES[mode], max_outer,
+                               inner_tol or INNER_TOL[(mode, value)], max_inner, work,
+                               check=False)
     return x, res
 
 
+@pytest.mark.parametrize("mode", ["reliable", "restart"])
 @pytest.mark.parametrize("fmt", ["csr", "sell", "bcrs3"])
 @pytest.mark.parametrize("value", ["f32", "bf16"])
-def test_mixed_matches_fp64_oracle(fe, fmt, value):
+def test_mixed_matches_fp64_oracle(fe, mode, fmt, value):
     dims = (30, 30, 30)
     sysm, x_or, x_star = reference(dims)
     s = fe.System(*dims).build()
-    x, res = solve_mixed(fe, s, fmt, value)
+    x, res = solve_mixed(fe, s, fmt, value, mode)
     assert res.status == fe.FE_OK and res.relres <= 1e-10
     xg = x.cpu().numpy()
     tr = oracle.true_relres(sysm["row_ptr"], sysm["cols"], sysm["vals"], sysm["b"], xg)
@@ -71,30 +76,66 @@ def test_mixed_matches_fp64_oracle(fe, fmt, value):
     assert res.outer_iterations >= 1 and res.inner_iterations >= res.outer_iterations
 
 
+@pytest.mark.parametrize("hi", ["sell", "bcrs3"])
+def test_reliable_with_sliced_fp64_matrix(fe, hi):
+    dims = (25, 21, 19)
+    sysm, x_or, x_star = reference(dims)
+    s = fe.System(*dims).build()
+    x, res = solve_mixed(fe, s, "bcrs3", "bf16", hi=hi)
+    assert res.status == fe.FE_OK
+    xg = x.cpu().numpy()
+    assert oracle.true_relres(sysm["row_ptr"], sysm["cols"], sysm["vals"], sysm["b"], xg) <= 1.5e-10
+
+
+@pytest.mark.parametrize("mode", ["reliable", "restart"])
 @pytest.mark.parametrize("value", ["f32", "bf16"])
-def test_mixed_face_data(fe, value):
+def test_mixed_face_data(fe, mode, value):
     dims = (20, 16, 24)
     face = fe_inputs.face_data(3, 9, *dims)
     sysm, x_or, x_star = reference(dims, face)
     s = fe.System(*dims, face_vals=torch.from_numpy(face).cuda()).build()
-    x, res = solve_mixed(fe, s, "bcrs3", value)
+    x, res = solve_mixed(fe, s, "bcrs3", value, mode)
     assert res.status == fe.FE_OK
     xg = x.cpu().numpy()
     assert oracle.true_relres(sysm["row_ptr"], sysm["cols"], sysm["vals"], sysm["b"], xg) <= 1.5e-10
     assert rel(xg, x_star) <= 2.0 * rel(x_or, x_star) + 1e-12
 
 
-def test_mixed_edge_cases(fe):
+@pytest.mark.parametrize("mode", ["reliable", "restart"])
+def test_mixed_edge_cases(fe, mode):
     s = fe.System(6, 5, 4).build()
-    # b = 0 gives x = 0 without an inner solve
+    # b = 0 gives x = 0 without an inner step
     s.b.zero_()
-    x, res = solve_mixed(fe, s, "bcrs3", "bf16")
+    x, res = solve_mixed(fe, s, "bcrs3", "bf16", mode)
     assert res.status == fe.FE_OK and res.outer_iterations == 0 and torch.count_nonzero(x) == 0
     s.build()
-    # max_outer = 1 stops after one refinement step with MAXIT
-    x, res = solve_mixed(fe, s, "csr", "bf16", max_outer=1)
+    # one refinement step allowed: stops with MAXIT after it
+    x, res = solve_mixed(fe, s, "csr", "bf16", mode, max_outer=1)
     assert res.status == fe.FE_ERR_MAXIT and res.outer_iterations == 1
-    assert 0 < res.relres < 1e-2
-    # tol reachable only in FP64: FP32-valued matrix, tight tolerance, still converges
-    x, res = solve_mixed(fe, s, "sell", "f32", tol=1e-13)
+    assert 0 < res.relres < 1.0
+    # a tolerance FP32 arithmetic alone cannot reach: the FP64 refinement gets there
+    x, res = solve_mixed(fe, s, "sell", "f32", mode, tol=1e-13)
     assert res.status == fe.FE_OK and res.relres <= 1e-13
+
+
+def test_reliable_rejects_fp64_inner(fe):
+    s = fe.System(4).build()
+    A64 = s.matrix("csr", "f64")
+    x = torch.zeros(s.m, dtype=torch.float64, device="cuda")
+    with pytest.raises(fe.FeError) as e:
+        fe.fe_cg_solve_mixed(A64.desc, A64.desc, s.b, x, 1e-10, 0, 10, 0.1, 100,
+                             fe.mixed_workspace(A64))
+    assert e.value.status == fe.FE_ERR_ARG
+
+
+def test_reliable_step_count_near_fp64(fe):
+    """Refinement steps keep the Krylov space: the FP32 step count stays within
+    15% of the FP64 solve's on the same problem."""
+    s = fe.System(40).build()
+    A = s.matrix("bcrs3", "f64")
+    x = torch.zeros(s.m, dtype=torch.float64, device="cuda")
+    ref = fe.fe_cg_solve(A.desc, s.b, x, 1e-10, 5000, fe.cg_workspace(A))
+    for value in ("f32", "bf16"):
+        x, res = solve_mixed(fe, s, "bcrs3", value)
+        assert res.status == fe.FE_OK
+        assert res.inner_iterations <= 1.15 * ref.iterations + 5, (value, res.inner_iterations, ref.iterations)
