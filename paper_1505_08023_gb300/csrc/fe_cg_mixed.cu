@@ -90,6 +90,7 @@ __global__ void __launch_bounds__(kCgThreads, kCgBlocksPerSm) k_cg_reliable(cons
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ CgBlockState st;
     __shared__ double s_rr_max;
+    __shared__ double s_rr_true;   // last FP64 true residual (reported)
     __shared__ int s_updates;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     // CSR staging: the FP64 residual needs double slots, the FP32 SpMV float slots
@@ -116,12 +117,13 @@ __global__ void __launch_bounds__(kCgThreads, kCgBlocksPerSm) k_cg_reliable(cons
         st.rr = rr_true;
         st.bb = bb;
         s_rr_max = rr_true;
+        s_rr_true = rr_true;
     }
     __syncthreads();
     if (alive && bb == 0.0) {  // b = 0: the solution is 0
         const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
         for (int row = tid; row < m; row += nth) a.x[row] = 0.0;
-        if (threadIdx.x == 0) st.rr = 0.0;
+        if (threadIdx.x == 0) s_rr_true = 0.0;
         status = FE_OK;
     } else if (alive && rr_true <= a.tol2 * bb) {
         status = FE_OK;
@@ -159,6 +161,7 @@ __global__ void __launch_bounds__(kCgThreads, kCgBlocksPerSm) k_cg_reliable(cons
                 if (threadIdx.x == 0) {
                     s_updates += 1;
                     s_rr_max = rr_true;
+                    s_rr_true = rr_true;
                 }
                 __syncthreads();
                 rr_new = rr_true;
@@ -178,7 +181,7 @@ __global__ void __launch_bounds__(kCgThreads, kCgBlocksPerSm) k_cg_reliable(cons
         a.ctrl->status = alive ? status : FE_ERR_TIMEOUT;
         a.ctrl->iterations = st.k;
         a.ctrl->pad = s_updates;
-        a.ctrl->rr = st.rr;
+        a.ctrl->rr = s_rr_true;
         a.ctrl->bb = st.bb;
     }
 }
