@@ -145,10 +145,11 @@ template <class XT> __device__ __forceinline__ XT &lane_of(typename Pack16<XT>::
     return reinterpret_cast<XT *>(&v)[i];
 }
 
+// The vectors below are rewritten by other blocks between grid barriers: no
+// __restrict__, so every load stays on the coherent path.
 // B: x += alpha p, r -= alpha w; returns this thread's partial of r.r
 template <class XT>
-__device__ __forceinline__ XT update_xr(XT *__restrict__ x, XT *__restrict__ r,
-                                        const XT *__restrict__ p, const XT *__restrict__ w,
+__device__ __forceinline__ XT update_xr(XT *x, XT *r, const XT *p, const XT *w,
                                         int64_t m, XT alpha) {
     using P = typename Pack16<XT>::T;
     constexpr int V = Pack16<XT>::N;
@@ -189,7 +190,7 @@ __device__ __forceinline__ XT update_xr(XT *__restrict__ x, XT *__restrict__ r,
 
 // C: p = r + beta p
 template <class XT>
-__device__ __forceinline__ void update_p(XT *__restrict__ p, const XT *__restrict__ r, int64_t m,
+__device__ __forceinline__ void update_p(XT *p, const XT *r, int64_t m,
                                          XT beta) {
     using P = typename Pack16<XT>::T;
     constexpr int V = Pack16<XT>::N;

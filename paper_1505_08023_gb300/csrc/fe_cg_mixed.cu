@@ -63,7 +63,7 @@ __device__ __forceinline__ void fp64_residual(const MixArgs &a, int m, int ns, b
 }
 
 // x += xs, xs = 0 (the FP64 refinement update)
-__device__ __forceinline__ void fold_correction(double *__restrict__ x, float *__restrict__ xs, int m) {
+__device__ __forceinline__ void fold_correction(double *x, float *xs, int m) {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
     const int npk = m / 4;
     float4 *xs4 = reinterpret_cast<float4 *>(xs);

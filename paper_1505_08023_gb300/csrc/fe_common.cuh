@@ -83,7 +83,7 @@ constexpr int kCsrStage = 32 * 27;
 // rows past the end).  XT: vector type, AT: accumulation type.
 template <class VT, class XT, class AT, bool kReadOnlyX>
 __device__ __forceinline__ AT slice_spmv_sell(const fe_matrix &A, int64_t s, int lane,
-                                              const XT *__restrict__ x) {
+                                              const XT *x) {
     const int64_t b = A.d_slice_ptr[s];
     const int w = (int)((A.d_slice_ptr[s + 1] - b) >> 5);
     const int32_t *c = A.d_cols + b + lane;
@@ -115,7 +115,7 @@ __device__ __forceinline__ AT slice_spmv_sell(const fe_matrix &A, int64_t s, int
 
 template <class VT, class XT, class AT, bool kReadOnlyX>
 __device__ __forceinline__ AT slice_spmv_bcrs3(const fe_matrix &A, int64_t s, int lane,
-                                               const XT *__restrict__ x) {
+                                               const XT *x) {
     const int64_t b = A.d_slice_ptr[s];
     const int w = (int)((A.d_slice_ptr[s + 1] - b) >> 5);
     const int32_t *c = A.d_cols + b + lane;
@@ -157,7 +157,7 @@ __device__ __forceinline__ AT slice_spmv_bcrs3(const fe_matrix &A, int64_t s, in
 // (one FMA per entry, all lanes busy).  sv/sx: kCsrStage entries per warp.
 template <class VT, class XT, class AT, bool kReadOnlyX>
 __device__ __forceinline__ AT slice_spmv_csr(const fe_matrix &A, int64_t s, int lane,
-                                             const XT *__restrict__ x, AT *sv, AT *sx) {
+                                             const XT *x, AT *sv, AT *sx) {
     const int64_t r0 = s * kSlice;
     const int64_t nrows = A.n_rows;
     const int64_t row = r0 + lane;
@@ -189,7 +189,7 @@ __device__ __forceinline__ AT slice_spmv_csr(const fe_matrix &A, int64_t s, int 
 
 template <int FMT, class VT, class XT, class AT, bool kReadOnlyX>
 __device__ __forceinline__ AT slice_spmv(const fe_matrix &A, int64_t s, int lane,
-                                         const XT *__restrict__ x, AT *sv, AT *sx) {
+                                         const XT *x, AT *sv, AT *sx) {
     if constexpr (FMT == FE_FMT_CSR) return slice_spmv_csr<VT, XT, AT, kReadOnlyX>(A, s, lane, x, sv, sx);
     else if constexpr (FMT == FE_FMT_SELL) return slice_spmv_sell<VT, XT, AT, kReadOnlyX>(A, s, lane, x);
     else return slice_spmv_bcrs3<VT, XT, AT, kReadOnlyX>(A, s, lane, x);
