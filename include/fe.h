@@ -237,7 +237,11 @@ typedef enum fe_mixed_mode {
  *     factor inner_tol since the last refinement step (or meets tol), the
  *     kernel sets x += d (FP64), recomputes r = b - A64 x (FP64) as the FP32
  *     residual and continues with the same search direction.  max_outer caps
- *     the refinement steps, max_inner the FP32 CG steps.  A_lo must not be FP64.
+ *     the refinement steps, max_inner the FP32 CG steps; four refinement
+ *     steps in a row that do not halve the true residual also end the solve
+ *     (FE_ERR_MAXIT): the low-precision operator is then too far from A64
+ *     (value error x condition number ~ 1), e.g. BF16 values on strongly
+ *     non-cubic elements.  A_lo must not be FP64.
  *   FE_MIXED_RESTART: repeat { r = b - A64 x; solve A_lo d = r by the FP32
  *     persistent CG from d = 0 to ||r_in|| <= inner_tol ||r|| or max_inner
  *     steps; x += d } at most max_outer times.

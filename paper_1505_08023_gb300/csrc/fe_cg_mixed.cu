@@ -24,6 +24,10 @@ static size_t mixed_workspace_bytes(const fe_matrix &lo) {
            align256(FE_RESID_WORK_BYTES) + 5 * vec;
 }
 
+// Refinement steps in a row without halving the true residual before the
+// reliable-update solve gives up (FE_ERR_MAXIT).
+constexpr int kMaxStalls = 4;
+
 struct MixArgs {
     fe_matrix A_lo, A_hi;
     const double *b;
@@ -85,6 +89,13 @@ __device__ __forceinline__ void fold_correction(double *x, float *xs, int m) {
     }
 }
 
+// Shared-memory bytes one warp needs for CSR staging: FP64 slots for a CSR
+// FP64 matrix, FP32 slots for a CSR low-precision matrix, 0 otherwise.
+template <int FL, int FH> __host__ __device__ constexpr size_t reliable_warp_stage_bytes() {
+    return FH == FE_FMT_CSR ? 2 * (size_t)kCsrStage * sizeof(double)
+                            : (FL == FE_FMT_CSR ? 2 * (size_t)kCsrStage * sizeof(float) : 0);
+}
+
 template <int FL, class VL, int FH>
 __global__ void __launch_bounds__(kCgThreads, kCgBlocksPerSm) k_cg_reliable(const MixArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -92,11 +103,15 @@ __global__ void __launch_bounds__(kCgThreads, kCgBlocksPerSm) k_cg_reliable(cons
     __shared__ double s_rr_max;
     __shared__ double s_rr_true;   // last FP64 true residual (reported)
     __shared__ int s_updates;
+    __shared__ int s_stalls;       // refinement steps in a row that did not halve the residual
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // CSR staging: the FP64 residual needs double slots, the FP32 SpMV float slots
-    double *svd = reinterpret_cast<double *>(smem_raw) + (size_t)warp * 2 * kCsrStage;
+    // CSR staging: the FP64 residual needs double slots, the FP32 SpMV float
+    // slots; each warp owns one region of the size the launch allocated
+    // (reliable_smem_bytes), which holds whichever of the two it needs.
+    unsigned char *mine = smem_raw + (size_t)warp * reliable_warp_stage_bytes<FL, FH>();
+    double *svd = reinterpret_cast<double *>(mine);
     double *sxd = svd + kCsrStage;
-    float *svf = reinterpret_cast<float *>(svd);
+    float *svf = reinterpret_cast<float *>(mine);
     float *sxf = svf + kCsrStage;
     const int m = (int)a.A_lo.n_rows, ns = (int)a.A_lo.n_slices;
     const int tw = gridDim.x * kCgWarps;
@@ -106,6 +121,7 @@ __global__ void __launch_bounds__(kCgThreads, kCgBlocksPerSm) k_cg_reliable(cons
         st.k = 0;
         st.ok = 1;
         s_updates = 0;
+        s_stalls = 0;
     }
     __syncthreads();
     int status = FE_ERR_MAXIT;
@@ -160,13 +176,19 @@ __global__ void __launch_bounds__(kCgThreads, kCgBlocksPerSm) k_cg_reliable(cons
                 __syncthreads();
                 if (threadIdx.x == 0) {
                     s_updates += 1;
+                    // the true residual must keep falling; if the low-precision
+                    // operator is too far from A64 (delta * cond(A) ~ 1) it stalls
+                    s_stalls = (rr_true > 0.25 * s_rr_true) ? s_stalls + 1 : 0;
                     s_rr_max = rr_true;
                     s_rr_true = rr_true;
                 }
                 __syncthreads();
                 rr_new = rr_true;
                 if (rr_true <= a.tol2 * st.bb) { status = FE_OK; break; }
-                if (st.k >= a.maxit || s_updates >= a.max_updates) { status = FE_ERR_MAXIT; break; }
+                if (st.k >= a.maxit || s_updates >= a.max_updates || s_stalls >= kMaxStalls) {
+                    status = FE_ERR_MAXIT;
+                    break;
+                }
             }
             const double beta = rr_new / st.rr;
             __syncthreads();
@@ -189,9 +211,7 @@ __global__ void __launch_bounds__(kCgThreads, kCgBlocksPerSm) k_cg_reliable(cons
 template <int FL, class VL, int FH>
 static fe_status launch_reliable(const MixArgs &args, cudaStream_t s) {
     auto kern = k_cg_reliable<FL, VL, FH>;
-    size_t smem = spmv_smem_bytes<FH, double>(kCgWarps);
-    const size_t smem_lo = spmv_smem_bytes<FL, float>(kCgWarps);
-    if (smem_lo > smem) smem = smem_lo;
+    const size_t smem = (size_t)kCgWarps * reliable_warp_stage_bytes<FL, FH>();
     if (smem > 48 * 1024)
         FE_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
