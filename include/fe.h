@@ -238,7 +238,8 @@ typedef enum fe_mixed_mode {
  *     kernel sets x += d (FP64), recomputes r = b - A64 x (FP64) as the FP32
  *     residual and continues with the same search direction.  max_outer caps
  *     the refinement steps, max_inner the FP32 CG steps; four refinement
- *     steps in a row that do not halve the true residual also end the solve
+ *     steps in a row that do not halve the true residual (a step is forced
+ *     after 256 FP32 steps without one) also end the solve
  *     (FE_ERR_MAXIT): the low-precision operator is then too far from A64
  *     (value error x condition number ~ 1), e.g. BF16 values on strongly
  *     non-cubic elements.  A_lo must not be FP64.

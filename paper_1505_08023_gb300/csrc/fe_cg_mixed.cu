@@ -27,6 +27,9 @@ static size_t mixed_workspace_bytes(const fe_matrix &lo) {
 // Refinement steps in a row without halving the true residual before the
 // reliable-update solve gives up (FE_ERR_MAXIT).
 constexpr int kMaxStalls = 4;
+// FP32 steps after which a refinement step is forced (a plateaued FP32
+// residual would otherwise never trigger one).
+constexpr int kForceRefineSteps = 256;
 
 struct MixArgs {
     fe_matrix A_lo, A_hi;
@@ -104,6 +107,7 @@ __global__ void __launch_bounds__(kCgThreads, kCgBlocksPerSm) k_cg_reliable(cons
     __shared__ double s_rr_true;   // last FP64 true residual (reported)
     __shared__ int s_updates;
     __shared__ int s_stalls;       // refinement steps in a row that did not halve the residual
+    __shared__ int s_last_refine;  // step count at the last refinement
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     // CSR staging: the FP64 residual needs double slots, the FP32 SpMV float
     // slots; each warp owns one region of the size the launch allocated
@@ -122,6 +126,7 @@ __global__ void __launch_bounds__(kCgThreads, kCgBlocksPerSm) k_cg_reliable(cons
         st.ok = 1;
         s_updates = 0;
         s_stalls = 0;
+        s_last_refine = 0;
     }
     __syncthreads();
     int status = FE_ERR_MAXIT;
@@ -166,7 +171,7 @@ __global__ void __launch_bounds__(kCgThreads, kCgBlocksPerSm) k_cg_reliable(cons
             if (threadIdx.x == 0) st.k += 1;
             __syncthreads();
             const bool refine = rr_new <= a.delta2 * s_rr_max || rr_new <= a.tol2 * st.bb ||
-                                st.k >= a.maxit;
+                                st.k >= a.maxit || st.k - s_last_refine >= kForceRefineSteps;
             if (refine) {
                 // x += xs in FP64, then r = b - A64 x in FP64 (stored as the FP32 residual)
                 fold_correction(a.x, a.xs, m);
@@ -176,6 +181,7 @@ __global__ void __launch_bounds__(kCgThreads, kCgBlocksPerSm) k_cg_reliable(cons
                 __syncthreads();
                 if (threadIdx.x == 0) {
                     s_updates += 1;
+                    s_last_refine = st.k;
                     // the true residual must keep falling; if the low-precision
                     // operator is too far from A64 (delta * cond(A) ~ 1) it stalls
                     s_stalls = (rr_true > 0.25 * s_rr_true) ? s_stalls + 1 : 0;
