@@ -19,6 +19,9 @@ Reported (one JSON line on rank 0):
                algorithmic bytes and FLOPs / its CUDA-event time)
   spmv         stand-alone SpMV GB/s of each storage format (the paper's
                CRS vs BCRS comparison) against the measured HBM peak
+  mixed        the mixed-precision form on the same system (FP32 values,
+               FP32 CG with FP64 reliable updates): time to 1e-10 and its
+               speedup over the FP64 solve, with the solutions' difference
   cpu_baseline the CPU oracle, single core, on a bounded sample of the same
                workload (a few CG iterations of the N = 256 system), scaled
                to the solve's iteration count
@@ -247,6 +250,7 @@ def main():
     ap.add_argument("--ref-iters", type=int, default=2, help="oracle CG iterations per reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-spmv", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -353,6 +357,42 @@ def main():
                      "fp64_flops_per_launch": int(2 * launch_fma),
                      "other": roof_hbm if bound == "alu" else roof_alu})
 
+    # ---- mixed-precision form on the same system (FP32 values, reliable updates)
+    mixed = None
+    if not args.no_mixed:
+        x64_ref = x.clone()                        # the FP64 solve's solution
+        A64 = state["A"]
+        Alo = s.convert(args.format, "f32")
+        mwork = fe.mixed_workspace(Alo, dev)
+        xm = torch.zeros(m, dtype=torch.float64, device=dev)
+
+        def mixed_solve():
+            xm.zero_()
+            a, b = EV(), EV()
+            a.record()
+            r = fe.fe_cg_solve_mixed(A64.desc, Alo.desc, s.b, xm, TOL, fe.FE_MIXED_RELIABLE, 200,
+                                     0.1, MAXIT, mwork, check=False)
+            b.record()
+            return a, b, r
+
+        for _ in range(args.warmup):
+            mixed_solve()
+        torch.cuda.synchronize()
+        recs = [mixed_solve() for _ in range(args.steps)]
+        torch.cuda.synchronize()
+        mt = statistics.mean(a.elapsed_time(b) for a, b, _ in recs)
+        r = recs[-1][2]
+        err = float(torch.linalg.norm(xm - x64_ref) / torch.linalg.norm(x64_ref))
+        mixed = {"value": round(mt * 1e-3, 6), "unit": "s", "values": "f32",
+                 "mode": "reliable updates (FP32 CG, FP64 residual/update/dots), delta 0.1",
+                 "speedup_vs_fp64": round(cg_ms / mt, 3), "fp32_iterations": r.inner_iterations,
+                 "refinement_steps": r.outer_iterations, "relres_true": r.relres,
+                 "status": r.status, "rel_diff_vs_fp64_solution": err,
+                 "ms_per_fp32_iteration": round(mt / max(r.inner_iterations, 1), 4)}
+        s._formats.pop((args.format, "f32"), None)
+        del Alo, mwork
+        torch.cuda.empty_cache()
+
     # ---- e2e: host boundary data in, host solution out, through the Python API
     e2e = None
     if True:
@@ -422,7 +462,7 @@ def main():
         del flush
         torch.cuda.empty_cache()
 
-    launches_per_step = 7   # mesh 1, assembly 2, slice plan 2, fill 1, CG 1
+    launches_per_step = 7   # mesh 1, assembly 2, slice plan 2, fill 1, CG 1 (timed FP64 steps)
 
     if rank == 0:
         cpu = None
@@ -436,7 +476,8 @@ def main():
                 "iterations": it, "relres_true": tr, "status": sorted(statuses),
                 "cg_ms_per_iteration": round(cg_ms / max(it, 1), 4),
                 "phase_ms": {k: round(statistics.mean(v), 3) for k, v in phases.items()},
-                "roofline": roofline, "spmv": spmv, "e2e": e2e, "cpu_baseline": cpu,
+                "roofline": roofline, "mixed": mixed, "spmv": spmv, "e2e": e2e,
+                "cpu_baseline": cpu,
                 "clocks": clocks, "gpu_launches": launches_per_step * args.steps,
                 "wall_s_timed_region": round(wall, 3)}
         print(json.dumps(line), flush=True)
