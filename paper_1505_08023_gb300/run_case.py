@@ -1,0 +1,60 @@
+"""Run one case of the path once (for profiling or a quick check).
+
+    python -m paper_1505_08023_gb300.run_case --n 128 --cg-steps 20 --mixed-steps 20
+
+Builds the N x N x N problem through the C ABI (mesh, assembly, conversion to
+--format), then runs, as asked: one stand-alone SpMV (--spmv), the fused FP64
+CG for --cg-steps steps (tol 0, or to --tol when --cg-steps is 0), and the
+mixed-precision reliable-update solve for --mixed-steps FP32 steps.  With
+--drop-csr the CSR arrays are released after conversion (smaller footprint
+for profiler captures that save and restore device memory).  Prints one line
+per step taken.
+"""
+from __future__ import annotations
+
+import argparse
+
+import torch
+
+from . import fe
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--n", type=int, default=128)
+    ap.add_argument("--format", choices=["csr", "sell", "bcrs3"], default="bcrs3")
+    ap.add_argument("--spmv", action="store_true")
+    ap.add_argument("--cg-steps", type=int, default=20)
+    ap.add_argument("--tol", type=float, default=1e-10)
+    ap.add_argument("--mixed-steps", type=int, default=0)
+    ap.add_argument("--mixed-values", choices=["f32", "bf16"], default="f32")
+    ap.add_argument("--drop-csr", action="store_true")
+    a = ap.parse_args()
+
+    s = fe.System(a.n).build()
+    A = s.matrix(a.format, "f64")
+    Alo = s.matrix(a.format, a.mixed_values) if a.mixed_steps > 0 else None
+    if a.drop_csr and a.format != "csr":
+        s.cols = s.vals = None
+        s.coords = None
+        torch.cuda.empty_cache()
+    x = torch.zeros(s.m, dtype=torch.float64, device="cuda")
+    if a.spmv:
+        y = torch.empty_like(x)
+        fe.fe_spmv(A.desc, s.b, y)
+        print("spmv done")
+    if a.cg_steps >= 0:
+        tol, steps = (0.0, a.cg_steps) if a.cg_steps > 0 else (a.tol, 100000)
+        r = fe.fe_cg_solve(A.desc, s.b, x, tol, steps, fe.cg_workspace(A), check=False)
+        print(f"cg: status {r.status} steps {r.iterations} relres {r.relres:.3e}")
+    if Alo is not None:
+        x.zero_()
+        r = fe.fe_cg_solve_mixed(A.desc, Alo.desc, s.b, x, a.tol, fe.FE_MIXED_RELIABLE, 200, 0.1,
+                                 a.mixed_steps, fe.mixed_workspace(Alo), check=False)
+        print(f"mixed: status {r.status} fp32 steps {r.inner_iterations} "
+              f"refinements {r.outer_iterations} relres {r.relres:.3e}")
+    torch.cuda.synchronize()
+
+
+if __name__ == "__main__":
+    main()
