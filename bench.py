@@ -53,6 +53,11 @@ MAXIT = 5000
 # both run to the end); the reference arm scales its per-step time by it.
 ITERS_TO_TOL = {256: 507}
 FP64_PEAK_TFLOPS = 1.25   # nominal dense FP64 of a GB300 (2 FMA/clk/SM x 152 SMs x ~2.06 GHz)
+# DRAM bytes (read + write) per row of k_cg<bcrs3,f64>: per CG step and for the
+# initial residual, from two ncu captures at N=180 where, as at N=256, the CG
+# vectors exceed L2 (profiles/k_cg_n180_ncu_traffic.md).  Valid for the kernel
+# as captured; set to None when k_cg changes until it is captured again.
+K_CG_BCRS3_TRAFFIC_PER_ROW = {"step": 331.3, "init": 256.5}
 
 
 def load_peaks():
@@ -345,11 +350,15 @@ def main():
     hbm_floor = launch_bytes / (hbm_peak * 1e9)
     alu_floor = 2 * launch_fma / (FP64_PEAK_TFLOPS * 1e12)
     bound = "alu" if alu_floor > hbm_floor else "hbm"
+    traffic = None
+    if args.format == "bcrs3" and K_CG_BCRS3_TRAFFIC_PER_ROW:
+        t = K_CG_BCRS3_TRAFFIC_PER_ROW
+        traffic = int((it * t["step"] + t["init"]) * m)
     roof_hbm = {"bound": "hbm", "achieved": round(hbm_ach, 1), "peak": hbm_peak, "unit": "GB/s",
-                "frac": round(hbm_ach / hbm_peak, 4), "traffic": None,
+                "frac": round(hbm_ach / hbm_peak, 4), "traffic": traffic,
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"}
     roof_alu = {"bound": "alu", "achieved": round(fp64_ach, 4), "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": round(fp64_ach / FP64_PEAK_TFLOPS, 4), "traffic": None,
+                "unit": "TFLOP/s", "frac": round(fp64_ach / FP64_PEAK_TFLOPS, 4), "traffic": traffic,
                 "peak_source": "nominal FP64 (2 DFMA/clk/SM x 152 SMs); probe measured 1.26"}
     roofline = dict(roof_alu if bound == "alu" else roof_hbm)
     roofline.update({"kernel": f"k_cg<{args.format},f64>",
