@@ -281,6 +281,52 @@ fe_status fe_cg_solve_noalloc(const fe_matrix *A, const double *d_b, double *d_x
                               int maxit, double timeout_s, fe_cg_result *h_result,
                               fe_stream_t stream);
 
+/*
+ * Batched form (the benchmark spec form X2; the paper solves one system): many
+ * independent CG solves -- meshes of different sizes, different boundary data
+ * -- in one persistent cooperative launch.  System i is A[i] x_i = b_i; every
+ * A[i] is FP64 with one common format (FE_FMT_BCRS3 or FE_FMT_SELL).  Systems
+ * whose descriptors point to the same arrays share the matrix and are solved
+ * together as an SpMM over up to `krhs` (1, 2 or 4) right-hand sides, so each
+ * matrix slot is read once per chunk.  Each system keeps its own alpha, beta,
+ * stopping test (||r|| <= tol ||b||) and status, exactly as fe_cg_solve; a
+ * converged system leaves the work list and the remaining work is
+ * re-partitioned over all blocks.  Dot products are summed in a fixed order.
+ *
+ * fe_cg_batched_plan   checks the systems, groups them, writes the work tables
+ *                      into d_work and fills *h_plan (synchronises `stream`).
+ *                      blocks_per_sm: 0 = the most that fit.
+ * fe_cg_batched_launch enqueues the solve (a memset and one cooperative
+ *                      kernel; no host synchronisation, no allocation), so it
+ *                      can be captured in a CUDA graph and replayed.
+ * fe_cg_batched_results copies the per-system results into h_results[i]
+ *                      (caller's order; synchronises) and returns the first
+ *                      non-OK status, or FE_OK.
+ * fe_cg_solve_batched  plan + launch + results.
+ * d_x[i]: start vectors in, solutions out.  At most FE_BATCH_MAX_SYSTEMS
+ * systems; FE_ERR_ARG if a block would have to reduce more than 32 systems.
+ */
+#define FE_BATCH_MAX_SYSTEMS 256
+typedef struct fe_batch_plan {
+    int32_t format, krhs, n_systems, n_chunks, grid, max_blocks;
+    void *d_work;
+    size_t work_bytes;
+    int32_t slot_of[FE_BATCH_MAX_SYSTEMS];  /* caller's index -> internal slot */
+} fe_batch_plan;
+
+fe_status fe_cg_batched_workspace(int n_systems, const fe_matrix *A, size_t *h_bytes);
+fe_status fe_cg_batched_plan(int n_systems, const fe_matrix *A, const double *const *d_b,
+                             double *const *d_x, int krhs, int blocks_per_sm, void *d_work,
+                             size_t work_bytes, fe_batch_plan *h_plan, fe_stream_t stream);
+fe_status fe_cg_batched_launch(const fe_batch_plan *plan, double tol, int maxit, double timeout_s,
+                               fe_stream_t stream);
+fe_status fe_cg_batched_results(const fe_batch_plan *plan, fe_cg_result *h_results,
+                                fe_stream_t stream);
+fe_status fe_cg_solve_batched(int n_systems, const fe_matrix *A, const double *const *d_b,
+                              double *const *d_x, double tol, int maxit, int krhs,
+                              double timeout_s, void *d_work, size_t work_bytes,
+                              fe_cg_result *h_results, fe_stream_t stream);
+
 /* Fault injection for tests of the barrier time limit: the next fe_cg_solve
  * on the calling thread has block 0 skip its arrival at grid barrier number
  * barrier_index (0 = the barrier after the initial residual), so every

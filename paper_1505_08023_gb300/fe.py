@@ -67,6 +67,17 @@ class fe_mixed_result(ctypes.Structure):
                 ("relres", ctypes.c_double), ("bnorm", ctypes.c_double)]
 
 
+BATCH_MAX_SYSTEMS = 256
+
+
+class fe_batch_plan(ctypes.Structure):
+    _fields_ = [("format", ctypes.c_int32), ("krhs", ctypes.c_int32),
+                ("n_systems", ctypes.c_int32), ("n_chunks", ctypes.c_int32),
+                ("grid", ctypes.c_int32), ("max_blocks", ctypes.c_int32),
+                ("d_work", ctypes.c_void_p), ("work_bytes", ctypes.c_size_t),
+                ("slot_of", ctypes.c_int32 * BATCH_MAX_SYSTEMS)]
+
+
 # Exported entry points: name -> (restype, argtypes).  Tests check that the
 # shared library exports exactly these names and that include/fe.h declares them.
 _VP, _I32, _I64, _D, _SZ = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_size_t
@@ -91,6 +102,15 @@ SIGNATURES = {
                                  _D, ctypes.c_int, ctypes.c_int, _D, ctypes.c_int, _D, _VP, _SZ,
                                  ctypes.POINTER(fe_mixed_result), _VP]),
     "fe_cg_solve_noalloc": (_I32, [ctypes.POINTER(fe_matrix), _VP, _VP, _D, ctypes.c_int, _D,
+                                   ctypes.POINTER(fe_cg_result), _VP]),
+    "fe_cg_batched_workspace": (_I32, [ctypes.c_int, ctypes.POINTER(fe_matrix), ctypes.POINTER(_SZ)]),
+    "fe_cg_batched_plan": (_I32, [ctypes.c_int, ctypes.POINTER(fe_matrix), ctypes.POINTER(_VP),
+                                  ctypes.POINTER(_VP), ctypes.c_int, ctypes.c_int, _VP, _SZ,
+                                  ctypes.POINTER(fe_batch_plan), _VP]),
+    "fe_cg_batched_launch": (_I32, [ctypes.POINTER(fe_batch_plan), _D, ctypes.c_int, _D, _VP]),
+    "fe_cg_batched_results": (_I32, [ctypes.POINTER(fe_batch_plan), ctypes.POINTER(fe_cg_result), _VP]),
+    "fe_cg_solve_batched": (_I32, [ctypes.c_int, ctypes.POINTER(fe_matrix), ctypes.POINTER(_VP),
+                                   ctypes.POINTER(_VP), _D, ctypes.c_int, ctypes.c_int, _D, _VP, _SZ,
                                    ctypes.POINTER(fe_cg_result), _VP]),
     "fe_inject_barrier_stall": (_I32, [ctypes.c_int]),
     "fe_last_cuda_error": (ctypes.c_int, []),
@@ -258,6 +278,56 @@ def fe_inject_barrier_stall(barrier_index: int):
     return _check("fe_inject_barrier_stall", load().fe_inject_barrier_stall(barrier_index))
 
 
+def _descs(mats) -> ctypes.Array:
+    arr = (fe_matrix * len(mats))()
+    for i, d in enumerate(mats):
+        arr[i] = d
+    return arr
+
+
+def _ptrs(tensors) -> ctypes.Array:
+    arr = (ctypes.c_void_p * len(tensors))()
+    for i, t in enumerate(tensors):
+        arr[i] = _ptr(t)
+    return arr
+
+
+def fe_cg_batched_workspace(mats) -> int:
+    n = ctypes.c_size_t(0)
+    _check("fe_cg_batched_workspace",
+           load().fe_cg_batched_workspace(len(mats), _descs(mats), ctypes.byref(n)))
+    return n.value
+
+
+def fe_cg_batched_plan(mats, bs, xs, krhs, work, blocks_per_sm=0, stream=None) -> fe_batch_plan:
+    plan = fe_batch_plan()
+    _check("fe_cg_batched_plan", load().fe_cg_batched_plan(
+        len(mats), _descs(mats), _ptrs(bs), _ptrs(xs), int(krhs), int(blocks_per_sm), _ptr(work),
+        work.numel() * work.element_size(), ctypes.byref(plan), _stream(stream)))
+    return plan
+
+
+def fe_cg_batched_launch(plan: fe_batch_plan, tol, maxit, timeout_s=0.0, stream=None):
+    return _check("fe_cg_batched_launch", load().fe_cg_batched_launch(
+        ctypes.byref(plan), float(tol), int(maxit), float(timeout_s), _stream(stream)))
+
+
+def fe_cg_batched_results(plan: fe_batch_plan, stream=None):
+    n = plan.n_systems
+    res = (fe_cg_result * n)()
+    st = load().fe_cg_batched_results(ctypes.byref(plan), res, _stream(stream))
+    return st, [res[i] for i in range(n)]
+
+
+def fe_cg_solve_batched(mats, bs, xs, tol, maxit, krhs, work, timeout_s=0.0, stream=None):
+    n = len(mats)
+    res = (fe_cg_result * n)()
+    st = load().fe_cg_solve_batched(n, _descs(mats), _ptrs(bs), _ptrs(xs), float(tol), int(maxit),
+                                    int(krhs), float(timeout_s), _ptr(work),
+                                    work.numel() * work.element_size(), res, _stream(stream))
+    return st, [res[i] for i in range(n)]
+
+
 def fe_version() -> str:
     return load().fe_version().decode()
 
@@ -401,3 +471,37 @@ def mixed_workspace(A_lo: DeviceMatrix, device="cuda") -> torch.Tensor:
 
 def resid_workspace(device="cuda") -> torch.Tensor:
     return _alloc_bytes(RESID_WORK_BYTES, device)
+
+
+class Batch:
+    """Independent problems of different mesh sizes and boundary data, ready
+    for the batched solve.  Problems with equal mesh share one matrix (the
+    assembled matrix does not depend on the boundary values); each keeps its
+    own right-hand side and solution vector."""
+
+    def __init__(self, sizes, faces=None, fmt: str = "bcrs3", device="cuda"):
+        self.sizes = [int(n) for n in sizes]
+        self.fmt = fmt
+        self.device = torch.device(device)
+        self.reps = {}       # mesh size -> System holding the shared matrix
+        self.b, self.x = [], []
+        for i, n in enumerate(self.sizes):
+            fv = None
+            if faces is not None and faces[i] is not None:
+                fv = torch.as_tensor(faces[i], dtype=torch.float64, device=self.device)
+            s = System(n, device=self.device, face_vals=fv).build()
+            self.b.append(s.b)
+            self.x.append(torch.zeros(s.m, dtype=torch.float64, device=self.device))
+            if n not in self.reps:
+                self.reps[n] = s
+                s.matrix(fmt, "f64")
+            else:
+                del s
+        self.mats = [self.reps[n].matrix(fmt, "f64").desc for n in self.sizes]
+
+    def reset(self):
+        for x in self.x:
+            x.zero_()
+
+    def workspace(self) -> torch.Tensor:
+        return _alloc_bytes(fe_cg_batched_workspace(self.mats), self.device)
