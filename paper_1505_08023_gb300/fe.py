@@ -499,6 +499,10 @@ class Batch:
                 del s
         self.mats = [self.reps[n].matrix(fmt, "f64").desc for n in self.sizes]
 
+    def mats_for(self, fmt: str):
+        """Descriptors of the shared matrices in another storage format."""
+        return [self.reps[n].matrix(fmt, "f64").desc for n in self.sizes]
+
     def reset(self):
         for x in self.x:
             x.zero_()
