@@ -147,3 +147,18 @@ def test_batched_rejects_mixed_formats(fe):
     with pytest.raises(fe.FeError):
         fe.fe_cg_batched_plan([a.mats[0], b.mats[0]], [a.b[0], b.b[0]], [a.x[0], b.x[0]], 1,
                               a.workspace())
+
+
+def test_autotuner_choice_solves(fe):
+    from paper_1505_08023_gb300 import autotune
+    batch, faces = make_batch(fe, [8, 12, 8, 10], "bcrs3", seed=7)
+    choice = autotune.tune(batch, steps=8, repeats=1)
+    assert choice.fmt in ("bcrs3", "sell") and choice.krhs in (1, 2, 4)
+    assert autotune.tune(batch) is choice            # cached by signature
+    mats = batch.mats_for(choice.fmt)
+    st, res = fe.fe_cg_solve_batched(mats, batch.b, batch.x, 1e-10, 2000, choice.krhs,
+                                     batch.workspace())
+    assert st == fe.FE_OK
+    for i, n in enumerate([8, 12, 8, 10]):
+        sysm, k_ref, _, _ = reference(n, faces[i])
+        assert abs(res[i].iterations - k_ref) <= 1
