@@ -18,7 +18,7 @@ from . import fe
 
 FORMATS = ("bcrs3", "sell")
 KRHS = (1, 2, 4)
-BLOCKS_PER_SM = (1, 2)
+BLOCKS_PER_SM = (0, 2)   # 0: as many as fit
 
 
 @dataclass

@@ -76,20 +76,35 @@ __device__ __forceinline__ int block_of_unit(long long U, long long u, int G) {
     return (int)(((u + 1) * G - 1) / U);
 }
 
-// Unit list of the chunks holding a system marked in sh.mask.
+// Unit list of the chunks holding a system marked in sh.mask (warp 0 runs a
+// prefix sum over the chunks, 32 at a time).
 __device__ __forceinline__ void batch_plan(const BatchArgs &a, BatchShared &sh) {
     __syncthreads();
-    if (threadIdx.x == 0) {
-        long long u = 0;
-        for (int c = 0; c < a.n_chunks; ++c) {
-            sh.unit_start[c] = u;
-            const BatchChunkDev &ch = a.chunks[c];
-            bool any = false;
-            for (int j = 0; j < ch.n_rhs; ++j) any |= sh.mask[ch.first_sys + j] != 0;
-            if (any) u += ch.n_slices;
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        long long base = 0;
+        for (int c0 = 0; c0 < a.n_chunks; c0 += 32) {
+            const int c = c0 + lane;
+            long long len = 0;
+            if (c < a.n_chunks) {
+                const int f = a.chunks[c].first_sys, nr = a.chunks[c].n_rhs;
+                bool any = false;
+                for (int j = 0; j < nr; ++j) any |= sh.mask[f + j] != 0;
+                if (any) len = a.chunks[c].n_slices;
+            }
+            long long incl = len;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const long long v = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += v;
+            }
+            if (c < a.n_chunks) sh.unit_start[c] = base + incl - len;
+            base += __shfl_sync(0xffffffffu, incl, 31);
         }
-        sh.unit_start[a.n_chunks] = u;
-        sh.n_units = u;
+        if (lane == 0) {
+            sh.unit_start[a.n_chunks] = base;
+            sh.n_units = base;
+        }
     }
     __syncthreads();
 }
@@ -116,7 +131,32 @@ __device__ __forceinline__ void slice_spmm(const fe_matrix &A, int s, int lane, 
     const int32_t *c = A.d_cols + b + lane;
     if constexpr (FMT == FE_FMT_BCRS3) {
         const double *v = reinterpret_cast<const double *>(A.d_vals) + 3 * b + lane;
-        for (int k = 0; k < w; ++k) {
+        int k = 0;
+        constexpr int U = 3;
+        for (; k + U <= w; k += U) {
+            int32_t col[U];
+            double vv[U][3];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                col[u] = ld_stream(c + 32 * (k + u));
+#pragma unroll
+                for (int t = 0; t < 3; ++t) vv[u][t] = ld_stream(v + 96 * (k + u) + 32 * t);
+            }
+#pragma unroll
+            for (int j = 0; j < KRHS; ++j) {
+                if (!on[j]) continue;
+                double xx[U][3];
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+#pragma unroll
+                    for (int t = 0; t < 3; ++t) xx[u][t] = xs[j][col[u] + t];
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+#pragma unroll
+                    for (int t = 0; t < 3; ++t) acc[j] = fma(vv[u][t], xx[u][t], acc[j]);
+            }
+        }
+        for (; k < w; ++k) {
             const int32_t col = ld_stream(c + 32 * k);
             const double v0 = ld_stream(v + 96 * k), v1 = ld_stream(v + 96 * k + 32),
                          v2 = ld_stream(v + 96 * k + 64);
@@ -263,7 +303,7 @@ __device__ bool batch_pass(const BatchArgs &a, BatchShared &sh, int pass) {
 }
 
 template <int FMT, int KRHS>
-__global__ void __launch_bounds__(kBatchThreads, 2) k_cg_batched(const BatchArgs a) {
+__global__ void __launch_bounds__(kBatchThreads, KRHS <= 2 ? 4 : 2) k_cg_batched(const BatchArgs a) {
     __shared__ BatchShared sh;
     const int n = a.n_sys;
     if (threadIdx.x == 0) {
