@@ -303,7 +303,7 @@ fe_status fe_cg_solve_noalloc(const fe_matrix *A, const double *d_b, double *d_x
  *                      (caller's order; synchronises) and returns the first
  *                      non-OK status, or FE_OK.
  * fe_cg_solve_batched  plan + launch + results.
- * d_x[i]: start vectors in, solutions out.  At most FE_BATCH_MAX_SYSTEMS
+ * d_x[i] (16-byte aligned): start vectors in, solutions out.  At most FE_BATCH_MAX_SYSTEMS
  * systems; FE_ERR_ARG if a block would have to reduce more than 32 systems.
  */
 #define FE_BATCH_MAX_SYSTEMS 256

@@ -199,51 +199,48 @@ __device__ bool batch_pass(const BatchArgs &a, BatchShared &sh, int pass) {
     const long long u_begin = U > 0 ? block_start(U, blockIdx.x, G) : 0;
     const long long u_end = U > 0 ? block_start(U, blockIdx.x + 1, G) : 0;
     const int first_sys = (u_begin < u_end) ? a.chunks[chunk_of_unit(sh, a.n_chunks, u_begin)].first_sys : 0;
-    for (long long u = u_begin + warp; u < u_end; u += kCgWarps) {
-        const int c = chunk_of_unit(sh, a.n_chunks, u);
-        const BatchChunkDev &ch = a.chunks[c];
-        const int slice = (int)(u - sh.unit_start[c]);
-        const int row = slice * kSlice + lane;
-        const bool in = row < (int)ch.A.n_rows;
-        bool on[KRHS];
-        const double *xin[KRHS];
-        double acc[KRHS];
-#pragma unroll
-        for (int j = 0; j < KRHS; ++j) {
-            on[j] = j < ch.n_rhs && sh.mask[ch.first_sys + j] != 0;
-            xin[j] = nullptr;
-            if (on[j]) xin[j] = (pass == kInit) ? a.sys[ch.first_sys + j].x : a.sys[ch.first_sys + j].p;
-        }
-        if (pass == kInit || pass == kSpmv) slice_spmm<FMT, KRHS>(ch.A, slice, lane, xin, on, acc);
-#pragma unroll
-        for (int j = 0; j < KRHS; ++j) {
-            if (!on[j]) continue;
-            const int s = ch.first_sys + j;
-            const BatchSysDev &sd = a.sys[s];
-            double d0 = 0.0, d1 = 0.0;
-            if (in) {
-                if (pass == kInit) {
-                    const double bi = sd.b[row], ri = bi - acc[j];
-                    sd.r[row] = ri;
-                    sd.p[row] = ri;
-                    d0 = ri * ri;
-                    d1 = bi * bi;
-                } else if (pass == kSpmv) {
-                    sd.w[row] = acc[j];
-                    d0 = sd.p[row] * acc[j];
-                } else if (pass == kUpdateXR) {
-                    const double al = sh.coef[s];
-                    sd.x[row] = fma(al, sd.p[row], sd.x[row]);
-                    const double ri = fma(-al, sd.w[row], sd.r[row]);
-                    sd.r[row] = ri;
-                    d0 = ri * ri;
-                } else if (pass == kUpdateP) {
-                    sd.p[row] = fma(sh.coef[s], sd.p[row], sd.r[row]);
-                } else {
-                    sd.x[row] = 0.0;
-                }
+    if (pass == kInit || pass == kSpmv) {
+        // warp per slice; the chunk lookup is reused while the warp stays in one chunk
+        int c = -1;
+        long long c_lo = 0, c_hi = 0;
+        for (long long u = u_begin + warp; u < u_end; u += kCgWarps) {
+            if (u < c_lo || u >= c_hi) {
+                c = chunk_of_unit(sh, a.n_chunks, u);
+                c_lo = sh.unit_start[c];
+                c_hi = c_lo + a.chunks[c].n_slices;
             }
-            if (has_dots) {
+            const BatchChunkDev &ch = a.chunks[c];
+            const int slice = (int)(u - c_lo);
+            const int row = slice * kSlice + lane;
+            const bool in = row < (int)ch.A.n_rows;
+            bool on[KRHS];
+            const double *xin[KRHS];
+            double acc[KRHS];
+#pragma unroll
+            for (int j = 0; j < KRHS; ++j) {
+                on[j] = j < ch.n_rhs && sh.mask[ch.first_sys + j] != 0;
+                xin[j] = nullptr;
+                if (on[j]) xin[j] = (pass == kInit) ? a.sys[ch.first_sys + j].x : a.sys[ch.first_sys + j].p;
+            }
+            slice_spmm<FMT, KRHS>(ch.A, slice, lane, xin, on, acc);
+#pragma unroll
+            for (int j = 0; j < KRHS; ++j) {
+                if (!on[j]) continue;
+                const int s = ch.first_sys + j;
+                const BatchSysDev &sd = a.sys[s];
+                double d0 = 0.0, d1 = 0.0;
+                if (in) {
+                    if (pass == kInit) {
+                        const double bi = sd.b[row], ri = bi - acc[j];
+                        sd.r[row] = ri;
+                        sd.p[row] = ri;
+                        d0 = ri * ri;
+                        d1 = bi * bi;
+                    } else {
+                        sd.w[row] = acc[j];
+                        d0 = sd.p[row] * acc[j];
+                    }
+                }
                 d0 = warp_sum(d0);
                 d1 = warp_sum(d1);
                 const int t = s - first_sys;
@@ -256,6 +253,76 @@ __device__ bool batch_pass(const BatchArgs &a, BatchShared &sh, int pass) {
                     }
                 }
             }
+        }
+    } else {
+        // streaming passes: the block's unit range is a contiguous row range of
+        // each chunk it touches; all threads stream each system's rows there in
+        // 16-byte packs (row ranges start on 32-row boundaries)
+        long long u = u_begin;
+        while (u < u_end) {
+            const int c = chunk_of_unit(sh, a.n_chunks, u);
+            const BatchChunkDev &ch = a.chunks[c];
+            const long long c_lo = sh.unit_start[c];
+            const long long u_stop = (c_lo + ch.n_slices < u_end) ? c_lo + ch.n_slices : u_end;
+            const int row0 = (int)(u - c_lo) * kSlice;
+            int row1 = (int)(u_stop - c_lo) * kSlice;
+            if (row1 > (int)ch.A.n_rows) row1 = (int)ch.A.n_rows;
+            for (int j = 0; j < ch.n_rhs; ++j) {
+                const int s = ch.first_sys + j;
+                if (!sh.mask[s]) continue;
+                const BatchSysDev &sd = a.sys[s];
+                const int npk = (row1 - row0) >> 1;
+                double d0 = 0.0;
+                if (pass == kUpdateXR) {
+                    const double al = sh.coef[s];
+                    double2 *x2 = reinterpret_cast<double2 *>(sd.x + row0);
+                    double2 *r2 = reinterpret_cast<double2 *>(sd.r + row0);
+                    const double2 *p2 = reinterpret_cast<const double2 *>(sd.p + row0);
+                    const double2 *w2 = reinterpret_cast<const double2 *>(sd.w + row0);
+                    for (int q = threadIdx.x; q < npk; q += blockDim.x) {
+                        double2 xv = x2[q], rv = r2[q];
+                        const double2 pv = p2[q], wv = w2[q];
+                        xv.x = fma(al, pv.x, xv.x);
+                        xv.y = fma(al, pv.y, xv.y);
+                        rv.x = fma(-al, wv.x, rv.x);
+                        rv.y = fma(-al, wv.y, rv.y);
+                        x2[q] = xv;
+                        r2[q] = rv;
+                        d0 = fma(rv.x, rv.x, d0);
+                        d0 = fma(rv.y, rv.y, d0);
+                    }
+                    for (int row = row0 + 2 * npk + threadIdx.x; row < row1; row += blockDim.x) {
+                        sd.x[row] = fma(al, sd.p[row], sd.x[row]);
+                        const double ri = fma(-al, sd.w[row], sd.r[row]);
+                        sd.r[row] = ri;
+                        d0 = fma(ri, ri, d0);
+                    }
+                } else if (pass == kUpdateP) {
+                    const double be = sh.coef[s];
+                    double2 *p2 = reinterpret_cast<double2 *>(sd.p + row0);
+                    const double2 *r2 = reinterpret_cast<const double2 *>(sd.r + row0);
+                    for (int q = threadIdx.x; q < npk; q += blockDim.x) {
+                        double2 pv = p2[q];
+                        const double2 rv = r2[q];
+                        pv.x = fma(be, pv.x, rv.x);
+                        pv.y = fma(be, pv.y, rv.y);
+                        p2[q] = pv;
+                    }
+                    for (int row = row0 + 2 * npk + threadIdx.x; row < row1; row += blockDim.x)
+                        sd.p[row] = fma(be, sd.p[row], sd.r[row]);
+                } else {
+                    for (int row = row0 + threadIdx.x; row < row1; row += blockDim.x) sd.x[row] = 0.0;
+                }
+                if (has_dots) {
+                    d0 = warp_sum(d0);
+                    const int t = s - first_sys;
+                    if (lane == 0) {
+                        if (t >= 0 && t < kBatchMaxTouch) sh.wpart[0][warp][t] += d0;
+                        else sh.touch_overflow = 1;
+                    }
+                }
+            }
+            u = u_stop;
         }
     }
     if (!has_dots) return grid_barrier(a.ctrl, &sh.st, a.timeout_ns, -1);
@@ -501,7 +568,7 @@ fe_status fe_cg_batched_plan(int n_systems, const fe_matrix *A, const double *co
         if (st != FE_OK) return st;
         if (A[i].format != fmt || A[i].value_type != FE_VAL_F64 || A[i].n_rows != A[i].n_cols)
             return FE_ERR_ARG;
-        if (!d_b[i] || !d_x[i] || !aligned(d_b[i], 8) || !aligned(d_x[i], 8)) return FE_ERR_ARG;
+        if (!d_b[i] || !d_x[i] || !aligned(d_b[i], 8) || !aligned(d_x[i], 16)) return FE_ERR_ARG;
     }
     size_t need = 0;
     fe_status st = fe_cg_batched_workspace(n_systems, A, &need);
