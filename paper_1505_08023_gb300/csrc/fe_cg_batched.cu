@@ -171,7 +171,27 @@ __device__ __forceinline__ void slice_spmm(const fe_matrix &A, int s, int lane, 
         }
     } else {
         const double *v = reinterpret_cast<const double *>(A.d_vals) + b + lane;
-        for (int k = 0; k < w; ++k) {
+        int k = 0;
+        constexpr int U = 9;
+        for (; k + U <= w; k += U) {
+            int32_t col[U];
+            double vv[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                col[u] = ld_stream(c + 32 * (k + u));
+                vv[u] = ld_stream(v + 32 * (k + u));
+            }
+#pragma unroll
+            for (int j = 0; j < KRHS; ++j) {
+                if (!on[j]) continue;
+                double xx[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) xx[u] = xs[j][col[u]];
+#pragma unroll
+                for (int u = 0; u < U; ++u) acc[j] = fma(vv[u], xx[u], acc[j]);
+            }
+        }
+        for (; k < w; ++k) {
             const int32_t col = ld_stream(c + 32 * k);
             const double vv = ld_stream(v + 32 * k);
 #pragma unroll
