@@ -327,6 +327,72 @@ fe_status fe_cg_solve_batched(int n_systems, const fe_matrix *A, const double *c
                               double timeout_s, void *d_work, size_t work_bytes,
                               fe_cg_result *h_results, fe_stream_t stream);
 
+/*
+ * Learned warm start (the benchmark spec form X3; not in the paper).  Kernels of a
+ * 3-D convolutional encoder-decoder that maps the boundary data of a mesh to
+ * a CG start vector, and of its training.  Volumes are FP32 arrays
+ * [C][D][H][W] (W fastest) on one sample; dims arrays are {D, H, W}.
+ * Weights of a 3x3x3 layer: FP32 master [cin][27][cout] (tap t = 9 dz + 3 dy
+ * + dx); the kernels read a BF16 copy (d_w: bfloat16 bits) and accumulate in
+ * FP32.  A layer in "gather" form computes
+ *   out[co][u] = bias[co] + sum_ci sum_t W[ci][t][co] in[ci][src(u, t)]
+ * with per axis src = u + d - 1 (FE_NN_S1), 2u + d - 1 (FE_NN_S2, D_out =
+ * (D_in - 1)/2 + 1) or (u + 1 - d)/2 where integral (FE_NN_T2, D_out =
+ * 2 (D_in - 1) + 1); zero outside the input grid; `relu` clamps at zero.
+ * The data gradient of S1 is S1 with fe_nn_pack_weights(transpose=1,
+ * flip=1); of S2 it is T2 and of T2 it is S2 with (transpose=1, flip=0).
+ */
+#define FE_NN_S1 0
+#define FE_NN_S2 1
+#define FE_NN_T2 2
+
+fe_status fe_nn_conv3d(int mode, const float *d_in, int cin, const int *h_dims_in, const void *d_w,
+                       const float *d_bias, float *d_out, int cout, const int *h_dims_out,
+                       int relu, fe_stream_t stream);
+/* BF16 copies of FP32 master weights [cin][27][cout]: transpose=0 keeps the
+ * layout; transpose=1 writes [cout][27][cin] (taps reversed if flip=1). */
+fe_status fe_nn_pack_weights(const float *d_w, int cin, int cout, int transpose, int flip,
+                             void *d_out, fe_stream_t stream);
+/* Scratch of fe_nn_conv3d_weight_grad: per-split partial sums; h_splits gets
+ * the split count.  stride 1 or 2; (ca, dims_a) describe the correlation's
+ * first operand (dY for S1/S2, X for T2). */
+fe_status fe_nn_corr_workspace(int stride, int ca, const int *h_dims_a, int cb, size_t *h_bytes,
+                               int *h_splits);
+/* dW[ci][t][co] = d loss / d W of a layer given its input X and the gradient
+ * dY of its output (FP32), summed over voxel tiles in a fixed order. */
+fe_status fe_nn_conv3d_weight_grad(int mode, const float *d_x, int cin, const int *h_dims_in,
+                                   const float *d_dy, int cout, const int *h_dims_out, float *d_dw,
+                                   float *d_work, size_t work_bytes, fe_stream_t stream);
+/* db[c] = sum over the volume of dY[c] (bias gradient), fixed order. */
+fe_status fe_nn_channel_sum(const float *d_dy, int c, const int *h_dims, float *d_db,
+                            fe_stream_t stream);
+/* dy[i] = 0 where y[i] <= 0 (backward of a fused ReLU). */
+fe_status fe_nn_relu_bwd(const float *d_y, float *d_dy, size_t n, fe_stream_t stream);
+/* y += a x. */
+fe_status fe_nn_axpy(float a, const float *d_x, float *d_y, size_t n, fe_stream_t stream);
+/* 1x1x1 head out[u] = b + sum_c w[c] h[c][u] (w: c bfloat16), and its
+ * backward (d_work: (c+1) * 64 floats). */
+fe_status fe_nn_head(const float *d_h, int c, const int *h_dims, const void *d_w, const float *d_b,
+                     float *d_out, fe_stream_t stream);
+fe_status fe_nn_head_bwd(const float *d_h, int c, const int *h_dims, const void *d_w,
+                         const float *d_dout, float *d_dh, float *d_dw, float *d_db, float *d_work,
+                         size_t work_bytes, fe_stream_t stream);
+/* Mean squared error over interior nodes (bc_flag == 0): d_dpred = 2 scale
+ * (pred - target) inside, 0 on boundary nodes; d_loss_parts[n_parts] get
+ * partial sums of the squared error (n_parts blocks, fixed order). */
+fe_status fe_nn_mse(const float *d_pred, const float *d_target, const uint8_t *d_bc_flag, size_t n,
+                    float scale, float *d_dpred, float *d_loss_parts, int n_parts,
+                    fe_stream_t stream);
+/* One Adam step on FP32 master weights; lr_t includes the bias corrections. */
+fe_status fe_nn_adam(float *d_w, const float *d_g, float *d_m, float *d_v, size_t n, float lr_t,
+                     float beta1, float beta2, float eps, fe_stream_t stream);
+/* Network input from the mesh: d_x[2][m] = (boundary value or 0, boundary flag). */
+fe_status fe_warmstart_input(const uint8_t *d_bc_flag, const double *d_bc_val, size_t n, float *d_x,
+                             fe_stream_t stream);
+/* CG start vector: prescribed value on boundary nodes, the prediction inside. */
+fe_status fe_warmstart_output(const float *d_pred, const uint8_t *d_bc_flag, const double *d_bc_val,
+                              size_t n, double *d_x0, fe_stream_t stream);
+
 /* Fault injection for tests of the barrier time limit: the next fe_cg_solve
  * on the calling thread has block 0 skip its arrival at grid barrier number
  * barrier_index (0 = the barrier after the initial residual), so every

@@ -112,6 +112,24 @@ SIGNATURES = {
     "fe_cg_solve_batched": (_I32, [ctypes.c_int, ctypes.POINTER(fe_matrix), ctypes.POINTER(_VP),
                                    ctypes.POINTER(_VP), _D, ctypes.c_int, ctypes.c_int, _D, _VP, _SZ,
                                    ctypes.POINTER(fe_cg_result), _VP]),
+    "fe_nn_conv3d": (_I32, [ctypes.c_int, _VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _VP, _VP, _VP,
+                            ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int, _VP]),
+    "fe_nn_pack_weights": (_I32, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, _VP]),
+    "fe_nn_corr_workspace": (_I32, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
+                                    ctypes.POINTER(_SZ), ctypes.POINTER(ctypes.c_int)]),
+    "fe_nn_conv3d_weight_grad": (_I32, [ctypes.c_int, _VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _VP,
+                                        ctypes.c_int, ctypes.POINTER(ctypes.c_int), _VP, _VP, _SZ, _VP]),
+    "fe_nn_channel_sum": (_I32, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _VP, _VP]),
+    "fe_nn_relu_bwd": (_I32, [_VP, _VP, _SZ, _VP]),
+    "fe_nn_axpy": (_I32, [ctypes.c_float, _VP, _VP, _SZ, _VP]),
+    "fe_nn_head": (_I32, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _VP, _VP, _VP, _VP]),
+    "fe_nn_head_bwd": (_I32, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _VP, _VP, _VP, _VP, _VP,
+                              _VP, _SZ, _VP]),
+    "fe_nn_mse": (_I32, [_VP, _VP, _VP, _SZ, ctypes.c_float, _VP, _VP, ctypes.c_int, _VP]),
+    "fe_nn_adam": (_I32, [_VP, _VP, _VP, _VP, _SZ, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                          ctypes.c_float, _VP]),
+    "fe_warmstart_input": (_I32, [_VP, _VP, _SZ, _VP, _VP]),
+    "fe_warmstart_output": (_I32, [_VP, _VP, _VP, _SZ, _VP, _VP]),
     "fe_inject_barrier_stall": (_I32, [ctypes.c_int]),
     "fe_last_cuda_error": (ctypes.c_int, []),
     "fe_version": (ctypes.c_char_p, []),
@@ -326,6 +344,85 @@ def fe_cg_solve_batched(mats, bs, xs, tol, maxit, krhs, work, timeout_s=0.0, str
                                     int(krhs), float(timeout_s), _ptr(work),
                                     work.numel() * work.element_size(), res, _stream(stream))
     return st, [res[i] for i in range(n)]
+
+
+FE_NN_S1, FE_NN_S2, FE_NN_T2 = 0, 1, 2
+NN_MODES = {"s1": FE_NN_S1, "s2": FE_NN_S2, "t2": FE_NN_T2}
+
+
+def _dims(d):
+    return (ctypes.c_int * 3)(*[int(v) for v in d])
+
+
+def fe_nn_conv3d(mode, x, cin, dims_in, w_bf16, bias, y, cout, dims_out, relu, stream=None):
+    return _check("fe_nn_conv3d", load().fe_nn_conv3d(
+        int(mode), _ptr(x), int(cin), _dims(dims_in), _ptr(w_bf16), _ptr(bias), _ptr(y), int(cout),
+        _dims(dims_out), int(relu), _stream(stream)))
+
+
+def fe_nn_pack_weights(w, cin, cout, transpose, flip, out, stream=None):
+    return _check("fe_nn_pack_weights", load().fe_nn_pack_weights(
+        _ptr(w), int(cin), int(cout), int(transpose), int(flip), _ptr(out), _stream(stream)))
+
+
+def fe_nn_corr_workspace(stride, ca, dims_a, cb):
+    n = ctypes.c_size_t(0)
+    k = ctypes.c_int(0)
+    _check("fe_nn_corr_workspace", load().fe_nn_corr_workspace(
+        int(stride), int(ca), _dims(dims_a), int(cb), ctypes.byref(n), ctypes.byref(k)))
+    return n.value, k.value
+
+
+def fe_nn_conv3d_weight_grad(mode, x, cin, dims_in, dy, cout, dims_out, dw, work, stream=None):
+    return _check("fe_nn_conv3d_weight_grad", load().fe_nn_conv3d_weight_grad(
+        int(mode), _ptr(x), int(cin), _dims(dims_in), _ptr(dy), int(cout), _dims(dims_out), _ptr(dw),
+        _ptr(work), work.numel() * work.element_size(), _stream(stream)))
+
+
+def fe_nn_channel_sum(dy, c, dims, db, stream=None):
+    return _check("fe_nn_channel_sum", load().fe_nn_channel_sum(_ptr(dy), int(c), _dims(dims), _ptr(db),
+                                                                _stream(stream)))
+
+
+def fe_nn_relu_bwd(y, dy, stream=None):
+    return _check("fe_nn_relu_bwd", load().fe_nn_relu_bwd(_ptr(y), _ptr(dy), dy.numel(), _stream(stream)))
+
+
+def fe_nn_axpy(a, x, y, stream=None):
+    return _check("fe_nn_axpy", load().fe_nn_axpy(float(a), _ptr(x), _ptr(y), y.numel(), _stream(stream)))
+
+
+def fe_nn_head(h, c, dims, w_bf16, b, out, stream=None):
+    return _check("fe_nn_head", load().fe_nn_head(_ptr(h), int(c), _dims(dims), _ptr(w_bf16), _ptr(b),
+                                                  _ptr(out), _stream(stream)))
+
+
+def fe_nn_head_bwd(h, c, dims, w_bf16, dout, dh, dw, db, work, stream=None):
+    return _check("fe_nn_head_bwd", load().fe_nn_head_bwd(
+        _ptr(h), int(c), _dims(dims), _ptr(w_bf16), _ptr(dout), _ptr(dh), _ptr(dw), _ptr(db), _ptr(work),
+        work.numel() * work.element_size(), _stream(stream)))
+
+
+def fe_nn_mse(pred, target, bc_flag, scale, dpred, parts, stream=None):
+    return _check("fe_nn_mse", load().fe_nn_mse(
+        _ptr(pred), _ptr(target), _ptr(bc_flag), pred.numel(), float(scale), _ptr(dpred), _ptr(parts),
+        parts.numel(), _stream(stream)))
+
+
+def fe_nn_adam(w, g, m, v, lr_t, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    return _check("fe_nn_adam", load().fe_nn_adam(_ptr(w), _ptr(g), _ptr(m), _ptr(v), w.numel(),
+                                                  float(lr_t), float(beta1), float(beta2), float(eps),
+                                                  _stream(stream)))
+
+
+def fe_warmstart_input(bc_flag, bc_val, x, stream=None):
+    return _check("fe_warmstart_input", load().fe_warmstart_input(
+        _ptr(bc_flag), _ptr(bc_val), bc_flag.numel(), _ptr(x), _stream(stream)))
+
+
+def fe_warmstart_output(pred, bc_flag, bc_val, x0, stream=None):
+    return _check("fe_warmstart_output", load().fe_warmstart_output(
+        _ptr(pred), _ptr(bc_flag), _ptr(bc_val), bc_flag.numel(), _ptr(x0), _stream(stream)))
 
 
 def fe_version() -> str:

@@ -1,0 +1,178 @@
+"""GPU kernels of the learned warm start against the FP64 network oracle
+(oracle/nn.py), through the C ABI, and the warm start's effect on CG.
+
+Both sides use the same BF16-rounded weights (the oracle applies them in
+FP64).  FP32 accumulation of K products is bounded by 2 K 2^-24 sum |w||x|
+(forward error of a dot product), written into each check.
+"""
+import numpy as np
+import pytest
+import torch
+
+import fe_inputs
+import oracle
+from oracle import nn as onn
+
+pytestmark = pytest.mark.gpu
+U32 = 2.0 ** -24
+
+
+@pytest.fixture(scope="module")
+def fe():
+    import paper_1505_08023_gb300.fe as fe_mod
+    fe_mod.load()
+    return fe_mod
+
+
+def bf16(a):
+    return oracle.round_to_bf16(np.asarray(a, dtype=np.float32).astype(np.float64))
+
+
+def cuda32(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+CASES = [("s1", 5, 20, (9, 7, 11)), ("s2", 17, 3, (9, 7, 11)), ("t2", 6, 16, (5, 4, 6)),
+         ("s1", 2, 16, (17, 17, 17)), ("s2", 16, 32, (17, 17, 17)), ("t2", 64, 64, (3, 3, 3))]
+
+
+def layer_setup(mode, cin, cout, dims, seed):
+    g = np.random.default_rng(seed)
+    x = g.standard_normal((cin,) + dims).astype(np.float32)
+    W = bf16(0.2 * g.standard_normal((cin, 27, cout)))
+    b = g.standard_normal(cout).astype(np.float32)
+    return x, W, b
+
+
+@pytest.mark.parametrize("mode,cin,cout,dims", CASES)
+def test_conv_forward(fe, mode, cin, cout, dims):
+    x, W, b = layer_setup(mode, cin, cout, dims, 1)
+    dout = onn.out_dims(mode, dims)
+    w32 = cuda32(W)
+    w16 = torch.empty(cin * 27 * cout, dtype=torch.bfloat16, device="cuda")
+    fe.fe_nn_pack_weights(w32, cin, cout, 0, 0, w16)
+    y = torch.empty((cout,) + dout, dtype=torch.float32, device="cuda")
+    fe.fe_nn_conv3d(fe.NN_MODES[mode], cuda32(x), cin, dims, w16, cuda32(b), y, cout, dout, 0)
+    ref = onn.conv(mode, x.astype(np.float64), W, b)
+    bound = onn.conv(mode, np.abs(x).astype(np.float64), np.abs(W), np.abs(b))
+    K = cin * 27 + 1
+    assert np.all(np.abs(y.cpu().numpy() - ref) <= 2 * K * U32 * bound + 1e-30)
+    # fused ReLU
+    fe.fe_nn_conv3d(fe.NN_MODES[mode], cuda32(x), cin, dims, w16, cuda32(b), y, cout, dout, 1)
+    assert np.all(np.abs(y.cpu().numpy() - np.maximum(ref, 0)) <= 2 * K * U32 * bound + 1e-30)
+
+
+@pytest.mark.parametrize("mode,cin,cout,dims", CASES)
+def test_conv_data_gradient(fe, mode, cin, cout, dims):
+    x, W, b = layer_setup(mode, cin, cout, dims, 2)
+    dout = onn.out_dims(mode, dims)
+    dy = np.random.default_rng(3).standard_normal((cout,) + dout).astype(np.float32)
+    wt16 = torch.empty(cin * 27 * cout, dtype=torch.bfloat16, device="cuda")
+    fe.fe_nn_pack_weights(cuda32(W), cin, cout, 1, 1 if mode == "s1" else 0, wt16)
+    adj = {"s1": "s1", "s2": "t2", "t2": "s2"}[mode]
+    dx = torch.empty((cin,) + dims, dtype=torch.float32, device="cuda")
+    fe.fe_nn_conv3d(fe.NN_MODES[adj], cuda32(dy), cout, dout, wt16, None, dx, cin, dims, 0)
+    ref = onn.conv_grad_x(mode, dy.astype(np.float64), W, dims)
+    bound = onn.conv_grad_x(mode, np.abs(dy).astype(np.float64), np.abs(W), dims)
+    K = cout * 27
+    assert np.all(np.abs(dx.cpu().numpy() - ref) <= 2 * K * U32 * bound + 1e-30)
+
+
+@pytest.mark.parametrize("mode,cin,cout,dims", CASES)
+def test_conv_weight_gradient(fe, mode, cin, cout, dims):
+    x, W, b = layer_setup(mode, cin, cout, dims, 4)
+    dout = onn.out_dims(mode, dims)
+    dy = np.random.default_rng(5).standard_normal((cout,) + dout).astype(np.float32)
+    if mode == "t2":
+        need, _ = fe.fe_nn_corr_workspace(2, cin, dims, cout)
+    else:
+        need, _ = fe.fe_nn_corr_workspace(1 if mode == "s1" else 2, cout, dout, cin)
+    work = torch.empty(need // 4 + 1, dtype=torch.float32, device="cuda")
+    dw = torch.empty((cin, 27, cout), dtype=torch.float32, device="cuda")
+    fe.fe_nn_conv3d_weight_grad(fe.NN_MODES[mode], cuda32(x), cin, dims, cuda32(dy), cout, dout, dw, work)
+    ref = onn.conv_grad_w(mode, x.astype(np.float64), dy.astype(np.float64))
+    bound = onn.conv_grad_w(mode, np.abs(x).astype(np.float64), np.abs(dy).astype(np.float64))
+    K = int(np.prod(dout)) if mode != "t2" else int(np.prod(dims))
+    assert np.all(np.abs(dw.cpu().numpy() - ref) <= 2 * K * U32 * bound + 1e-30)
+    db = torch.empty(cout, dtype=torch.float32, device="cuda")
+    fe.fe_nn_channel_sum(cuda32(dy), cout, dout, db)
+    assert np.allclose(db.cpu().numpy(), dy.reshape(cout, -1).astype(np.float64).sum(axis=1),
+                       rtol=1e-5, atol=1e-4)
+
+
+def test_network_gradients_match_oracle(fe):
+    from paper_1505_08023_gb300 import warmstart as ws
+    n = 9
+    ch = (3, 4, 4, 5)
+    g = np.random.default_rng(6)
+    net = ws.WarmStartNet(n, channels=ch)
+    params = {}
+    for name, l in net.layers.items():
+        W = bf16(0.3 * g.standard_normal((l.cin, 27, l.cout)))
+        b = (0.1 * g.standard_normal(l.cout)).astype(np.float32)
+        l.w.copy_(cuda32(W))
+        l.b.copy_(cuda32(b))
+        params[name] = (W, b.astype(np.float64))
+    hw = bf16(0.5 * g.standard_normal(ch[0]))
+    net.hw.copy_(cuda32(hw))
+    net.hb.fill_(0.05)
+    params["head"] = (hw, float(np.float32(0.05)))
+    net.pack()
+    x = g.standard_normal((2, n, n, n)).astype(np.float32)
+    target = g.standard_normal((n, n, n)).astype(np.float32)
+    interior = np.zeros((n, n, n), dtype=bool)
+    interior[1:-1, 1:-1, 1:-1] = True
+    flag = torch.from_numpy((~interior).astype(np.uint8).ravel()).cuda()
+    pred = net.forward(cuda32(x))
+    dpred = net.loss_and_grad(pred, cuda32(target), flag, int(interior.sum()))
+    net.backward(dpred)
+    loss_gpu = float(net.loss_parts.sum()) / interior.sum()
+    loss, grad = onn.unet_loss_grad(params, x.astype(np.float64), target.astype(np.float64), interior)
+    assert abs(loss_gpu - loss) <= 1e-4 * abs(loss)
+    for name, l in net.layers.items():
+        gw_ref, gb_ref = grad[name]
+        gw = l.gw.cpu().numpy()
+        assert np.linalg.norm(gw - gw_ref) <= 2e-4 * np.linalg.norm(gw_ref) + 1e-8, name
+        assert np.linalg.norm(l.gb.cpu().numpy() - gb_ref) <= 2e-4 * np.linalg.norm(gb_ref) + 1e-8, name
+    assert np.linalg.norm(net.ghw.cpu().numpy() - grad["head"][0]) <= 2e-4 * np.linalg.norm(grad["head"][0])
+
+
+def test_adam_step(fe):
+    g = np.random.default_rng(7)
+    w, gr = g.standard_normal(1000).astype(np.float32), g.standard_normal(1000).astype(np.float32)
+    m, v = np.zeros(1000, np.float32), np.zeros(1000, np.float32)
+    tw, tg, tm, tv = cuda32(w), cuda32(gr), cuda32(m), cuda32(v)
+    lr_t = 1e-3 * np.sqrt(1 - 0.999) / (1 - 0.9)
+    fe.fe_nn_adam(tw, tg, tm, tv, lr_t, 0.9, 0.999, 1e-8)
+    m1 = 0.1 * gr.astype(np.float64)
+    v1 = 0.001 * gr.astype(np.float64) ** 2
+    want = w - lr_t * m1 / (np.sqrt(v1) + 1e-8)
+    assert np.allclose(tw.cpu().numpy(), want, rtol=1e-5, atol=1e-7)
+
+
+def test_training_reduces_loss_and_warm_start_saves_iterations(fe):
+    """N = 32: train on 96 CG solutions for 3 epochs, then solve 6 held-out
+    problems from x0 = 0 and from the network's x0, each to 1e-10."""
+    from paper_1505_08023_gb300 import warmstart as ws
+    N = 32
+    prob = ws.Problem(N)
+    faces = ws.face_set(100, 0, 96, N)
+    targets = ws.generate_targets(prob, faces)
+    net = ws.WarmStartNet(N + 1, channels=(8, 16, 16, 16))
+    log = ws.train(net, prob, faces, targets, epochs=3, lr=2e-3, log_every=24)
+    first, last = log[0][2], log[-1][2]
+    assert last < 0.5 * first
+    rows = ws.evaluate(net, prob, ws.face_set(200, 0, 6, N))
+    rep = ws.summarize(rows)
+    assert rep["all_converged"]
+    assert rep["mean_iters_warm"] < rep["mean_iters_cold"]
+    assert rep["max_rel_diff_vs_cold"] < 1e-6
+    # final error against the oracle on one held-out problem
+    face = ws.face_set(200, 0, 1, N)[0]
+    sysm = oracle.build_system(N, N, N, face)
+    prob.set_faces(face)
+    x0 = torch.empty(prob.sys.m, dtype=torch.float64, device="cuda")
+    ws.predict_x0(net, prob, x0)
+    r = fe.fe_cg_solve(prob.A.desc, prob.sys.b, x0, 1e-10, 5000, prob.work)
+    tr = oracle.true_relres(sysm["row_ptr"], sysm["cols"], sysm["vals"], sysm["b"], x0.cpu().numpy())
+    assert r.status == fe.FE_OK and tr <= 1.5e-10
