@@ -133,6 +133,100 @@ k_conv_fwd(const float *__restrict__ in, int cin, Dims di, const __nv_bfloat16 *
     }
 }
 
+// Stride-1 forward, register-blocked: each thread computes 4 consecutive
+// voxels along x for 16 output channels.  For a (ci, dz, dy) the 6 input
+// values x-1 .. x+4 serve all three dx taps of the 4 voxels, so one input
+// load feeds 8 FMAs and one broadcast float4 weight load feeds 16.
+constexpr int kV = 4;
+constexpr int kS1TZ = 4, kS1TY = 8, kS1TX = 8 * kV;   // 256 threads x 4 voxels
+
+__global__ void __launch_bounds__(kNnThreads)
+k_conv_fwd_s1v(const float *__restrict__ in, int cin, Dims di, const __nv_bfloat16 *__restrict__ wt,
+               const float *__restrict__ bias, float *__restrict__ out, int cout, Dims dout, int relu) {
+    constexpr int EZ = kS1TZ + 2, EY = kS1TY + 2, EX = kS1TX + 2;
+    constexpr int EV = EZ * EY * EX;
+    __shared__ float s_in[kCiChunk][EV];
+    __shared__ __align__(16) float s_w[kCiChunk][27][kCoTile];
+    const int tiles_x = (dout.w + kS1TX - 1) / kS1TX, tiles_y = (dout.h + kS1TY - 1) / kS1TY;
+    int t = blockIdx.x;
+    const int bx = t % tiles_x;
+    t /= tiles_x;
+    const int by = t % tiles_y;
+    const int bz = t / tiles_y;
+    const int co0 = blockIdx.y * kCoTile;
+    const int tx = threadIdx.x % 8, ty = (threadIdx.x / 8) % kS1TY, tz = threadIdx.x / (8 * kS1TY);
+    const int ux0 = bx * kS1TX + kV * tx, uy = by * kS1TY + ty, uz = bz * kS1TZ + tz;
+    const int oz = bz * kS1TZ - 1, oy = by * kS1TY - 1, ox = bx * kS1TX - 1;
+    float acc[kV][kCoTile];
+#pragma unroll
+    for (int v = 0; v < kV; ++v)
+#pragma unroll
+        for (int c = 0; c < kCoTile; ++c) acc[v][c] = 0.0f;
+    for (int ci0 = 0; ci0 < cin; ci0 += kCiChunk) {
+        for (int i = threadIdx.x; i < kCiChunk * EV; i += kNnThreads) {
+            const int c = i / EV, e = i % EV;
+            const int ex = e % EX, ey = (e / EX) % EY, ez = e / (EX * EY);
+            const int gx = ox + ex, gy = oy + ey, gz = oz + ez;
+            float v = 0.0f;
+            if (ci0 + c < cin && gx >= 0 && gx < di.w && gy >= 0 && gy < di.h && gz >= 0 && gz < di.d)
+                v = in[((size_t)(ci0 + c) * di.d + gz) * di.h * di.w + (size_t)gy * di.w + gx];
+            s_in[c][e] = v;
+        }
+        for (int i = threadIdx.x; i < kCiChunk * 27 * kCoTile; i += kNnThreads) {
+            const int co = i % kCoTile, tap = (i / kCoTile) % 27, c = i / (kCoTile * 27);
+            float v = 0.0f;
+            if (ci0 + c < cin && co0 + co < cout)
+                v = __bfloat162float(wt[((size_t)(ci0 + c) * 27 + tap) * cout + co0 + co]);
+            s_w[c][tap][co] = v;
+        }
+        __syncthreads();
+#pragma unroll 1
+        for (int c = 0; c < kCiChunk; ++c) {
+#pragma unroll
+            for (int dzy = 0; dzy < 9; ++dzy) {
+                const int dz = dzy / 3, dy = dzy % 3;
+                const float *row = &s_in[c][((tz + dz) * EY + ty + dy) * EX + kV * tx];
+                float xv[kV + 2];
+#pragma unroll
+                for (int k = 0; k < kV + 2; ++k) xv[k] = row[k];
+#pragma unroll
+                for (int dx = 0; dx < 3; ++dx) {
+                    const float4 *w4 = reinterpret_cast<const float4 *>(&s_w[c][dzy * 3 + dx][0]);
+#pragma unroll
+                    for (int q = 0; q < kCoTile / 4; ++q) {
+                        const float4 w = w4[q];
+#pragma unroll
+                        for (int v = 0; v < kV; ++v) {
+                            const float xin = xv[v + dx];
+                            acc[v][4 * q + 0] = fmaf(w.x, xin, acc[v][4 * q + 0]);
+                            acc[v][4 * q + 1] = fmaf(w.y, xin, acc[v][4 * q + 1]);
+                            acc[v][4 * q + 2] = fmaf(w.z, xin, acc[v][4 * q + 2]);
+                            acc[v][4 * q + 3] = fmaf(w.w, xin, acc[v][4 * q + 3]);
+                        }
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (uy < dout.h && uz < dout.d) {
+        const size_t plane = (size_t)dout.d * dout.h * dout.w;
+        const size_t vrow = ((size_t)uz * dout.h + uy) * dout.w;
+#pragma unroll
+        for (int c = 0; c < kCoTile; ++c) {
+            if (co0 + c >= cout) break;
+            const float bc = bias ? bias[co0 + c] : 0.0f;
+#pragma unroll
+            for (int v = 0; v < kV; ++v) {
+                if (ux0 + v >= dout.w) break;
+                float y = acc[v][c] + bc;
+                if (relu) y = y > 0.0f ? y : 0.0f;
+                out[(size_t)(co0 + c) * plane + vrow + ux0 + v] = y;
+            }
+        }
+    }
+}
+
 // voxel tile of the correlation kernel (A's grid); B's halo tile is (S T + 2 - (S - 1)) per axis
 __host__ __device__ constexpr int corr_tz(int S) { return 2; }
 __host__ __device__ constexpr int corr_ty(int S) { return S == 1 ? 8 : 2; }
@@ -397,8 +491,12 @@ fe_status fe_nn_conv3d(int mode, const float *d_in, int cin, const int *dims_in,
                       ((dout.d + tile_z() - 1) / tile_z());
     dim3 grid(tiles, (cout + kCoTile - 1) / kCoTile);
     cudaStream_t s = (cudaStream_t)stream;
-    if (mode == FE_NN_S1) k_conv_fwd<FE_NN_S1><<<grid, kNnThreads, 0, s>>>(d_in, cin, di, d_w, d_bias, d_out, cout, dout, relu);
-    else if (mode == FE_NN_S2) k_conv_fwd<FE_NN_S2><<<grid, kNnThreads, 0, s>>>(d_in, cin, di, d_w, d_bias, d_out, cout, dout, relu);
+    if (mode == FE_NN_S1) {
+        const int tv = ((dout.w + kS1TX - 1) / kS1TX) * ((dout.h + kS1TY - 1) / kS1TY) *
+                       ((dout.d + kS1TZ - 1) / kS1TZ);
+        k_conv_fwd_s1v<<<dim3(tv, (cout + kCoTile - 1) / kCoTile), kNnThreads, 0, s>>>(
+            d_in, cin, di, d_w, d_bias, d_out, cout, dout, relu);
+    } else if (mode == FE_NN_S2) k_conv_fwd<FE_NN_S2><<<grid, kNnThreads, 0, s>>>(d_in, cin, di, d_w, d_bias, d_out, cout, dout, relu);
     else k_conv_fwd<FE_NN_T2><<<grid, kNnThreads, 0, s>>>(d_in, cin, di, d_w, d_bias, d_out, cout, dout, relu);
     FE_TRY_LAUNCH();
     return FE_OK;
