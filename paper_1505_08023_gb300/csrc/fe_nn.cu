@@ -17,6 +17,7 @@
 // are correlations R[a][b][t] = sum_z A[a][z] B[b][s z + d - 1], split over
 // voxel tiles and summed in a fixed order.  Weights are used in BF16 (rounded
 // from FP32 master weights), all accumulation is FP32.
+#include <cooperative_groups.h>
 #include <cuda_bf16.h>
 
 #include "fe_common.cuh"
@@ -227,45 +228,159 @@ k_conv_fwd_s1v(const float *__restrict__ in, int cin, Dims di, const __nv_bfloat
     }
 }
 
-// voxel tile of the correlation kernel (A's grid); B's halo tile is (S T + 2 - (S - 1)) per axis
-__host__ __device__ constexpr int corr_tz(int S) { return 2; }
-__host__ __device__ constexpr int corr_ty(int S) { return S == 1 ? 8 : 2; }
-__host__ __device__ constexpr int corr_tx(int S) { return 8; }
+// Transposed stride-2 forward by output parity class.  Output u = 2v + p
+// (p = 0 or 1 per axis) receives, per axis, tap d = 1 from input v when p = 0,
+// and taps d = 0 (input v + 1) and d = 2 (input v) when p = 1.  A block works
+// on one class (blockIdx.z), so every thread runs the same 1..8 taps with no
+// parity test; each thread computes 4 consecutive v along x x 16 channels.
+constexpr int kT2TZ = 4, kT2TY = 8, kT2TX = 8 * kV;
 
-// Correlation R[a][b][t] = sum_z A[a][z] B[b][S z + d_t - 1] over a voxel
-// tile, for a 16 x 16 tile of (a, b); one thread per (a, b), 27 accumulators.
-// Partials per split go to part[split][a][b][t].
-template <int S>
 __global__ void __launch_bounds__(kNnThreads)
-k_corr(const float *__restrict__ A, int ca, Dims da, const float *__restrict__ B, int cb, Dims dbg,
-       float *__restrict__ part, int n_split) {
-    constexpr int TZ = corr_tz(S), TY = corr_ty(S), TX = corr_tx(S);
-    constexpr int EZ = S * TZ + 2 - (S - 1), EY = S * TY + 2 - (S - 1), EX = S * TX + 2 - (S - 1);
+k_conv_fwd_t2p(const float *__restrict__ in, int cin, Dims di, const __nv_bfloat16 *__restrict__ wt,
+               const float *__restrict__ bias, float *__restrict__ out, int cout, Dims dout, int relu) {
+    constexpr int EZ = kT2TZ + 1, EY = kT2TY + 1, EX = kT2TX + 1;
     constexpr int EV = EZ * EY * EX;
-    constexpr int NV = TZ * TY * TX;
-    __shared__ float s_a[16][NV];
-    __shared__ float s_b[16][EV];
-    const int ia = threadIdx.x / 16, ib = threadIdx.x % 16;
-    const int a0 = (blockIdx.y / ((cb + 15) / 16)) * 16, b0 = (blockIdx.y % ((cb + 15) / 16)) * 16;
+    __shared__ float s_in[kCiChunk][EV];
+    __shared__ __align__(16) float s_w[kCiChunk][27][kCoTile];
+    const int pz = (blockIdx.z >> 2) & 1, py = (blockIdx.z >> 1) & 1, px = blockIdx.z & 1;
+    // class sub-grid sizes: v with 2v + p < D
+    const int cz = (dout.d - pz + 1) / 2, cy = (dout.h - py + 1) / 2, cx = (dout.w - px + 1) / 2;
+    const int tiles_x = (cx + kT2TX - 1) / kT2TX, tiles_y = (cy + kT2TY - 1) / kT2TY;
+    // the grid is sized for the largest class (p = 0); smaller classes skip extra tiles
+    const int full_x = ((dout.w + 1) / 2 + kT2TX - 1) / kT2TX, full_y = ((dout.h + 1) / 2 + kT2TY - 1) / kT2TY;
+    int t = blockIdx.x;
+    const int bx = t % full_x;
+    t /= full_x;
+    const int by = t % full_y;
+    const int bz = t / full_y;
+    if (bx >= tiles_x || by >= tiles_y || bz * kT2TZ >= cz) return;
+    const int co0 = blockIdx.y * kCoTile;
+    const int tx = threadIdx.x % 8, ty = (threadIdx.x / 8) % kT2TY, tz = threadIdx.x / (8 * kT2TY);
+    const int v0z = bz * kT2TZ, v0y = by * kT2TY, v0x = bx * kT2TX;
+    const int nz = pz ? 2 : 1, ny = py ? 2 : 1, nxt = px ? 2 : 1;
+    float acc[kV][kCoTile];
+#pragma unroll
+    for (int v = 0; v < kV; ++v)
+#pragma unroll
+        for (int c = 0; c < kCoTile; ++c) acc[v][c] = 0.0f;
+    for (int ci0 = 0; ci0 < cin; ci0 += kCiChunk) {
+        for (int i = threadIdx.x; i < kCiChunk * EV; i += kNnThreads) {
+            const int c = i / EV, e = i % EV;
+            const int ex = e % EX, ey = (e / EX) % EY, ez = e / (EX * EY);
+            const int gx = v0x + ex, gy = v0y + ey, gz = v0z + ez;
+            float v = 0.0f;
+            if (ci0 + c < cin && gx < di.w && gy < di.h && gz < di.d)
+                v = in[((size_t)(ci0 + c) * di.d + gz) * di.h * di.w + (size_t)gy * di.w + gx];
+            s_in[c][e] = v;
+        }
+        for (int i = threadIdx.x; i < kCiChunk * 27 * kCoTile; i += kNnThreads) {
+            const int co = i % kCoTile, tap = (i / kCoTile) % 27, c = i / (kCoTile * 27);
+            float v = 0.0f;
+            if (ci0 + c < cin && co0 + co < cout)
+                v = __bfloat162float(wt[((size_t)(ci0 + c) * 27 + tap) * cout + co0 + co]);
+            s_w[c][tap][co] = v;
+        }
+        __syncthreads();
+#pragma unroll 1
+        for (int c = 0; c < kCiChunk; ++c) {
+            for (int iz = 0; iz < nz; ++iz) {
+                const int dz = pz ? 2 * iz : 1, oz = pz ? 1 - iz : 0;
+                for (int iy = 0; iy < ny; ++iy) {
+                    const int dy = py ? 2 * iy : 1, oy = py ? 1 - iy : 0;
+                    const float *row = &s_in[c][((tz + oz) * EY + ty + oy) * EX + kV * tx];
+                    float xv[kV + 1];
+#pragma unroll
+                    for (int k = 0; k < kV + 1; ++k) xv[k] = row[k];
+                    for (int ix = 0; ix < nxt; ++ix) {
+                        const int dx = px ? 2 * ix : 1, ox = px ? 1 - ix : 0;
+                        const float4 *w4 = reinterpret_cast<const float4 *>(&s_w[c][dz * 9 + dy * 3 + dx][0]);
+#pragma unroll
+                        for (int q = 0; q < kCoTile / 4; ++q) {
+                            const float4 w = w4[q];
+#pragma unroll
+                            for (int v = 0; v < kV; ++v) {
+                                const float xin = ox ? xv[v + 1] : xv[v];
+                                acc[v][4 * q + 0] = fmaf(w.x, xin, acc[v][4 * q + 0]);
+                                acc[v][4 * q + 1] = fmaf(w.y, xin, acc[v][4 * q + 1]);
+                                acc[v][4 * q + 2] = fmaf(w.z, xin, acc[v][4 * q + 2]);
+                                acc[v][4 * q + 3] = fmaf(w.w, xin, acc[v][4 * q + 3]);
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+    const int vz = v0z + tz, vy = v0y + ty;
+    if (vz < cz && vy < cy) {
+        const int uz = 2 * vz + pz, uy = 2 * vy + py;
+        const size_t plane = (size_t)dout.d * dout.h * dout.w;
+        const size_t vrow = ((size_t)uz * dout.h + uy) * dout.w;
+#pragma unroll
+        for (int c = 0; c < kCoTile; ++c) {
+            if (co0 + c >= cout) break;
+            const float bc = bias ? bias[co0 + c] : 0.0f;
+#pragma unroll
+            for (int v = 0; v < kV; ++v) {
+                const int vx = v0x + kV * tx + v;
+                if (vx >= cx) break;
+                float y = acc[v][c] + bc;
+                if (relu) y = y > 0.0f ? y : 0.0f;
+                out[(size_t)(co0 + c) * plane + vrow + 2 * vx + px] = y;
+            }
+        }
+    }
+}
+
+// Weight gradient, register-blocked: R[a][b][t] = sum_z A[a][z] B[b][S z + d_t - 1].
+// Each thread accumulates 4 consecutive a x one b x 27 taps; a block has
+// ag a-groups x bt b's x zs voxel sub-splits (ag bt zs = 256), fitted to the
+// channel counts so that few threads idle when a layer has few channels.
+// The sub-splits are summed in the block; each block (or each warp, when a
+// block has more than 32 sub-splits) writes one partial; k_corr_reduce sums them.
+struct CorrShape {
+    int ag, bt, zs;
+};
+constexpr int kCorrMaxB = 16;
+
+template <int S>
+__global__ void __launch_bounds__(kNnThreads, 2)   // 2 blocks/SM: one stages while the other computes
+k_corr4(const float *__restrict__ A, int ca, Dims da, const float *__restrict__ B, int cb, Dims dbg,
+        float *__restrict__ part, int n_split, CorrShape cs) {
+    constexpr int TZ = 2, TY = (S == 1) ? 8 : 2, TX = 8;
+    constexpr int EZ = S * TZ + 2 - (S - 1), EY = S * TY + 2 - (S - 1), EX = S * TX + 2 - (S - 1);
+    constexpr int EV = EZ * EY * EX, NV = TZ * TY * TX;
+    constexpr int MAXA = 16, MAXB = kCorrMaxB;  // 34 KB (S = 1) / 29 KB (S = 2) of static shared memory
+    __shared__ __align__(16) float s_a[NV][MAXA];   // [voxel][a]: one float4 per a-group
+    __shared__ float s_b[MAXB][EV];
+    const int at = 4 * cs.ag;
+    const int tid = threadIdx.x;
+    const int zsub = tid % cs.zs, rest = tid / cs.zs;
+    const int ib = rest % cs.bt, ig = rest / cs.bt;
+    const int n_bt = (cb + cs.bt - 1) / cs.bt;
+    const int a0 = (blockIdx.y / n_bt) * at, b0 = (blockIdx.y % n_bt) * cs.bt;
     const int tiles_x = (da.w + TX - 1) / TX, tiles_y = (da.h + TY - 1) / TY, tiles_z = (da.d + TZ - 1) / TZ;
     const int n_tiles = tiles_x * tiles_y * tiles_z;
-    float acc[27];
+    float acc[4][27];
 #pragma unroll
-    for (int t = 0; t < 27; ++t) acc[t] = 0.0f;
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int t = 0; t < 27; ++t) acc[k][t] = 0.0f;
     for (int tile = blockIdx.x; tile < n_tiles; tile += n_split) {
         const int bx = tile % tiles_x, by = (tile / tiles_x) % tiles_y, bz = tile / (tiles_x * tiles_y);
         const int z0 = bz * TZ, y0 = by * TY, x0 = bx * TX;
-        for (int i = threadIdx.x; i < 16 * NV; i += kNnThreads) {
-            const int c = i / NV, e = i % NV;
+        for (int i = tid; i < NV * MAXA; i += kNnThreads) {
+            const int e = i / MAXA, c = i % MAXA;
             const int ex = e % TX, ey = (e / TX) % TY, ez = e / (TX * TY);
             const int gx = x0 + ex, gy = y0 + ey, gz = z0 + ez;
             float v = 0.0f;
-            if (a0 + c < ca && gx < da.w && gy < da.h && gz < da.d)
+            if (c < at && a0 + c < ca && gx < da.w && gy < da.h && gz < da.d)
                 v = A[((size_t)(a0 + c) * da.d + gz) * da.h * da.w + (size_t)gy * da.w + gx];
-            s_a[c][e] = v;
+            s_a[e][c] = v;
         }
         const int oz = S * z0 - 1, oy = S * y0 - 1, ox = S * x0 - 1;
-        for (int i = threadIdx.x; i < 16 * EV; i += kNnThreads) {
+        for (int i = tid; i < cs.bt * EV; i += kNnThreads) {
             const int c = i / EV, e = i % EV;
             const int ex = e % EX, ey = (e / EX) % EY, ez = e / (EX * EY);
             const int gx = ox + ex, gy = oy + ey, gz = oz + ez;
@@ -275,54 +390,130 @@ k_corr(const float *__restrict__ A, int ca, Dims da, const float *__restrict__ B
             s_b[c][e] = v;
         }
         __syncthreads();
-        for (int e = 0; e < NV; ++e) {
-            const float av = s_a[ia][e];
+        for (int e = zsub; e < NV; e += cs.zs) {
+            const float4 av = *reinterpret_cast<const float4 *>(&s_a[e][4 * ig]);
             const int ex = e % TX, ey = (e / TX) % TY, ez = e / (TX * TY);
             const float *bb = &s_b[ib][((S * ez) * EY + S * ey) * EX + S * ex];
 #pragma unroll
             for (int t = 0; t < 27; ++t) {
                 const int dz = t / 9, dy = (t / 3) % 3, dx = t % 3;
-                acc[t] = fmaf(av, bb[(dz * EY + dy) * EX + dx], acc[t]);
+                const float bv = bb[(dz * EY + dy) * EX + dx];
+                acc[0][t] = fmaf(av.x, bv, acc[0][t]);
+                acc[1][t] = fmaf(av.y, bv, acc[1][t]);
+                acc[2][t] = fmaf(av.z, bv, acc[2][t]);
+                acc[3][t] = fmaf(av.w, bv, acc[3][t]);
             }
         }
         __syncthreads();
     }
-    if (a0 + ia < ca && b0 + ib < cb) {
-        float *p = part + (((size_t)blockIdx.x * ca + a0 + ia) * cb + b0 + ib) * 27;
+    // Sum the sub-splits: they are the low log2(zs) bits of the thread index,
+    // so within a warp a fixed xor butterfly combines them; when zs > 32 each
+    // warp's sum is its own partial (zs / 32 per block).
+    for (int off = 1; off < cs.zs && off < 32; off <<= 1) {
 #pragma unroll
-        for (int t = 0; t < 27; ++t) p[t] = acc[t];
+        for (int k = 0; k < 4; ++k)
+#pragma unroll
+            for (int t = 0; t < 27; ++t) acc[k][t] += __shfl_xor_sync(0xffffffffu, acc[k][t], off);
     }
+    if ((zsub & 31) != 0) return;
+    const int per_block = cs.zs > 32 ? cs.zs / 32 : 1;
+    const int split = blockIdx.x * per_block + (zsub >> 5);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int a = a0 + 4 * ig + k, b = b0 + ib;
+        if (a < ca && b < cb) {
+            float *p = part + (((size_t)split * ca + a) * cb + b) * 27;
+#pragma unroll
+            for (int t = 0; t < 27; ++t) p[t] = acc[k][t];
+        }
+    }
+}
+
+// ag a-groups of 4 channels (1, 2 or 4), bt b-channels (power of 2, at most
+// kCorrMaxB so the B halo tile fits static shared memory), zs voxel sub-splits
+// filling 256 threads (a power of 2, so the sub-splits are the low thread bits).
+static CorrShape corr_shape(int stride, int ca, int cb) {
+    (void)stride;
+    CorrShape cs;
+    cs.ag = ca > 8 ? 4 : (ca > 4 ? 2 : 1);
+    int bt = 1;
+    while (bt < cb && bt < kCorrMaxB && cs.ag * bt * 2 <= kNnThreads) bt *= 2;
+    cs.bt = bt;
+    cs.zs = kNnThreads / (cs.ag * cs.bt);
+    return cs;
 }
 
 // R = sum over splits (fixed order); scattered into dW[ci][t][co]:
 // a_is_co = 1: R[a=co][b=ci][t]; a_is_co = 0: R[a=ci][b=co][t].
-__global__ void k_corr_reduce(const float *__restrict__ part, int n_split, int ca, int cb,
-                              int a_is_co, float *__restrict__ dw) {
+// A block covers 32 consecutive outputs (one per lane); warp w sums the
+// partials of its contiguous share in order, then warp 0 adds the eight warp
+// sums in warp order.
+__global__ void __launch_bounds__(kNnThreads)
+k_corr_reduce(const float *__restrict__ part, int n_split, int ca, int cb, int a_is_co, float *__restrict__ dw) {
+    __shared__ float red[kNnThreads / 32][32];
     const int n = ca * cb * 27;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        float s = 0.0f;
-        for (int k = 0; k < n_split; ++k) s += part[(size_t)k * n + i];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int i = blockIdx.x * 32 + lane;
+    const int per = (n_split + kNnThreads / 32 - 1) / (kNnThreads / 32);
+    const int k0 = warp * per, k1 = min(n_split, k0 + per);
+    float s = 0.0f;
+    if (i < n)
+        for (int k = k0; k < k1; ++k) s += part[(size_t)k * n + i];
+    red[warp][lane] = s;
+    __syncthreads();
+    if (warp == 0 && i < n) {
+        float tot = 0.0f;
+#pragma unroll
+        for (int w = 0; w < kNnThreads / 32; ++w) tot += red[w][lane];
         const int t = i % 27, b = (i / 27) % cb, a = i / (27 * cb);
         const int ci = a_is_co ? b : a, co = a_is_co ? a : b;
         const int cout = a_is_co ? ca : cb;
-        dw[((size_t)ci * 27 + t) * cout + co] = s;
+        dw[((size_t)ci * 27 + t) * cout + co] = tot;
     }
 }
 
-// Bias gradient db[c] = sum over the volume of dy[c] (one block per channel, fixed order).
-__global__ void k_channel_sum(const float *__restrict__ dy, size_t plane, float *__restrict__ db) {
-    __shared__ float red[kNnThreads / 32];
-    const float *p = dy + (size_t)blockIdx.x * plane;
-    float s = 0.0f;
-    for (size_t i = threadIdx.x; i < plane; i += blockDim.x) s += p[i];
-    s = warp_sum(s);
+// Bias gradient db[c] = sum over the volume of dy[c].  One cluster of 8
+// blocks per channel: block r sums the r-th eighth of the volume (four
+// interleaved accumulators per thread, then warps, then warps in order), and
+// block 0 adds the eight block sums in rank order through distributed shared
+// memory, so the result is fixed for a given volume size.
+constexpr int kSumCluster = 8, kSumThreads = 1024;
+
+__global__ void __cluster_dims__(kSumCluster, 1, 1) __launch_bounds__(kSumThreads)
+k_channel_sum(const float *__restrict__ dy, size_t plane, float *__restrict__ db) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    __shared__ float red[kSumThreads / 32];
+    __shared__ float block_total;
+    const unsigned rank = cluster.block_rank();
+    const size_t c = blockIdx.x / kSumCluster;
+    const size_t chunk = (plane + kSumCluster - 1) / kSumCluster;
+    const size_t lo = rank * chunk, hi = min(plane, lo + chunk);
+    const float *p = dy + c * plane;
+    float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
+    size_t i = lo + threadIdx.x;
+    for (; i + 3 * kSumThreads < hi; i += 4 * kSumThreads) {
+        s0 += p[i];
+        s1 += p[i + kSumThreads];
+        s2 += p[i + 2 * kSumThreads];
+        s3 += p[i + 3 * kSumThreads];
+    }
+    for (; i < hi; i += kSumThreads) s0 += p[i];
+    float s = warp_sum((s0 + s1) + (s2 + s3));
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
     __syncthreads();
     if (threadIdx.x == 0) {
         float t = 0.0f;
-        for (int w = 0; w < kNnThreads / 32; ++w) t += red[w];
-        db[blockIdx.x] = t;
+        for (int w = 0; w < kSumThreads / 32; ++w) t += red[w];
+        block_total = t;
     }
+    cluster.sync();
+    if (rank == 0 && threadIdx.x == 0) {
+        float t = 0.0f;
+        for (int r = 0; r < kSumCluster; ++r) t += *cluster.map_shared_rank(&block_total, r);
+        db[c] = t;
+    }
+    cluster.sync();   // peers keep their shared memory until block 0 has read it
 }
 
 // Weight copies in BF16: forward (same layout) or transposed for the data
@@ -496,8 +687,14 @@ fe_status fe_nn_conv3d(int mode, const float *d_in, int cin, const int *dims_in,
                        ((dout.d + kS1TZ - 1) / kS1TZ);
         k_conv_fwd_s1v<<<dim3(tv, (cout + kCoTile - 1) / kCoTile), kNnThreads, 0, s>>>(
             d_in, cin, di, d_w, d_bias, d_out, cout, dout, relu);
-    } else if (mode == FE_NN_S2) k_conv_fwd<FE_NN_S2><<<grid, kNnThreads, 0, s>>>(d_in, cin, di, d_w, d_bias, d_out, cout, dout, relu);
-    else k_conv_fwd<FE_NN_T2><<<grid, kNnThreads, 0, s>>>(d_in, cin, di, d_w, d_bias, d_out, cout, dout, relu);
+    } else if (mode == FE_NN_S2) {
+        k_conv_fwd<FE_NN_S2><<<grid, kNnThreads, 0, s>>>(d_in, cin, di, d_w, d_bias, d_out, cout, dout, relu);
+    } else {
+        const int cz = (dout.d + 1) / 2, cy = (dout.h + 1) / 2, cx = (dout.w + 1) / 2;  // largest class
+        const int tv = ((cx + kT2TX - 1) / kT2TX) * ((cy + kT2TY - 1) / kT2TY) * ((cz + kT2TZ - 1) / kT2TZ);
+        k_conv_fwd_t2p<<<dim3(tv, (cout + kCoTile - 1) / kCoTile, 8), kNnThreads, 0, s>>>(
+            d_in, cin, di, d_w, d_bias, d_out, cout, dout, relu);
+    }
     FE_TRY_LAUNCH();
     return FE_OK;
 }
@@ -505,15 +702,17 @@ fe_status fe_nn_conv3d(int mode, const float *d_in, int cin, const int *dims_in,
 fe_status fe_nn_corr_workspace(int stride, int ca, const int *dims_a, int cb, size_t *h_bytes,
                                int *h_splits) {
     if ((stride != 1 && stride != 2) || ca < 1 || cb < 1 || !dims_ok(dims_a) || !h_bytes) return FE_ERR_ARG;
-    const int TZ = corr_tz(stride), TY = corr_ty(stride), TX = corr_tx(stride);
+    const int TZ = 2, TY = stride == 1 ? 8 : 2, TX = 8;
     const long long tiles = (long long)((dims_a[2] + TX - 1) / TX) * ((dims_a[1] + TY - 1) / TY) *
                             ((dims_a[0] + TZ - 1) / TZ);
-    const int pairs = ((ca + 15) / 16) * ((cb + 15) / 16);
-    long long split = (long long)(sm_count() > 0 ? sm_count() : 132) * 4 / pairs;
+    const CorrShape cs = corr_shape(stride, ca, cb);
+    const long long blocks_yz = (long long)((ca + 4 * cs.ag - 1) / (4 * cs.ag)) * ((cb + cs.bt - 1) / cs.bt);
+    long long split = (long long)(sm_count() > 0 ? sm_count() : 132) * 4 / blocks_yz;
     if (split < 1) split = 1;
     if (split > tiles) split = tiles;
-    *h_bytes = (size_t)split * ca * cb * 27 * sizeof(float);
-    if (h_splits) *h_splits = (int)split;
+    const int per_block = cs.zs > 32 ? cs.zs / 32 : 1;
+    *h_bytes = (size_t)split * per_block * ca * cb * 27 * sizeof(float);
+    if (h_splits) *h_splits = (int)(split * per_block);
     return FE_OK;
 }
 
@@ -532,16 +731,18 @@ fe_status fe_nn_conv3d_weight_grad(int mode, const float *d_x, int cin, const in
     const int *da = t2 ? dims_in : dims_out, *dbv = t2 ? dims_out : dims_in;
     const int stride = mode == FE_NN_S1 ? 1 : 2;
     size_t need = 0;
-    int split = 1;
-    fe_status st = fe_nn_corr_workspace(stride, ca, da, cb, &need, &split);
+    int total_splits = 1;
+    fe_status st = fe_nn_corr_workspace(stride, ca, da, cb, &need, &total_splits);
     if (st != FE_OK) return st;
     if (work_bytes < need) return FE_ERR_WORKSPACE;
     cudaStream_t s = (cudaStream_t)stream;
-    dim3 grid(split, ((ca + 15) / 16) * ((cb + 15) / 16));
-    if (stride == 1) k_corr<1><<<grid, kNnThreads, 0, s>>>(A, ca, dims_of(da), B, cb, dims_of(dbv), d_work, split);
-    else k_corr<2><<<grid, kNnThreads, 0, s>>>(A, ca, dims_of(da), B, cb, dims_of(dbv), d_work, split);
+    const CorrShape cs = corr_shape(stride, ca, cb);
+    const int split = total_splits / (cs.zs > 32 ? cs.zs / 32 : 1);
+    dim3 grid(split, ((ca + 4 * cs.ag - 1) / (4 * cs.ag)) * ((cb + cs.bt - 1) / cs.bt));
+    if (stride == 1) k_corr4<1><<<grid, kNnThreads, 0, s>>>(A, ca, dims_of(da), B, cb, dims_of(dbv), d_work, split, cs);
+    else k_corr4<2><<<grid, kNnThreads, 0, s>>>(A, ca, dims_of(da), B, cb, dims_of(dbv), d_work, split, cs);
     FE_TRY_LAUNCH();
-    k_corr_reduce<<<grid1((size_t)ca * cb * 27), kNnThreads, 0, s>>>(d_work, split, ca, cb, t2 ? 0 : 1, d_dw);
+    k_corr_reduce<<<(ca * cb * 27 + 31) / 32, kNnThreads, 0, s>>>(d_work, total_splits, ca, cb, t2 ? 0 : 1, d_dw);
     FE_TRY_LAUNCH();
     return FE_OK;
 }
@@ -549,7 +750,7 @@ fe_status fe_nn_conv3d_weight_grad(int mode, const float *d_x, int cin, const in
 fe_status fe_nn_channel_sum(const float *d_dy, int c, const int *dims, float *d_db, fe_stream_t stream) {
     if (!d_dy || !d_db || c < 1 || !dims_ok(dims)) return FE_ERR_ARG;
     const size_t plane = (size_t)dims[0] * dims[1] * dims[2];
-    k_channel_sum<<<c, kNnThreads, 0, (cudaStream_t)stream>>>(d_dy, plane, d_db);
+    k_channel_sum<<<c * kSumCluster, kSumThreads, 0, (cudaStream_t)stream>>>(d_dy, plane, d_db);
     FE_TRY_LAUNCH();
     return FE_OK;
 }
@@ -606,7 +807,7 @@ fe_status fe_nn_head_bwd(const float *d_h, int c, const int *dims, const void *d
     FE_TRY_LAUNCH();
     k_rows_sum<<<1, 64, 0, s>>>(d_work, c, nb, d_dw);
     FE_TRY_LAUNCH();
-    k_channel_sum<<<1, kNnThreads, 0, s>>>(d_dout, plane, d_db);
+    k_channel_sum<<<kSumCluster, kSumThreads, 0, s>>>(d_dout, plane, d_db);
     FE_TRY_LAUNCH();
     return FE_OK;
 }
