@@ -246,6 +246,23 @@ class Problem:
             self.sys.assemble()        # b for these faces (the matrix does not change)
         fe.fe_warmstart_input(self.sys.bc_flag, self.sys.bc_val, self.x_in)
 
+    def add_residual_grad(self, dpred, weight: float):
+        """Add the gradient of weight * sum((A e)^2) / (n d^2) to the MSE
+        gradient dpred = 2 e / n, where e = pred - target is zero on boundary
+        nodes and d = 8h/3 is the interior diagonal of A (so the term is
+        dimensionless).  With q = A dpred = 2 A e / n and g = A q, that
+        gradient is (weight / d^2) g; rows of boundary nodes are identity rows,
+        so g stays zero there.  FP32 SELL SpMV."""
+        if getattr(self, "A32", None) is None:
+            self.A32 = self.sys.matrix("sell", "f32")
+            self.q = torch.empty(self.sys.m, dtype=torch.float32, device=self.dev)
+            self.g = torch.empty_like(self.q)
+        flat = dpred.view(-1)
+        fe.fe_spmv_f32(self.A32.desc, flat, self.q)
+        fe.fe_spmv_f32(self.A32.desc, self.q, self.g)
+        d = 8.0 / (3.0 * self.N)
+        fe.fe_nn_axpy(weight / (d * d), self.g, flat)
+
 
 def face_set(base_seed: int, first: int, count: int, N: int):
     import fe_inputs
@@ -269,17 +286,28 @@ def generate_targets(prob: Problem, faces, tol=1e-10, chunk=64):
     return out
 
 
-def train(net: WarmStartNet, prob: Problem, faces, targets, epochs=1, lr=1e-3, log_every=0):
+def train(net: WarmStartNet, prob: Problem, faces, targets, epochs=1, lr=1e-3, log_every=0,
+          lr_final=None, res_weight=0.0):
+    """Adam over the samples in a fixed shuffled order, one sample per step.
+    With lr_final the step size follows a cosine from lr to lr_final; with
+    res_weight > 0 the loss adds the scaled squared residual of the error
+    (Problem.add_residual_grad), the quantity CG's stopping test measures."""
     losses = []
     n = len(faces)
     order = np.random.default_rng(0).permutation(n)
+    total = epochs * n
     for ep in range(epochs):
         for k, i in enumerate(order):
             prob.set_faces(faces[i], need_b=False)
             pred = net.forward(prob.x_in)
             dpred = net.loss_and_grad(pred, targets[i], prob.sys.bc_flag, prob.n_interior)
+            if res_weight > 0.0:
+                prob.add_residual_grad(dpred, res_weight)
             net.backward(dpred)
-            net.adam_step(lr)
+            step_lr = lr
+            if lr_final is not None:
+                step_lr = lr_final + 0.5 * (lr - lr_final) * (1.0 + math.cos(math.pi * (ep * n + k) / total))
+            net.adam_step(step_lr)
             if log_every and (k % log_every == 0 or k == n - 1):
                 losses.append((ep, k, float(net.loss_parts.sum()) / prob.n_interior))
     return losses
@@ -348,7 +376,7 @@ def summarize(rows):
 
 
 def run(N=128, n_train=2000, n_test=200, epochs=1, lr=1e-3, device="cuda", seed_train=1000,
-        seed_test=2000):
+        seed_test=2000, lr_final=None, res_weight=0.0):
     t0 = time.time()
     prob = Problem(N, device)
     faces_tr = face_set(seed_train, 0, n_train, N)
@@ -358,7 +386,8 @@ def run(N=128, n_train=2000, n_test=200, epochs=1, lr=1e-3, device="cuda", seed_
     torch.cuda.synchronize()
     t2 = time.time()
     net = WarmStartNet(N + 1, device=device)
-    losses = train(net, prob, faces_tr, targets, epochs=epochs, lr=lr, log_every=max(1, n_train // 10))
+    losses = train(net, prob, faces_tr, targets, epochs=epochs, lr=lr, log_every=max(1, n_train // 10),
+                   lr_final=lr_final, res_weight=res_weight)
     torch.cuda.synchronize()
     t3 = time.time()
     del targets
@@ -366,6 +395,7 @@ def run(N=128, n_train=2000, n_test=200, epochs=1, lr=1e-3, device="cuda", seed_
     t4 = time.time()
     rep = summarize(rows)
     rep.update({"N": N, "n_train": n_train, "n_test": n_test, "epochs": epochs, "lr": lr,
+                "lr_final": lr_final, "res_weight": res_weight,
                 "train_seeds": f"PCG64({seed_train}, 0..{n_train - 1})",
                 "test_seeds": f"PCG64({seed_test}, 0..{n_test - 1})",
                 "s_faces": round(t1 - t0, 2), "s_targets": round(t2 - t1, 2),
@@ -381,9 +411,11 @@ def main():
     ap.add_argument("--test", type=int, default=200)
     ap.add_argument("--epochs", type=int, default=1)
     ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--lr-final", type=float, default=None)
+    ap.add_argument("--res-weight", type=float, default=0.0)
     ap.add_argument("--out", default=None)
     a = ap.parse_args()
-    rep = run(a.n, a.train, a.test, a.epochs, a.lr)
+    rep = run(a.n, a.train, a.test, a.epochs, a.lr, lr_final=a.lr_final, res_weight=a.res_weight)
     s = json.dumps(rep)
     print(s)
     if a.out:

@@ -176,3 +176,27 @@ def test_training_reduces_loss_and_warm_start_saves_iterations(fe):
     r = fe.fe_cg_solve(prob.A.desc, prob.sys.b, x0, 1e-10, 5000, prob.work)
     tr = oracle.true_relres(sysm["row_ptr"], sysm["cols"], sysm["vals"], sysm["b"], x0.cpu().numpy())
     assert r.status == fe.FE_OK and tr <= 1.5e-10
+
+
+def test_residual_loss_gradient(fe):
+    """Problem.add_residual_grad adds (w / d^2) A (A dpred) with the FP32
+    matrix; checked against the oracle's assembled CSR matrix in FP64."""
+    from paper_1505_08023_gb300 import warmstart as ws
+    N = 8
+    prob = ws.Problem(N)
+    face = ws.face_set(300, 0, 1, N)[0]
+    prob.set_faces(face)
+    sysm = oracle.build_system(N, N, N, face)
+    g = np.random.default_rng(8)
+    e = g.standard_normal(prob.sys.m)
+    e[sysm["bc_flag"] != 0] = 0.0
+    e = e.astype(np.float32)
+    dpred = cuda32(e)
+    prob.add_residual_grad(dpred, 0.5)
+    rp, cols, vals = sysm["row_ptr"], sysm["cols"], sysm["vals"]
+    A = lambda v: oracle.spmv_csr(rp, cols, vals, v)
+    d = 8.0 / (3.0 * N)
+    want = e.astype(np.float64) + 0.5 / d ** 2 * A(A(e.astype(np.float64)))
+    got = dpred.cpu().numpy().astype(np.float64)
+    assert np.all(got[sysm["bc_flag"] != 0] == 0.0)
+    assert np.linalg.norm(got - want) <= 1e-5 * np.linalg.norm(want)
