@@ -25,6 +25,8 @@ Reported (one JSON line on rank 0):
   cpu_baseline the CPU oracle, single core, on a bounded sample of the same
                workload (a few CG iterations of the N = 256 system), scaled
                to the solve's iteration count
+  cpu_parallel the paper's CG (CRS and variable-length BCRS) with OpenMP on
+               all host cores, on the same system, sampled and scaled alike
 With --gpus N > 1 (torchrun) every rank solves its own copy (replicas,
 weak scaling); the path needs no collective on one mesh per GPU.
 ``--impl reference`` times the CPU oracle (the only reference that exists
@@ -177,7 +179,9 @@ def spmv_bytes(fmt: str, m: int, n_slices: int, n_stored: int, nnz: int, vec_byt
 
 def cpu_oracle_sample(n: int, iters_sample: int, iters_to_tol: int):
     """Oracle (single core) on the N-mesh: build the system (untimed setup),
-    time `iters_sample` CG steps, scale to the iteration count to 1e-10."""
+    time `iters_sample` CG steps, scale to the iteration count to 1e-10.
+    Returns the baseline entry and the oracle's system (reused by the
+    multi-core leg)."""
     import oracle
     t0 = time.perf_counter()
     sysm = oracle.build_system(n, n, n)
@@ -190,7 +194,30 @@ def cpu_oracle_sample(n: int, iters_sample: int, iters_to_tol: int):
             "sample": (f"oracle (plain C, 1 thread) on the N={n} system: {iters_sample} CG "
                        f"iterations timed ({dt:.1f} s, {per_it:.3f} s/iteration) and scaled to "
                        f"{iters_to_tol} iterations; its mesh+pattern+assembly took "
-                       f"{setup:.1f} s (untimed setup)")}
+                       f"{setup:.1f} s (untimed setup)")}, sysm
+
+
+def cpu_parallel_sample(sysm, n: int, iters_sample: int, iters_to_tol: int):
+    """The paper's CG on all host cores (OpenMP, CRS and the paper's
+    variable-length BCRS) on the oracle's system: `iters_sample` CG steps
+    timed inside the C code, scaled to the iteration count to 1e-10."""
+    import oracle
+    out = {"unit": "s", "kind": "openmp", "cores_online": os.cpu_count()}
+    t0 = time.perf_counter()
+    ptr, jas, off = oracle.csr_to_bcrs(sysm["row_ptr"], sysm["cols"])
+    conv = time.perf_counter() - t0
+    for fmt, args in (("csr", (sysm["row_ptr"], sysm["cols"], sysm["vals"])),
+                      ("bcrs", (ptr, jas, sysm["vals"]))):
+        kw = {"offsets": off} if fmt == "bcrs" else {}
+        _, it, _, st, sec, thr = oracle.omp_cg(fmt, sysm["b"], *args, tol=0.0, maxit=iters_sample, **kw)
+        per_it = sec / max(it, 1)
+        out[fmt] = {"value": round(per_it * iters_to_tol, 4), "s_per_iteration": round(per_it, 5),
+                    "threads": thr}
+        out["cores"] = thr
+    out["sample"] = (f"OpenMP CG (gcc -O3 -fopenmp, {out['cores']} threads) on the oracle's N={n} "
+                     f"system, {iters_sample} steps per storage form timed and scaled to "
+                     f"{iters_to_tol} steps; BCRS index build {conv:.1f} s (untimed)")
+    return out
 
 
 # ------------------------------------------------------------------ reference arm
@@ -252,6 +279,8 @@ def main():
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--format", choices=["csr", "sell", "bcrs3"], default="bcrs3")
     ap.add_argument("--cpu-iters", type=int, default=8, help="oracle CG iterations in the CPU sample")
+    ap.add_argument("--cpu-parallel-iters", type=int, default=40,
+                    help="OpenMP CG iterations per storage form in the multi-core CPU sample (0: skip)")
     ap.add_argument("--ref-iters", type=int, default=2, help="oracle CG iterations per reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-spmv", action="store_true")
@@ -481,9 +510,12 @@ def main():
     launches_per_step = 7   # mesh 1, assembly 2, slice plan 2, fill 1, CG 1 (timed FP64 steps)
 
     if rank == 0:
-        cpu = None
+        cpu = cpu_par = None
         if world == 1 and not args.no_cpu_baseline:
-            cpu = cpu_oracle_sample(n, args.cpu_iters, int(round(it)))
+            cpu, sysm = cpu_oracle_sample(n, args.cpu_iters, int(round(it)))
+            if args.cpu_parallel_iters > 0:
+                cpu_par = cpu_parallel_sample(sysm, n, args.cpu_parallel_iters, int(round(it)))
+            del sysm
         line = {"metric": METRIC, "value": round(cg_ms * 1e-3, 6), "unit": "s",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": round(step_ms, 3), "higher_is_better": False, "scaling": "weak",
@@ -493,7 +525,7 @@ def main():
                 "cg_ms_per_iteration": round(cg_ms / max(it, 1), 4),
                 "phase_ms": {k: round(statistics.mean(v), 3) for k, v in phases.items()},
                 "roofline": roofline, "mixed": mixed, "batched": batched, "spmv": spmv, "e2e": e2e,
-                "cpu_baseline": cpu,
+                "cpu_baseline": cpu, "cpu_parallel": cpu_par,
                 "clocks": clocks, "gpu_launches": launches_per_step * args.steps,
                 "wall_s_timed_region": round(wall, 3)}
         print(json.dumps(line), flush=True)

@@ -277,3 +277,59 @@ def round_to_bf16(v: np.ndarray) -> np.ndarray:
     lsb = (bits >> drop) & np.uint64(1)
     rounded = (bits + half + lsb) & ~np.uint64((1 << 45) - 1)
     return rounded.view(np.float64)
+
+
+# ----------------------------------------------------------------------------
+# Multi-core CPU CG (fe_cpu_omp.c): a timing comparison for the benchmark's
+# CPU leg, not part of the oracle's reference arithmetic.
+# ----------------------------------------------------------------------------
+
+_OMP_SRC = os.path.join(_HERE, "fe_cpu_omp.c")
+_OMP_LIB_PATH = os.path.join(_BUILD_DIR, "liboracle_omp.so")
+_omp_lib = None
+
+
+def build_omp(force: bool = False) -> str:
+    """Compile fe_cpu_omp.c into oracle/_build/liboracle_omp.so (gcc -O3 -fopenmp)."""
+    os.makedirs(_BUILD_DIR, exist_ok=True)
+    if (not force and os.path.exists(_OMP_LIB_PATH)
+            and os.path.getmtime(_OMP_LIB_PATH) >= os.path.getmtime(_OMP_SRC)):
+        return _OMP_LIB_PATH
+    tmp = _OMP_LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O3", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _OMP_SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _OMP_LIB_PATH)
+    return _OMP_LIB_PATH
+
+
+def _load_omp():
+    global _omp_lib
+    with _lock:
+        if _omp_lib is not None:
+            return _omp_lib
+        lib = ctypes.CDLL(build_omp())
+        lib.omp_cg.restype = ctypes.c_int
+        lib.omp_cg.argtypes = [ctypes.c_int64, ctypes.c_int, _i32p, _i32p, ctypes.c_void_p, _f64p,
+                               _f64p, _f64p, ctypes.c_double, ctypes.c_int,
+                               ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
+                               ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]
+        _omp_lib = lib
+        return lib
+
+
+def omp_cg(fmt: str, b, ptr, idx, vals, offsets=None, x0=None, tol=1e-10, maxit=1000):
+    """Multi-core CG in CRS (fmt "csr": ptr = row_ptr, idx = cols) or the
+    paper's BCRS (fmt "bcrs": ptr, idx = jas, offsets from csr_to_bcrs; vals =
+    the CRS values).  Returns (x, iterations, relres, status, seconds, threads)."""
+    lib = _load_omp()
+    m = b.shape[0]
+    x = np.zeros(m) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+    f = {"csr": 0, "bcrs": 1}[fmt]
+    if f == 1 and offsets is None:
+        raise ValueError("BCRS needs offsets")
+    off = None if offsets is None else np.ascontiguousarray(offsets, dtype=np.int32)
+    it, rel, sec, thr = ctypes.c_int(0), ctypes.c_double(0.0), ctypes.c_double(0.0), ctypes.c_int(0)
+    st = lib.omp_cg(m, f, ptr, idx, None if off is None else off.ctypes.data, vals,
+                    np.ascontiguousarray(b), x, float(tol), int(maxit), ctypes.byref(it),
+                    ctypes.byref(rel), ctypes.byref(sec), ctypes.byref(thr))
+    return x, it.value, rel.value, st, sec.value, thr.value
