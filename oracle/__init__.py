@@ -19,6 +19,9 @@ Parity pins (each checked by ``tests/test_oracle_*.py``):
   * Dirichlet system     -- symmetric, Cholesky succeeds (SPD)
   * SpMV (CRS and BCRS)  -- dense matrix-vector product on small meshes
   * CG                   -- dense direct solve on meshes up to 4^3
+  * single-reduction CG   -- Krylov termination (k distinct eigenvalues -> k
+                            steps), textbook CG's iterates step by step,
+                            dense direct solve, status codes
   * whole solve          -- series solution: centre value 1/6, O(h^2) error
 """
 from __future__ import annotations
@@ -90,6 +93,8 @@ def _load():
         lib.orc_cg.restype = i32
         lib.orc_cg.argtypes = [i64, _i32p, _i32p, _f64p, _f64p, _f64p, f64, i32,
                                ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
+        lib.orc_cg_sr.restype = i32
+        lib.orc_cg_sr.argtypes = lib.orc_cg.argtypes
         lib.orc_true_relres.restype = f64
         lib.orc_true_relres.argtypes = [i64, _i32p, _i32p, _f64p, _f64p, _f64p]
         _lib = lib
@@ -228,6 +233,18 @@ def cg(row_ptr, cols, vals, b, x0=None, tol=1e-10, maxit=1000):
     rel = ctypes.c_double(0.0)
     st = lib.orc_cg(m, row_ptr, cols, vals, np.ascontiguousarray(b), x, float(tol),
                     int(maxit), ctypes.byref(it), ctypes.byref(rel))
+    return x, it.value, rel.value, st
+
+
+def cg_sr(row_ptr, cols, vals, b, x0=None, tol=1e-10, maxit=1000):
+    """Single-reduction (Chronopoulos-Gear) CG; returns (x, iterations, relres, status)."""
+    lib = _load()
+    m = b.shape[0]
+    x = np.zeros(m) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+    it = ctypes.c_int(0)
+    rel = ctypes.c_double(0.0)
+    st = lib.orc_cg_sr(m, row_ptr, cols, vals, np.ascontiguousarray(b), x, float(tol),
+                       int(maxit), ctypes.byref(it), ctypes.byref(rel))
     return x, it.value, rel.value, st
 
 

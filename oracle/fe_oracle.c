@@ -461,6 +461,86 @@ done:
     return status;
 }
 
+/*
+ * Single-reduction CG (Chronopoulos and Gear, 1989; the s = 1 member of their
+ * s-step family).  In exact arithmetic it produces the iterates of orc_cg.
+ * A step performs one product w = A r and forms both inner products it needs,
+ * gamma = (r, r) and delta = (w, r), from the same vectors; the curvature
+ * p.Ap is not formed directly but follows from
+ *     p_k . A p_k = delta_k - beta_k gamma_k / alpha_{k-1}      (k >= 1),
+ * and s = A p is carried by the recurrence s_k = w_k + beta_k s_{k-1}.
+ * Step k:  beta_k = gamma_k / gamma_{k-1} (beta_0 = 0),
+ *          alpha_k = gamma_k / (p_k . A p_k),
+ *          p = r + beta p,  s = w + beta s,  x = x + alpha p,  r = r - alpha s,
+ *          w = A r,  gamma = (r, r),  delta = (w, r).
+ * Stopping rule and status codes as orc_cg (gamma is the recursive r.r).
+ */
+int orc_cg_sr(int64_t m, const int32_t *row_ptr, const int32_t *cols, const double *vals,
+              const double *b, double *x, double tol, int maxit,
+              int *iters_out, double *relres_out)
+{
+    double *r = (double *)malloc((size_t)m * sizeof(double));
+    double *w = (double *)malloc((size_t)m * sizeof(double));
+    double *p = (double *)calloc((size_t)m, sizeof(double));
+    double *s = (double *)calloc((size_t)m, sizeof(double));
+    int status = 1, k = 0;
+    double bb = orc_dot(m, b, b);
+    double gamma = 0.0, gamma_prev = 0.0, delta = 0.0, alpha_prev = 0.0;
+
+    if (bb == 0.0) {
+        for (int64_t i = 0; i < m; ++i)
+            x[i] = 0.0;
+        status = 0;
+        goto done;
+    }
+    orc_spmv_csr(m, row_ptr, cols, vals, x, w);
+    orc_waxpby(m, 1.0, b, -1.0, w, r);              /* r = b - A x */
+    orc_spmv_csr(m, row_ptr, cols, vals, r, w);     /* w = A r */
+    gamma = orc_dot(m, r, r);
+    delta = orc_dot(m, w, r);
+
+    while (1) {
+        if (gamma <= tol * tol * bb) {
+            status = 0;
+            break;
+        }
+        if (k >= maxit) {
+            status = 1;
+            break;
+        }
+        double beta = 0.0, curv = delta;
+        if (k > 0) {
+            beta = gamma / gamma_prev;
+            curv = delta - beta * gamma / alpha_prev;
+        }
+        if (!(curv > 0.0) || !isfinite(curv)) {
+            status = 2;
+            break;
+        }
+        double alpha = gamma / curv;
+        orc_waxpby(m, 1.0, r, beta, p, p);          /* p = r + beta p */
+        orc_waxpby(m, 1.0, w, beta, s, s);          /* s = w + beta s */
+        orc_waxpby(m, 1.0, x, alpha, p, x);         /* x = x + alpha p */
+        orc_waxpby(m, 1.0, r, -alpha, s, r);        /* r = r - alpha s */
+        orc_spmv_csr(m, row_ptr, cols, vals, r, w); /* w = A r */
+        gamma_prev = gamma;
+        gamma = orc_dot(m, r, r);
+        delta = orc_dot(m, w, r);
+        alpha_prev = alpha;
+        ++k;
+    }
+done:
+    if (iters_out)
+        *iters_out = k;
+    if (relres_out)
+        *relres_out = (bb == 0.0) ? 0.0 : sqrt(gamma / bb);
+    free(r);
+    free(w);
+    free(p);
+    free(s);
+    return status;
+}
+
 /* True relative residual ||b - A x|| / ||b|| (0 when b = 0 and A x = 0). */
 double orc_true_relres(int64_t m, const int32_t *row_ptr, const int32_t *cols,
                        const double *vals, const double *b, const double *x)
