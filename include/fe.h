@@ -204,6 +204,28 @@ fe_status fe_cg_solve(const fe_matrix *A, const double *d_b, double *d_x, double
                       double timeout_s, void *d_work, size_t work_bytes,
                       fe_cg_result *h_result, fe_stream_t stream);
 
+/* Workspace of fe_cg_solve_sr: four vectors (r, p, w, s) of 32 * n_slices
+ * doubles plus the reduction and barrier block. */
+fe_status fe_cg_sr_workspace(const fe_matrix *A, size_t *h_bytes);
+
+/*
+ * Single-reduction CG (Chronopoulos and Gear, 1989, s = 1): the same Krylov
+ * iterates as fe_cg_solve in exact arithmetic (the paper's CG module,
+ * Sec. 1), reorganised so that each step needs one grid reduction: w = A r
+ * with r.r and w.r fused into the SpMV epilogue, then
+ *   beta = gamma_k / gamma_{k-1},  p.Ap = delta_k - beta gamma_k / alpha_{k-1},
+ *   alpha = gamma_k / p.Ap,  p = r + beta p,  s = w + beta s (s = A p),
+ *   x += alpha p,  r -= alpha s.
+ * Two grid barriers per step instead of three (faster where barriers
+ * dominate: small meshes); one extra vector and one extra FMA per row.
+ * Arguments, stopping rule, timeout, determinism and result as fe_cg_solve
+ * (d_work: fe_cg_sr_workspace() bytes).  FE_ERR_BREAKDOWN when the curvature
+ * recurrence gives p.Ap <= 0.
+ */
+fe_status fe_cg_solve_sr(const fe_matrix *A, const double *d_b, double *d_x, double tol, int maxit,
+                         double timeout_s, void *d_work, size_t work_bytes,
+                         fe_cg_result *h_result, fe_stream_t stream);
+
 /* Result of a mixed-precision solve. */
 typedef struct fe_mixed_result {
     int32_t status;            /* fe_status of the solve */
@@ -394,7 +416,7 @@ fe_status fe_warmstart_output(const float *d_pred, const uint8_t *d_bc_flag, con
                               size_t n, double *d_x0, fe_stream_t stream);
 
 /* Fault injection for tests of the barrier time limit: the next fe_cg_solve
- * on the calling thread has block 0 skip its arrival at grid barrier number
+ * or fe_cg_solve_sr on the calling thread has block 0 skip its arrival at grid barrier number
  * barrier_index (0 = the barrier after the initial residual), so every
  * block's bounded wait runs out and the solve returns FE_ERR_TIMEOUT with
  * the GPU context intact.  -1 clears it.  Nothing faults, traps or hangs. */

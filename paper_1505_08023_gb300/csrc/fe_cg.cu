@@ -170,6 +170,12 @@ fe_status launch_cg_f32(const CgArgs<float> &args, cudaStream_t s) { return disp
 
 static thread_local long long g_stall_barrier = -1;
 
+long long take_stall_barrier() {
+    const long long v = g_stall_barrier;
+    g_stall_barrier = -1;
+    return v;
+}
+
 }  // namespace fe
 
 using namespace fe;
@@ -217,10 +223,9 @@ fe_status fe_cg_solve(const fe_matrix *A, const double *d_b, double *d_x, double
     args.maxit = maxit;
     const double tmo = timeout_s > 0.0 ? timeout_s : 2.0;
     args.timeout_ns = (long long)(tmo * 1e9);
-    args.stall_barrier = g_stall_barrier;
+    args.stall_barrier = take_stall_barrier();
     args.x0_zero = 0;
     args.x64 = nullptr;
-    g_stall_barrier = -1;
 
     FE_TRY_CUDA(cudaMemsetAsync(args.ctrl, 0, sizeof(CgCtrl), s));
     st = dispatch_cg(args, s);

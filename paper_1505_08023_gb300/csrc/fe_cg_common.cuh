@@ -321,4 +321,8 @@ static inline fe_status dispatch_resid(const fe_matrix &A, const double *b, cons
 // of the restarted mixed-precision mode.
 fe_status launch_cg_f32(const CgArgs<float> &args, cudaStream_t s);
 
+// Barrier index armed by fe_inject_barrier_stall (test hook), consumed by the
+// next solve that takes it (-1: none).  Defined in fe_cg.cu.
+long long take_stall_barrier();
+
 }  // namespace fe

@@ -95,6 +95,9 @@ SIGNATURES = {
     "fe_cg_workspace": (_I32, [ctypes.POINTER(fe_matrix), ctypes.POINTER(_SZ)]),
     "fe_cg_solve": (_I32, [ctypes.POINTER(fe_matrix), _VP, _VP, _D, ctypes.c_int, _D, _VP, _SZ,
                            ctypes.POINTER(fe_cg_result), _VP]),
+    "fe_cg_sr_workspace": (_I32, [ctypes.POINTER(fe_matrix), ctypes.POINTER(_SZ)]),
+    "fe_cg_solve_sr": (_I32, [ctypes.POINTER(fe_matrix), _VP, _VP, _D, ctypes.c_int, _D, _VP, _SZ,
+                              ctypes.POINTER(fe_cg_result), _VP]),
     "fe_true_relres": (_I32, [ctypes.POINTER(fe_matrix), _VP, _VP, _VP, _SZ,
                               ctypes.POINTER(_D), _VP]),
     "fe_cg_mixed_workspace": (_I32, [ctypes.POINTER(fe_matrix), ctypes.POINTER(_SZ)]),
@@ -245,6 +248,23 @@ def fe_cg_solve(A: fe_matrix, b, x, tol, maxit, work, timeout_s=0.0, stream=None
                             ctypes.byref(res), _stream(stream))
     if check and st not in (FE_OK,):
         raise FeError("fe_cg_solve", st)
+    return res
+
+
+def fe_cg_sr_workspace(A: fe_matrix) -> int:
+    n = ctypes.c_size_t(0)
+    _check("fe_cg_sr_workspace", load().fe_cg_sr_workspace(ctypes.byref(A), ctypes.byref(n)))
+    return n.value
+
+
+def fe_cg_solve_sr(A: fe_matrix, b, x, tol, maxit, work, timeout_s=0.0, stream=None,
+                   check=True) -> fe_cg_result:
+    res = fe_cg_result()
+    st = load().fe_cg_solve_sr(ctypes.byref(A), _ptr(b), _ptr(x), float(tol), int(maxit),
+                               float(timeout_s), _ptr(work), work.numel() * work.element_size(),
+                               ctypes.byref(res), _stream(stream))
+    if check and st not in (FE_OK,):
+        raise FeError("fe_cg_solve_sr", st)
     return res
 
 
@@ -560,6 +580,10 @@ class System:
 
 def cg_workspace(A: DeviceMatrix, device="cuda") -> torch.Tensor:
     return _alloc_bytes(fe_cg_workspace(A.desc), device)
+
+
+def sr_workspace(A: DeviceMatrix, device="cuda") -> torch.Tensor:
+    return _alloc_bytes(fe_cg_sr_workspace(A.desc), device)
 
 
 def mixed_workspace(A_lo: DeviceMatrix, device="cuda") -> torch.Tensor:
