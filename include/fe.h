@@ -219,8 +219,9 @@ fe_status fe_cg_sr_workspace(const fe_matrix *A, size_t *h_bytes);
  * Two grid barriers per step instead of three (faster where barriers
  * dominate: small meshes); one extra vector and one extra FMA per row.
  * Arguments, stopping rule, timeout, determinism and result as fe_cg_solve
- * (d_work: fe_cg_sr_workspace() bytes).  FE_ERR_BREAKDOWN when the curvature
- * recurrence gives p.Ap <= 0.
+ * (d_work: fe_cg_sr_workspace() bytes).  When the curvature recurrence gives
+ * p.Ap <= 0 (rounding near convergence) the step restarts the direction
+ * (beta = 0, p.Ap = r.Ar); FE_ERR_BREAKDOWN when r.Ar <= 0.
  */
 fe_status fe_cg_solve_sr(const fe_matrix *A, const double *d_b, double *d_x, double tol, int maxit,
                          double timeout_s, void *d_work, size_t work_bytes,
@@ -317,6 +318,9 @@ fe_status fe_cg_solve_noalloc(const fe_matrix *A, const double *d_b, double *d_x
  *
  * fe_cg_batched_plan   checks the systems, groups them, writes the work tables
  *                      into d_work and fills *h_plan (synchronises `stream`).
+ *                      method: FE_BATCH_TEXTBOOK (three grid barriers per
+ *                      step) or FE_BATCH_SINGLE_REDUCTION (the recurrences of
+ *                      fe_cg_solve_sr, two barriers per step).
  *                      blocks_per_sm: 0 = the most that fit.
  * fe_cg_batched_launch enqueues the solve (a memset and one cooperative
  *                      kernel; no host synchronisation, no allocation), so it
@@ -324,13 +328,15 @@ fe_status fe_cg_solve_noalloc(const fe_matrix *A, const double *d_b, double *d_x
  * fe_cg_batched_results copies the per-system results into h_results[i]
  *                      (caller's order; synchronises) and returns the first
  *                      non-OK status, or FE_OK.
- * fe_cg_solve_batched  plan + launch + results.
+ * fe_cg_solve_batched  plan (FE_BATCH_TEXTBOOK) + launch + results.
  * d_x[i] (16-byte aligned): start vectors in, solutions out.  At most FE_BATCH_MAX_SYSTEMS
  * systems; FE_ERR_ARG if a block would have to reduce more than 32 systems.
  */
 #define FE_BATCH_MAX_SYSTEMS 256
+#define FE_BATCH_TEXTBOOK 0
+#define FE_BATCH_SINGLE_REDUCTION 1
 typedef struct fe_batch_plan {
-    int32_t format, krhs, n_systems, n_chunks, grid, max_blocks;
+    int32_t format, krhs, n_systems, n_chunks, grid, max_blocks, method;
     void *d_work;
     size_t work_bytes;
     int32_t slot_of[FE_BATCH_MAX_SYSTEMS];  /* caller's index -> internal slot */
@@ -338,8 +344,9 @@ typedef struct fe_batch_plan {
 
 fe_status fe_cg_batched_workspace(int n_systems, const fe_matrix *A, size_t *h_bytes);
 fe_status fe_cg_batched_plan(int n_systems, const fe_matrix *A, const double *const *d_b,
-                             double *const *d_x, int krhs, int blocks_per_sm, void *d_work,
-                             size_t work_bytes, fe_batch_plan *h_plan, fe_stream_t stream);
+                             double *const *d_x, int krhs, int method, int blocks_per_sm,
+                             void *d_work, size_t work_bytes, fe_batch_plan *h_plan,
+                             fe_stream_t stream);
 fe_status fe_cg_batched_launch(const fe_batch_plan *plan, double tol, int maxit, double timeout_s,
                                fe_stream_t stream);
 fe_status fe_cg_batched_results(const fe_batch_plan *plan, fe_cg_result *h_results,

@@ -474,6 +474,11 @@ done:
  *          p = r + beta p,  s = w + beta s,  x = x + alpha p,  r = r - alpha s,
  *          w = A r,  gamma = (r, r),  delta = (w, r).
  * Stopping rule and status codes as orc_cg (gamma is the recursive r.r).
+ * Safeguard: in finite precision the curvature recurrence can lose its sign
+ * near convergence (the subtraction cancels); when it gives p.Ap <= 0 (or a
+ * non-finite value) the step restarts the direction instead -- beta = 0, so
+ * p = r, s = w and p.Ap = delta = r.Ar, positive for an SPD matrix -- and only
+ * delta <= 0 is a breakdown.
  */
 int orc_cg_sr(int64_t m, const int32_t *row_ptr, const int32_t *cols, const double *vals,
               const double *b, double *x, double tol, int maxit,
@@ -512,6 +517,10 @@ int orc_cg_sr(int64_t m, const int32_t *row_ptr, const int32_t *cols, const doub
         if (k > 0) {
             beta = gamma / gamma_prev;
             curv = delta - beta * gamma / alpha_prev;
+            if (!(curv > 0.0) || !isfinite(curv)) {   /* restart the direction */
+                beta = 0.0;
+                curv = delta;
+            }
         }
         if (!(curv > 0.0) || !isfinite(curv)) {
             status = 2;

@@ -14,6 +14,12 @@
 // warps' partials are summed in warp order.  No atomics: reruns give the same
 // bits.  All systems step in lockstep; each has its own alpha, beta, stopping
 // test and status, as fe_cg_solve would give it.
+//
+// Two step forms (template SR): textbook CG (passes SpMV w = A p with p.w,
+// x/r update with r.r, p update: three barriers per step) and the
+// single-reduction form of fe_cg_solve_sr (SpMV w = A r with r.r and w.r, then
+// one streaming pass p = r + beta p, s = w + beta s, x += alpha p,
+// r -= alpha s: two barriers per step).
 #include <vector>
 #include <algorithm>
 
@@ -27,7 +33,7 @@ constexpr int kBatchThreads = kCgThreads;
 
 struct BatchSysDev {
     const double *b;
-    double *x, *r, *p, *w;
+    double *x, *r, *p, *w, *s;   // s = A p (single-reduction form only)
     int chunk;
     int pad;
 };
@@ -67,6 +73,7 @@ struct BatchShared {
     int iters[kBatchMaxSystems];
     double rr[kBatchMaxSystems], bb[kBatchMaxSystems];
     double coef[kBatchMaxSystems];     // alpha or beta of the current pass
+    double coef2[kBatchMaxSystems];    // beta of the single-reduction update
     double red[2][kBatchMaxSystems];   // reduced dot products of the last pass
     double wpart[2][kCgWarps][kBatchMaxTouch];
 };
@@ -201,25 +208,26 @@ __device__ __forceinline__ void slice_spmm(const fe_matrix &A, int s, int lane, 
     }
 }
 
-enum BatchPass { kInit = 0, kSpmv = 1, kUpdateXR = 2, kUpdateP = 3, kZeroX = 4 };
+enum BatchPass { kInit = 0, kSpmv = 1, kUpdateXR = 2, kUpdateP = 3, kZeroX = 4, kSpmvR = 5,
+                 kUpdateSR = 6 };
 
 // One pass over the block's units for the systems in sh.mask.  Passes with a
 // dot product leave the per-system block partials in global memory
 // (part[round][v][block][t]); returns false if a barrier gave up.
-template <int FMT, int KRHS>
+template <int FMT, int KRHS, bool SR>
 __device__ bool batch_pass(const BatchArgs &a, BatchShared &sh, int pass) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int G = gridDim.x;
     batch_plan(a, sh);
     const long long U = sh.n_units;
-    const bool has_dots = pass == kInit || pass == kSpmv || pass == kUpdateXR;
+    const bool has_dots = pass == kInit || pass == kSpmv || pass == kUpdateXR || pass == kSpmvR;
     for (int i = threadIdx.x; i < 2 * kCgWarps * kBatchMaxTouch; i += blockDim.x)
         (&sh.wpart[0][0][0])[i] = 0.0;
     __syncthreads();
     const long long u_begin = U > 0 ? block_start(U, blockIdx.x, G) : 0;
     const long long u_end = U > 0 ? block_start(U, blockIdx.x + 1, G) : 0;
     const int first_sys = (u_begin < u_end) ? a.chunks[chunk_of_unit(sh, a.n_chunks, u_begin)].first_sys : 0;
-    if (pass == kInit || pass == kSpmv) {
+    if (pass == kInit || pass == kSpmv || pass == kSpmvR) {
         // warp per slice; the chunk lookup is reused while the warp stays in one chunk
         int c = -1;
         long long c_lo = 0, c_hi = 0;
@@ -240,7 +248,10 @@ __device__ bool batch_pass(const BatchArgs &a, BatchShared &sh, int pass) {
             for (int j = 0; j < KRHS; ++j) {
                 on[j] = j < ch.n_rhs && sh.mask[ch.first_sys + j] != 0;
                 xin[j] = nullptr;
-                if (on[j]) xin[j] = (pass == kInit) ? a.sys[ch.first_sys + j].x : a.sys[ch.first_sys + j].p;
+                if (on[j])
+                    xin[j] = (pass == kInit) ? a.sys[ch.first_sys + j].x
+                                             : (pass == kSpmvR ? a.sys[ch.first_sys + j].r
+                                                               : a.sys[ch.first_sys + j].p);
             }
             slice_spmm<FMT, KRHS>(ch.A, slice, lane, xin, on, acc);
 #pragma unroll
@@ -253,9 +264,19 @@ __device__ bool batch_pass(const BatchArgs &a, BatchShared &sh, int pass) {
                     if (pass == kInit) {
                         const double bi = sd.b[row], ri = bi - acc[j];
                         sd.r[row] = ri;
-                        sd.p[row] = ri;
+                        if (SR) {
+                            sd.p[row] = 0.0;
+                            sd.s[row] = 0.0;
+                        } else {
+                            sd.p[row] = ri;
+                        }
                         d0 = ri * ri;
                         d1 = bi * bi;
+                    } else if (pass == kSpmvR) {
+                        const double ri = sd.r[row];
+                        sd.w[row] = acc[j];
+                        d0 = ri * ri;
+                        d1 = acc[j] * ri;
                     } else {
                         sd.w[row] = acc[j];
                         d0 = sd.p[row] * acc[j];
@@ -316,6 +337,37 @@ __device__ bool batch_pass(const BatchArgs &a, BatchShared &sh, int pass) {
                         const double ri = fma(-al, sd.w[row], sd.r[row]);
                         sd.r[row] = ri;
                         d0 = fma(ri, ri, d0);
+                    }
+                } else if (pass == kUpdateSR) {
+                    const double al = sh.coef[s], be = sh.coef2[s];
+                    double2 *x2 = reinterpret_cast<double2 *>(sd.x + row0);
+                    double2 *r2 = reinterpret_cast<double2 *>(sd.r + row0);
+                    double2 *p2 = reinterpret_cast<double2 *>(sd.p + row0);
+                    double2 *s2 = reinterpret_cast<double2 *>(sd.s + row0);
+                    const double2 *w2 = reinterpret_cast<const double2 *>(sd.w + row0);
+                    for (int q = threadIdx.x; q < npk; q += blockDim.x) {
+                        double2 xv = x2[q], rv = r2[q], pv = p2[q], sv = s2[q];
+                        const double2 wv = w2[q];
+                        pv.x = fma(be, pv.x, rv.x);
+                        pv.y = fma(be, pv.y, rv.y);
+                        sv.x = fma(be, sv.x, wv.x);
+                        sv.y = fma(be, sv.y, wv.y);
+                        xv.x = fma(al, pv.x, xv.x);
+                        xv.y = fma(al, pv.y, xv.y);
+                        rv.x = fma(-al, sv.x, rv.x);
+                        rv.y = fma(-al, sv.y, rv.y);
+                        x2[q] = xv;
+                        r2[q] = rv;
+                        p2[q] = pv;
+                        s2[q] = sv;
+                    }
+                    for (int row = row0 + 2 * npk + threadIdx.x; row < row1; row += blockDim.x) {
+                        const double pi = fma(be, sd.p[row], sd.r[row]);
+                        const double si = fma(be, sd.s[row], sd.w[row]);
+                        sd.p[row] = pi;
+                        sd.s[row] = si;
+                        sd.x[row] = fma(al, pi, sd.x[row]);
+                        sd.r[row] = fma(-al, si, sd.r[row]);
                     }
                 } else if (pass == kUpdateP) {
                     const double be = sh.coef[s];
@@ -389,7 +441,7 @@ __device__ bool batch_pass(const BatchArgs &a, BatchShared &sh, int pass) {
     return true;
 }
 
-template <int FMT, int KRHS>
+template <int FMT, int KRHS, bool SR>
 __global__ void __launch_bounds__(kBatchThreads, KRHS <= 2 ? 4 : 2) k_cg_batched(const BatchArgs a) {
     __shared__ BatchShared sh;
     const int n = a.n_sys;
@@ -406,7 +458,7 @@ __global__ void __launch_bounds__(kBatchThreads, KRHS <= 2 ? 4 : 2) k_cg_batched
         sh.status[s] = FE_ERR_MAXIT;
         sh.iters[s] = 0;
     }
-    bool alive = batch_pass<FMT, KRHS>(a, sh, kInit);
+    bool alive = batch_pass<FMT, KRHS, SR>(a, sh, kInit);
     if (alive) {
         int any_zero = 0;
         for (int s = threadIdx.x; s < n; s += blockDim.x) {
@@ -424,16 +476,62 @@ __global__ void __launch_bounds__(kBatchThreads, KRHS <= 2 ? 4 : 2) k_cg_batched
                 sh.active[s] = 0;
             }
         }
-        if (__syncthreads_or(any_zero)) alive = batch_pass<FMT, KRHS>(a, sh, kZeroX);
+        if (__syncthreads_or(any_zero)) alive = batch_pass<FMT, KRHS, SR>(a, sh, kZeroX);
     }
-    while (alive) {
+    bool first = true;
+    while (alive && SR) {
+        for (int s = threadIdx.x; s < n; s += blockDim.x) sh.mask[s] = sh.active[s];
+        __syncthreads();
+        int na = 0;
+        for (int s = 0; s < n; ++s) na += sh.active[s];
+        if (na == 0) break;
+        // w = A r, gamma = r.r, delta = w.r
+        if (!(alive = batch_pass<FMT, KRHS, SR>(a, sh, kSpmvR))) break;
+        for (int s = threadIdx.x; s < n; s += blockDim.x) {
+            if (!sh.active[s]) continue;
+            const double gamma = sh.red[0][s], delta = sh.red[1][s];
+            if (!first) sh.iters[s] += 1;
+            double beta = 0.0, curv = delta;
+            if (!first) {
+                beta = gamma / sh.rr[s];
+                curv = delta - beta * gamma / sh.coef[s];   // coef: alpha of the previous step
+                if (!(curv > 0.0) || !(curv < INFINITY)) {  // lost its sign: restart the direction
+                    beta = 0.0;
+                    curv = delta;
+                }
+            }
+            sh.rr[s] = gamma;
+            if (gamma <= a.tol2 * sh.bb[s]) {
+                sh.status[s] = FE_OK;
+                sh.active[s] = 0;
+            } else if (sh.iters[s] >= a.maxit) {
+                sh.status[s] = FE_ERR_MAXIT;
+                sh.active[s] = 0;
+            } else if (!(curv > 0.0) || !(curv < INFINITY)) {
+                sh.status[s] = FE_ERR_BREAKDOWN;
+                sh.active[s] = 0;
+            } else {
+                sh.coef[s] = gamma / curv;
+                sh.coef2[s] = beta;
+            }
+            sh.mask[s] = sh.active[s];
+        }
+        __syncthreads();
+        na = 0;
+        for (int s = 0; s < n; ++s) na += sh.active[s];
+        if (na == 0) break;
+        // p = r + beta p, s = w + beta s, x += alpha p, r -= alpha s
+        if (!(alive = batch_pass<FMT, KRHS, SR>(a, sh, kUpdateSR))) break;
+        first = false;
+    }
+    while (alive && !SR) {
         for (int s = threadIdx.x; s < n; s += blockDim.x) sh.mask[s] = sh.active[s];
         __syncthreads();
         int na = 0;
         for (int s = 0; s < n; ++s) na += sh.active[s];
         if (na == 0) break;
         // w = A p, p.w
-        if (!(alive = batch_pass<FMT, KRHS>(a, sh, kSpmv))) break;
+        if (!(alive = batch_pass<FMT, KRHS, SR>(a, sh, kSpmv))) break;
         for (int s = threadIdx.x; s < n; s += blockDim.x) {
             if (!sh.active[s]) continue;
             const double pw = sh.red[0][s];
@@ -446,7 +544,7 @@ __global__ void __launch_bounds__(kBatchThreads, KRHS <= 2 ? 4 : 2) k_cg_batched
             }
         }
         // x += alpha p, r -= alpha w, r.r
-        if (!(alive = batch_pass<FMT, KRHS>(a, sh, kUpdateXR))) break;
+        if (!(alive = batch_pass<FMT, KRHS, SR>(a, sh, kUpdateXR))) break;
         for (int s = threadIdx.x; s < n; s += blockDim.x) {
             if (!sh.active[s]) continue;
             const double rr_new = sh.red[0][s];
@@ -464,7 +562,7 @@ __global__ void __launch_bounds__(kBatchThreads, KRHS <= 2 ? 4 : 2) k_cg_batched
             }
         }
         // p = r + beta p
-        if (!(alive = batch_pass<FMT, KRHS>(a, sh, kUpdateP))) break;
+        if (!(alive = batch_pass<FMT, KRHS, SR>(a, sh, kUpdateP))) break;
     }
     __syncthreads();
     if (blockIdx.x == 0) {
@@ -500,39 +598,33 @@ static Fixed fixed_offsets(int n, int max_blocks) {
     return F;
 }
 
-// Offsets of each system's r, p, w block (caller's numbering) and the total.
+// Offsets of each system's r, p, w, s block (caller's numbering) and the total.
 static size_t vector_offsets(int n, const fe_matrix *A, int max_blocks, std::vector<size_t> *off) {
     size_t o = fixed_offsets(n, max_blocks).vecs;
     for (int i = 0; i < n; ++i) {
         if (off) off->push_back(o);
-        o += 3 * align256((size_t)A[i].n_slices * kSlice * sizeof(double));
+        o += 4 * align256((size_t)A[i].n_slices * kSlice * sizeof(double));
     }
     return o;
 }
 
-template <int FMT, int KRHS>
-static fe_status batch_occupancy(int *per_sm) {
-    FE_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_cg_batched<FMT, KRHS>, kBatchThreads, 0));
-    return FE_OK;
+// The kernel instance of (format, RHS chunk, method).
+template <int FMT, int KRHS> static const void *kernel_of(int method) {
+    return method == FE_BATCH_SINGLE_REDUCTION ? (const void *)k_cg_batched<FMT, KRHS, true>
+                                               : (const void *)k_cg_batched<FMT, KRHS, false>;
 }
 
-static fe_status occupancy_for(int fmt, int krhs, int *per_sm) {
+static const void *batched_kernel(int fmt, int krhs, int method) {
     if (fmt == FE_FMT_BCRS3) {
-        if (krhs == 1) return batch_occupancy<FE_FMT_BCRS3, 1>(per_sm);
-        if (krhs == 2) return batch_occupancy<FE_FMT_BCRS3, 2>(per_sm);
-        return batch_occupancy<FE_FMT_BCRS3, 4>(per_sm);
+        if (krhs == 1) return kernel_of<FE_FMT_BCRS3, 1>(method);
+        if (krhs == 2) return kernel_of<FE_FMT_BCRS3, 2>(method);
+        if (krhs == 4) return kernel_of<FE_FMT_BCRS3, 4>(method);
+    } else if (fmt == FE_FMT_SELL) {
+        if (krhs == 1) return kernel_of<FE_FMT_SELL, 1>(method);
+        if (krhs == 2) return kernel_of<FE_FMT_SELL, 2>(method);
+        if (krhs == 4) return kernel_of<FE_FMT_SELL, 4>(method);
     }
-    if (krhs == 1) return batch_occupancy<FE_FMT_SELL, 1>(per_sm);
-    if (krhs == 2) return batch_occupancy<FE_FMT_SELL, 2>(per_sm);
-    return batch_occupancy<FE_FMT_SELL, 4>(per_sm);
-}
-
-template <int FMT, int KRHS>
-static fe_status launch_batched(const BatchArgs &args, int grid, cudaStream_t s) {
-    void *params[] = {(void *)&args};
-    FE_TRY_CUDA(cudaLaunchCooperativeKernel((const void *)k_cg_batched<FMT, KRHS>, dim3((unsigned)grid),
-                                            dim3(kBatchThreads), params, 0, s));
-    return FE_OK;
+    return nullptr;
 }
 
 static BatchArgs args_of(const fe_batch_plan *plan, double tol, int maxit, double timeout_s) {
@@ -575,11 +667,12 @@ fe_status fe_cg_batched_workspace(int n_systems, const fe_matrix *A, size_t *h_b
 }
 
 fe_status fe_cg_batched_plan(int n_systems, const fe_matrix *A, const double *const *d_b,
-                             double *const *d_x, int krhs, int blocks_per_sm, void *d_work,
+                             double *const *d_x, int krhs, int method, int blocks_per_sm, void *d_work,
                              size_t work_bytes, fe_batch_plan *h_plan, fe_stream_t stream) {
     if (n_systems < 1 || n_systems > kBatchMaxSystems || !A || !d_b || !d_x || !d_work || !h_plan)
         return FE_ERR_ARG;
     if (krhs != 1 && krhs != 2 && krhs != 4) return FE_ERR_ARG;
+    if (method != FE_BATCH_TEXTBOOK && method != FE_BATCH_SINGLE_REDUCTION) return FE_ERR_ARG;
     if (!aligned(d_work, 256)) return FE_ERR_ARG;
     const int fmt = A[0].format;
     if (fmt != FE_FMT_BCRS3 && fmt != FE_FMT_SELL) return FE_ERR_ARG;
@@ -638,6 +731,7 @@ fe_status fe_cg_batched_plan(int n_systems, const fe_matrix *A, const double *co
                 sd.r = (double *)base;
                 sd.p = (double *)(base + vb);
                 sd.w = (double *)(base + 2 * vb);
+                sd.s = (double *)(base + 3 * vb);
                 sd.chunk = (int)chunks.size();
                 sd.pad = i;   // caller's index
                 slot_of[i] = pos;
@@ -650,8 +744,9 @@ fe_status fe_cg_batched_plan(int n_systems, const fe_matrix *A, const double *co
     }
 
     int per_sm = 0;
-    st = occupancy_for(fmt, krhs, &per_sm);
-    if (st != FE_OK) return st;
+    const void *kern = batched_kernel(fmt, krhs, method);
+    if (kern == nullptr) return FE_ERR_ARG;
+    FE_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBatchThreads, 0));
     if (per_sm < 1) return FE_ERR_CUDA;
     if (blocks_per_sm > 0 && blocks_per_sm < per_sm) per_sm = blocks_per_sm;
     long long total_slices = 0;
@@ -678,6 +773,7 @@ fe_status fe_cg_batched_plan(int n_systems, const fe_matrix *A, const double *co
     FE_TRY_CUDA(cudaStreamSynchronize(s));
     h_plan->format = fmt;
     h_plan->krhs = krhs;
+    h_plan->method = method;
     h_plan->n_systems = n_systems;
     h_plan->n_chunks = (int)chunks.size();
     h_plan->grid = (int)grid;
@@ -695,17 +791,12 @@ fe_status fe_cg_batched_launch(const fe_batch_plan *plan, double tol, int maxit,
         return FE_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     BatchArgs a = args_of(plan, tol, maxit, timeout_s);
+    const void *kern = batched_kernel(plan->format, plan->krhs, plan->method);
+    if (kern == nullptr || plan->grid < 1 || plan->grid > plan->max_blocks) return FE_ERR_ARG;
     FE_TRY_CUDA(cudaMemsetAsync(a.ctrl, 0, sizeof(CgCtrl), s));
-    if (plan->format == FE_FMT_BCRS3) {
-        if (plan->krhs == 1) return launch_batched<FE_FMT_BCRS3, 1>(a, plan->grid, s);
-        if (plan->krhs == 2) return launch_batched<FE_FMT_BCRS3, 2>(a, plan->grid, s);
-        if (plan->krhs == 4) return launch_batched<FE_FMT_BCRS3, 4>(a, plan->grid, s);
-    } else if (plan->format == FE_FMT_SELL) {
-        if (plan->krhs == 1) return launch_batched<FE_FMT_SELL, 1>(a, plan->grid, s);
-        if (plan->krhs == 2) return launch_batched<FE_FMT_SELL, 2>(a, plan->grid, s);
-        if (plan->krhs == 4) return launch_batched<FE_FMT_SELL, 4>(a, plan->grid, s);
-    }
-    return FE_ERR_ARG;
+    void *params[] = {(void *)&a};
+    FE_TRY_CUDA(cudaLaunchCooperativeKernel(kern, dim3((unsigned)plan->grid), dim3(kBatchThreads), params, 0, s));
+    return FE_OK;
 }
 
 fe_status fe_cg_batched_results(const fe_batch_plan *plan, fe_cg_result *h_results,
@@ -741,7 +832,8 @@ fe_status fe_cg_solve_batched(int n_systems, const fe_matrix *A, const double *c
                               void *d_work, size_t work_bytes, fe_cg_result *h_results,
                               fe_stream_t stream) {
     fe_batch_plan plan;
-    fe_status st = fe_cg_batched_plan(n_systems, A, d_b, d_x, krhs, 0, d_work, work_bytes, &plan, stream);
+    fe_status st = fe_cg_batched_plan(n_systems, A, d_b, d_x, krhs, FE_BATCH_TEXTBOOK, 0, d_work,
+                                      work_bytes, &plan, stream);
     if (st != FE_OK) return st;
     st = fe_cg_batched_launch(&plan, tol, maxit, timeout_s, stream);
     if (st != FE_OK) return st;

@@ -11,6 +11,10 @@
 // The scalars follow from the reduced pair:
 //   beta_k = gamma_k / gamma_{k-1},  p.Ap = delta_k - beta_k gamma_k / alpha_{k-1},
 //   alpha_k = gamma_k / p.Ap          (k = 0: beta = 0, p.Ap = delta).
+// In finite precision the curvature recurrence can lose its sign near
+// convergence (cancellation); a step whose recurrence gives p.Ap <= 0 restarts
+// the direction (beta = 0, p.Ap = delta = r.Ar) -- the oracle does the same --
+// and only delta <= 0 is a breakdown.
 // It pays off where barriers dominate the step (small meshes); on large
 // meshes it moves the same bytes as textbook CG and does one more FMA per
 // row (the s update), which matters on GB300's FP64 pipe.
@@ -144,6 +148,10 @@ __global__ void __launch_bounds__(kCgThreads, kCgBlocksPerSm) k_cg_sr(const CgSr
             if (!first) {
                 beta = sr.gamma / sr.gamma_prev;
                 curv = sr.delta - beta * sr.gamma / sr.alpha_prev;
+                if (!(curv > 0.0) || !(curv < INFINITY)) {  // lost its sign: restart the direction
+                    beta = 0.0;
+                    curv = sr.delta;
+                }
             }
             if (!(curv > 0.0) || !(curv < INFINITY)) { status = FE_ERR_BREAKDOWN; break; }
             const double alpha = sr.gamma / curv;

@@ -74,6 +74,7 @@ class fe_batch_plan(ctypes.Structure):
     _fields_ = [("format", ctypes.c_int32), ("krhs", ctypes.c_int32),
                 ("n_systems", ctypes.c_int32), ("n_chunks", ctypes.c_int32),
                 ("grid", ctypes.c_int32), ("max_blocks", ctypes.c_int32),
+                ("method", ctypes.c_int32),
                 ("d_work", ctypes.c_void_p), ("work_bytes", ctypes.c_size_t),
                 ("slot_of", ctypes.c_int32 * BATCH_MAX_SYSTEMS)]
 
@@ -108,7 +109,7 @@ SIGNATURES = {
                                    ctypes.POINTER(fe_cg_result), _VP]),
     "fe_cg_batched_workspace": (_I32, [ctypes.c_int, ctypes.POINTER(fe_matrix), ctypes.POINTER(_SZ)]),
     "fe_cg_batched_plan": (_I32, [ctypes.c_int, ctypes.POINTER(fe_matrix), ctypes.POINTER(_VP),
-                                  ctypes.POINTER(_VP), ctypes.c_int, ctypes.c_int, _VP, _SZ,
+                                  ctypes.POINTER(_VP), ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, _SZ,
                                   ctypes.POINTER(fe_batch_plan), _VP]),
     "fe_cg_batched_launch": (_I32, [ctypes.POINTER(fe_batch_plan), _D, ctypes.c_int, _D, _VP]),
     "fe_cg_batched_results": (_I32, [ctypes.POINTER(fe_batch_plan), ctypes.POINTER(fe_cg_result), _VP]),
@@ -337,10 +338,15 @@ def fe_cg_batched_workspace(mats) -> int:
     return n.value
 
 
-def fe_cg_batched_plan(mats, bs, xs, krhs, work, blocks_per_sm=0, stream=None) -> fe_batch_plan:
+BATCH_TEXTBOOK, BATCH_SINGLE_REDUCTION = 0, 1
+
+
+def fe_cg_batched_plan(mats, bs, xs, krhs, work, blocks_per_sm=0, stream=None,
+                       method=BATCH_TEXTBOOK) -> fe_batch_plan:
     plan = fe_batch_plan()
     _check("fe_cg_batched_plan", load().fe_cg_batched_plan(
-        len(mats), _descs(mats), _ptrs(bs), _ptrs(xs), int(krhs), int(blocks_per_sm), _ptr(work),
+        len(mats), _descs(mats), _ptrs(bs), _ptrs(xs), int(krhs), int(method), int(blocks_per_sm),
+        _ptr(work),
         work.numel() * work.element_size(), ctypes.byref(plan), _stream(stream)))
     return plan
 

@@ -83,3 +83,22 @@ def test_status_codes():
     rp, cols, vals = diag_csr([2.0, 4.0])
     _, it, _, st = oracle.cg_sr(rp, cols, vals, np.array([2.0, 4.0]), x0=np.ones(2))
     assert st == oracle.CG_CONVERGED and it == 0
+
+
+def test_restart_when_the_curvature_recurrence_is_not_positive():
+    """diag(3, -1), b = (1, 1), worked by hand.  Step 1: r0 = b, delta = 2,
+    alpha = 1, x1 = (1, 1), r1 = (-2, 2), gamma = 8, w1 = A r1 = (-6, -2),
+    delta = 8.  Step 2: beta = 4 and the recurrence gives p.Ap = 8 - 4*8/1 = -24
+    (textbook CG breaks down here: p = (2, 6), p.Ap = -24); the single-reduction
+    form restarts the direction: p = r1, alpha = gamma / delta = 1,
+    x2 = x1 + r1 = (-1, 3)."""
+    rp, cols, vals = diag_csr([3.0, -1.0])
+    b = np.array([1.0, 1.0])
+    _, _, _, st = oracle.cg(rp, cols, vals, b, tol=1e-12, maxit=2)
+    assert st == oracle.CG_BREAKDOWN
+    x, it, rel, st = oracle.cg_sr(rp, cols, vals, b, tol=1e-12, maxit=2)
+    assert st == oracle.CG_MAXIT and it == 2
+    assert np.array_equal(x, np.array([-1.0, 3.0]))
+    _, it, _, _ = oracle.cg_sr(rp, cols, vals, b, tol=1e-12, maxit=1)
+    x1, _, _, _ = oracle.cg_sr(rp, cols, vals, b, tol=0.0, maxit=1)
+    assert np.array_equal(x1, np.array([1.0, 1.0]))
