@@ -61,7 +61,7 @@ FP64_PEAK_TFLOPS = 1.25   # nominal dense FP64 of a GB300 (2 FMA/clk/SM x 152 SM
 # initial residual, from two ncu captures at N=180 where, as at N=256, the CG
 # vectors exceed L2 (profiles/k_cg_n180_ncu_traffic.md).  Valid for the kernel
 # as captured; set to None when k_cg changes until it is captured again.
-K_CG_BCRS3_TRAFFIC_PER_ROW = None
+K_CG_BCRS3_TRAFFIC_PER_ROW = {"step": 334.3, "init": 254.5}
 
 
 def load_peaks():

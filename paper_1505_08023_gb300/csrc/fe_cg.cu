@@ -27,12 +27,9 @@
 namespace fe {
 
 template <int FMT, class VT, class XT>
-__global__ void __launch_bounds__(kCgThreads, kCgBlocksPerSm) k_cg(const CgArgs<XT> a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+__global__ void __launch_bounds__(kCgThreads, cg_min_blocks<FMT>()) k_cg(const CgArgs<XT> a) {
     __shared__ CgBlockState st;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    XT *sv = reinterpret_cast<XT *>(smem_raw) + (size_t)warp * 2 * kCsrStage;
-    XT *sx = sv + kCsrStage;
     // rows fit int32 (check_matrix); slices are walked in a grid-stride order
     const int m = (int)a.A.n_rows, ns = (int)a.A.n_slices;
     const int tw = gridDim.x * kCgWarps;
@@ -51,7 +48,7 @@ __global__ void __launch_bounds__(kCgThreads, kCgBlocksPerSm) k_cg(const CgArgs<
         XT s0 = XT(0), s1 = XT(0);
         for (int s = blockIdx.x * kCgWarps + warp; s < ns; s += tw) {
             XT ax = XT(0);
-            if (!a.x0_zero) ax = slice_spmv<FMT, VT, XT, XT, false>(a.A, s, lane, a.x, sv, sx);
+            if (!a.x0_zero) ax = slice_spmv<FMT, VT, XT, XT, false>(a.A, s, lane, a.x);
             const int row = s * kSlice + lane;
             if (row < m) {
                 const XT bi = a.b[row];
@@ -85,7 +82,7 @@ __global__ void __launch_bounds__(kCgThreads, kCgBlocksPerSm) k_cg(const CgArgs<
             // A: w = A p, p.w
             XT pw_part = XT(0);
             for (int s = blockIdx.x * kCgWarps + warp; s < ns; s += tw) {
-                const XT y = slice_spmv<FMT, VT, XT, XT, false>(a.A, s, lane, a.p, sv, sx);
+                const XT y = slice_spmv<FMT, VT, XT, XT, false>(a.A, s, lane, a.p);
                 const int row = s * kSlice + lane;
                 if (row < m) {
                     a.w[row] = y;
@@ -134,11 +131,8 @@ static size_t cg_workspace_bytes(const fe_matrix &A) {
 template <int FMT, class VT, class XT>
 static fe_status launch_cg(const CgArgs<XT> &args, cudaStream_t s) {
     auto kern = k_cg<FMT, VT, XT>;
-    const size_t smem = spmv_smem_bytes<FMT, XT>(kCgWarps);
-    if (smem > 48 * 1024)
-        FE_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
-    FE_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kCgThreads, smem));
+    FE_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kCgThreads, 0));
     if (per_sm < 1) return FE_ERR_CUDA;
     int64_t blocks = (int64_t)sm_count() * per_sm;
     const int64_t need = (args.A.n_slices + kCgWarps - 1) / kCgWarps;
@@ -147,7 +141,7 @@ static fe_status launch_cg(const CgArgs<XT> &args, cudaStream_t s) {
     if (blocks < 1) blocks = 1;
     void *params[] = {(void *)&args};
     FE_TRY_CUDA(cudaLaunchCooperativeKernel((const void *)kern, dim3((unsigned)blocks), dim3(kCgThreads),
-                                            params, smem, s));
+                                            params, 0, s));
     return FE_OK;
 }
 

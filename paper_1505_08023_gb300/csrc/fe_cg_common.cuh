@@ -13,6 +13,10 @@ constexpr int kCgWarps = 8;
 constexpr int kCgThreads = kCgWarps * 32;
 constexpr int kCgMaxBlocks = 4096;
 constexpr int kCgBlocksPerSm = 4;
+// Resident blocks the persistent kernels are compiled for: the CSR slice
+// kernel keeps seven entries per lane in flight, which needs more than the
+// 64 registers of four blocks per SM.
+template <int FMT> constexpr int cg_min_blocks() { return FMT == FE_FMT_CSR ? 3 : kCgBlocksPerSm; }
 constexpr unsigned kMaxPolls = 1u << 28;
 
 struct CgCtrl {
@@ -238,15 +242,12 @@ __global__ void __launch_bounds__(kCgThreads) k_resid(const fe_matrix A, const d
                                                       const double *__restrict__ x,
                                                       double *__restrict__ part,
                                                       float *__restrict__ r32) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[kCgWarps][2];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    double *sv = reinterpret_cast<double *>(smem_raw) + (size_t)warp * 2 * kCsrStage;
-    double *sx = sv + kCsrStage;
     double s0 = 0.0, s1 = 0.0;
     const int64_t tw = (int64_t)gridDim.x * kCgWarps;
     for (int64_t s = (int64_t)blockIdx.x * kCgWarps + warp; s < A.n_slices; s += tw) {
-        const double ax = slice_spmv<FMT, VT, double, double, true>(A, s, lane, x, sv, sx);
+        const double ax = slice_spmv<FMT, VT, double, double, true>(A, s, lane, x);
         const int64_t row = s * kSlice + lane;
         if (row < A.n_rows) {
             const double bi = b[row], ri = bi - ax;
@@ -294,18 +295,15 @@ template <int FMT, class VT>
 static fe_status launch_resid(const fe_matrix &A, const double *b, const double *x, double *part,
                               float *r32, int *nblocks, cudaStream_t s) {
     auto kern = k_resid<FMT, VT>;
-    const size_t smem = spmv_smem_bytes<FMT, double>(kCgWarps);
-    if (smem > 48 * 1024)
-        FE_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
-    FE_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kCgThreads, smem));
+    FE_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kCgThreads, 0));
     if (per_sm < 1) per_sm = 1;
     int64_t blocks = (int64_t)sm_count() * per_sm;
     const int64_t need = (A.n_slices + kCgWarps - 1) / kCgWarps;
     if (blocks > need) blocks = need;
     if (blocks > kCgMaxBlocks) blocks = kCgMaxBlocks;
     if (blocks < 1) blocks = 1;
-    kern<<<(int)blocks, kCgThreads, smem, s>>>(A, b, x, part, r32);
+    kern<<<(int)blocks, kCgThreads, 0, s>>>(A, b, x, part, r32);
     FE_TRY_LAUNCH();
     *nblocks = (int)blocks;
     return FE_OK;

@@ -48,13 +48,13 @@ struct MixArgs {
 // this thread's partials of r.r and b.b in FP64.
 template <int FH>
 __device__ __forceinline__ void fp64_residual(const MixArgs &a, int m, int ns, bool set_p,
-                                              double *svd, double *sxd, double &s0, double &s1) {
+                                              double &s0, double &s1) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int tw = gridDim.x * kCgWarps;
     s0 = 0.0;
     s1 = 0.0;
     for (int s = blockIdx.x * kCgWarps + warp; s < ns; s += tw) {
-        const double ax = slice_spmv<FH, double, double, double, false>(a.A_hi, s, lane, a.x, svd, sxd);
+        const double ax = slice_spmv<FH, double, double, double, false>(a.A_hi, s, lane, a.x);
         const int row = s * kSlice + lane;
         if (row < m) {
             const double bi = a.b[row], ri = bi - ax;
@@ -92,16 +92,9 @@ __device__ __forceinline__ void fold_correction(double *x, float *xs, int m) {
     }
 }
 
-// Shared-memory bytes one warp needs for CSR staging: FP64 slots for a CSR
-// FP64 matrix, FP32 slots for a CSR low-precision matrix, 0 otherwise.
-template <int FL, int FH> __host__ __device__ constexpr size_t reliable_warp_stage_bytes() {
-    return FH == FE_FMT_CSR ? 2 * (size_t)kCsrStage * sizeof(double)
-                            : (FL == FE_FMT_CSR ? 2 * (size_t)kCsrStage * sizeof(float) : 0);
-}
-
 template <int FL, class VL, int FH>
-__global__ void __launch_bounds__(kCgThreads, kCgBlocksPerSm) k_cg_reliable(const MixArgs a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+__global__ void __launch_bounds__(kCgThreads, (FL == FE_FMT_CSR || FH == FE_FMT_CSR) ? 3 : kCgBlocksPerSm)
+k_cg_reliable(const MixArgs a) {
     __shared__ CgBlockState st;
     __shared__ double s_rr_max;
     __shared__ double s_rr_true;   // last FP64 true residual (reported)
@@ -109,14 +102,6 @@ __global__ void __launch_bounds__(kCgThreads, kCgBlocksPerSm) k_cg_reliable(cons
     __shared__ int s_stalls;       // refinement steps in a row that did not halve the residual
     __shared__ int s_last_refine;  // step count at the last refinement
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // CSR staging: the FP64 residual needs double slots, the FP32 SpMV float
-    // slots; each warp owns one region of the size the launch allocated
-    // (reliable_smem_bytes), which holds whichever of the two it needs.
-    unsigned char *mine = smem_raw + (size_t)warp * reliable_warp_stage_bytes<FL, FH>();
-    double *svd = reinterpret_cast<double *>(mine);
-    double *sxd = svd + kCsrStage;
-    float *svf = reinterpret_cast<float *>(mine);
-    float *sxf = svf + kCsrStage;
     const int m = (int)a.A_lo.n_rows, ns = (int)a.A_lo.n_slices;
     const int tw = gridDim.x * kCgWarps;
     if (threadIdx.x == 0) {
@@ -132,7 +117,7 @@ __global__ void __launch_bounds__(kCgThreads, kCgBlocksPerSm) k_cg_reliable(cons
     int status = FE_ERR_MAXIT;
     bool alive = true;
     double s0, s1, rr_true, bb;
-    fp64_residual<FH>(a, m, ns, true, svd, sxd, s0, s1);
+    fp64_residual<FH>(a, m, ns, true, s0, s1);
     alive = grid_sum2(a, &st, s0, s1, rr_true, bb);
     if (threadIdx.x == 0) {
         st.rr = rr_true;
@@ -153,7 +138,7 @@ __global__ void __launch_bounds__(kCgThreads, kCgBlocksPerSm) k_cg_reliable(cons
             // A: w = A_lo p (FP32), p.w
             float pw_part = 0.0f;
             for (int s = blockIdx.x * kCgWarps + warp; s < ns; s += tw) {
-                const float y = slice_spmv<FL, VL, float, float, false>(a.A_lo, s, lane, a.p, svf, sxf);
+                const float y = slice_spmv<FL, VL, float, float, false>(a.A_lo, s, lane, a.p);
                 const int row = s * kSlice + lane;
                 if (row < m) {
                     a.w[row] = y;
@@ -176,7 +161,7 @@ __global__ void __launch_bounds__(kCgThreads, kCgBlocksPerSm) k_cg_reliable(cons
                 // x += xs in FP64, then r = b - A64 x in FP64 (stored as the FP32 residual)
                 fold_correction(a.x, a.xs, m);
                 if (!(alive = grid_barrier(a.ctrl, &st, a.timeout_ns, a.stall_barrier))) break;
-                fp64_residual<FH>(a, m, ns, false, svd, sxd, s0, s1);
+                fp64_residual<FH>(a, m, ns, false, s0, s1);
                 if (!(alive = grid_sum2(a, &st, s0, 0.0, rr_true, unused))) break;
                 __syncthreads();
                 if (threadIdx.x == 0) {
@@ -217,11 +202,8 @@ __global__ void __launch_bounds__(kCgThreads, kCgBlocksPerSm) k_cg_reliable(cons
 template <int FL, class VL, int FH>
 static fe_status launch_reliable(const MixArgs &args, cudaStream_t s) {
     auto kern = k_cg_reliable<FL, VL, FH>;
-    const size_t smem = (size_t)kCgWarps * reliable_warp_stage_bytes<FL, FH>();
-    if (smem > 48 * 1024)
-        FE_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
-    FE_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kCgThreads, smem));
+    FE_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kCgThreads, 0));
     if (per_sm < 1) return FE_ERR_CUDA;
     int64_t blocks = (int64_t)sm_count() * per_sm;
     const int64_t need = (args.A_lo.n_slices + kCgWarps - 1) / kCgWarps;
@@ -230,7 +212,7 @@ static fe_status launch_reliable(const MixArgs &args, cudaStream_t s) {
     if (blocks < 1) blocks = 1;
     void *params[] = {(void *)&args};
     FE_TRY_CUDA(cudaLaunchCooperativeKernel((const void *)kern, dim3((unsigned)blocks), dim3(kCgThreads),
-                                            params, smem, s));
+                                            params, 0, s));
     return FE_OK;
 }
 

@@ -71,13 +71,10 @@ __device__ __forceinline__ void update_sr(double *x, double *r, double *p, doubl
 }
 
 template <int FMT, class VT>
-__global__ void __launch_bounds__(kCgThreads, kCgBlocksPerSm) k_cg_sr(const CgSrArgs a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+__global__ void __launch_bounds__(kCgThreads, cg_min_blocks<FMT>()) k_cg_sr(const CgSrArgs a) {
     __shared__ CgBlockState st;
     __shared__ SrState sr;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    double *sv = reinterpret_cast<double *>(smem_raw) + (size_t)warp * 2 * kCsrStage;
-    double *sx = sv + kCsrStage;
     const int m = (int)a.A.n_rows, ns = (int)a.A.n_slices;
     const int tw = gridDim.x * kCgWarps;
     if (threadIdx.x == 0) {
@@ -95,7 +92,7 @@ __global__ void __launch_bounds__(kCgThreads, kCgBlocksPerSm) k_cg_sr(const CgSr
     {
         double bb_part = 0.0;
         for (int sl = blockIdx.x * kCgWarps + warp; sl < ns; sl += tw) {
-            const double ax = slice_spmv<FMT, VT, double, double, false>(a.A, sl, lane, a.x, sv, sx);
+            const double ax = slice_spmv<FMT, VT, double, double, false>(a.A, sl, lane, a.x);
             const int row = sl * kSlice + lane;
             if (row < m) {
                 const double bi = a.b[row];
@@ -123,7 +120,7 @@ __global__ void __launch_bounds__(kCgThreads, kCgBlocksPerSm) k_cg_sr(const CgSr
             // S: w = A r, gamma = r.r, delta = w.r
             double g_part = 0.0, d_part = 0.0;
             for (int sl = blockIdx.x * kCgWarps + warp; sl < ns; sl += tw) {
-                const double y = slice_spmv<FMT, VT, double, double, false>(a.A, sl, lane, a.r, sv, sx);
+                const double y = slice_spmv<FMT, VT, double, double, false>(a.A, sl, lane, a.r);
                 const int row = sl * kSlice + lane;
                 if (row < m) {
                     a.w[row] = y;
@@ -178,11 +175,8 @@ static size_t cg_sr_workspace_bytes(const fe_matrix &A) {
 
 template <int FMT, class VT> static fe_status launch_cg_sr(const CgSrArgs &args, cudaStream_t s) {
     auto kern = k_cg_sr<FMT, VT>;
-    const size_t smem = spmv_smem_bytes<FMT, double>(kCgWarps);
-    if (smem > 48 * 1024)
-        FE_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
-    FE_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kCgThreads, smem));
+    FE_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kCgThreads, 0));
     if (per_sm < 1) return FE_ERR_CUDA;
     int64_t blocks = (int64_t)sm_count() * per_sm;
     const int64_t need = (args.A.n_slices + kCgWarps - 1) / kCgWarps;
@@ -191,7 +185,7 @@ template <int FMT, class VT> static fe_status launch_cg_sr(const CgSrArgs &args,
     if (blocks < 1) blocks = 1;
     void *params[] = {(void *)&args};
     FE_TRY_CUDA(cudaLaunchCooperativeKernel((const void *)kern, dim3((unsigned)blocks), dim3(kCgThreads),
-                                            params, smem, s));
+                                            params, 0, s));
     return FE_OK;
 }
 

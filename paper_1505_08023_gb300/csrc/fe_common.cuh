@@ -75,10 +75,6 @@ __device__ __forceinline__ int warp_max(int v) {
 
 // ---------------------------------------------------------------- slice SpMV
 
-// Shared-memory staging for the CSR slice kernel: values and gathered vector
-// entries of one warp's 32 rows, in chunks of kCsrStage entries.
-constexpr int kCsrStage = 32 * 27;
-
 // One warp computes the 32 rows of slice s; returns lane's row sum (0 for
 // rows past the end).  XT: vector type, AT: accumulation type.
 template <class VT, class XT, class AT, bool kReadOnlyX>
@@ -152,52 +148,68 @@ __device__ __forceinline__ AT slice_spmv_bcrs3(const fe_matrix &A, int64_t s, in
     return acc;
 }
 
-// CSR: the warp stages its rows' values and gathered x entries in shared
-// memory with coalesced loads, then each lane runs its own row sequentially
-// (one FMA per entry, all lanes busy).  sv/sx: kCsrStage entries per warp.
+// CSR: four lanes per row, eight rows per pass, four passes per slice.  Lane
+// j of group g runs entries lo + j, lo + j + 4, ... of row 8p + g (one FMA
+// per entry slot; the four lanes read 32 contiguous bytes of values per step;
+// slots past the row end load nothing and add 0 * 0).
+// The four per-pass partials of a lane are then combined across its group by
+// a fixed transpose-reduce (xor 1 then xor 2: three adds per lane) and one
+// shuffle hands each row's sum to the lane of that row.  The order of every
+// addition is fixed, so results are bitwise repeatable.
 template <class VT, class XT, class AT, bool kReadOnlyX>
 __device__ __forceinline__ AT slice_spmv_csr(const fe_matrix &A, int64_t s, int lane,
-                                             const XT *x, AT *sv, AT *sx) {
+                                             const XT *x) {
+    const int g = lane >> 2, j = lane & 3;
     const int64_t r0 = s * kSlice;
     const int64_t nrows = A.n_rows;
-    const int64_t row = r0 + lane;
-    const int64_t last = (r0 + kSlice < nrows) ? r0 + kSlice : nrows;
-    const int32_t base = A.d_row_ptr[r0];
-    const int32_t end = A.d_row_ptr[last];
-    int32_t my_lo = 0, my_hi = 0;
-    if (row < nrows) {
-        my_lo = A.d_row_ptr[row];
-        my_hi = A.d_row_ptr[row + 1];
-    }
     const VT *vals = reinterpret_cast<const VT *>(A.d_vals);
-    AT acc = AT(0);
-    for (int32_t c0 = base; c0 < end; c0 += kCsrStage) {
-        const int32_t cn = (end - c0 < kCsrStage) ? end - c0 : kCsrStage;
-        for (int32_t t = lane; t < cn; t += 32) {
-            const int32_t col = ld_stream(A.d_cols + c0 + t);
-            sv[t] = to_acc<AT>(ld_stream(vals + c0 + t));
-            sx[t] = (AT)ld_vec<kReadOnlyX>(x + col);
+    AT part[4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        const int64_t row = r0 + 8 * p + g;
+        AT acc = AT(0);
+        if (row < nrows) {
+            const int32_t lo = A.d_row_ptr[row], hi = A.d_row_ptr[row + 1];
+            // 28 entries per group per trip (7 per lane, a 27-point row in one
+            // trip); every load of the trip is issued before the first FMA
+            for (int32_t k = lo + j; k < hi; k += 28) {
+                int32_t c[7];
+                VT v[7];
+#pragma unroll
+                for (int u = 0; u < 7; ++u) {
+                    const bool ok = k + 4 * u < hi;
+                    c[u] = ok ? ld_stream(A.d_cols + k + 4 * u) : 0;
+                    v[u] = ok ? ld_stream(vals + k + 4 * u) : VT(0);
+                }
+                XT xx[7];
+#pragma unroll
+                for (int u = 0; u < 7; ++u) xx[u] = (k + 4 * u < hi) ? ld_vec<kReadOnlyX>(x + c[u]) : XT(0);
+#pragma unroll
+                for (int u = 0; u < 7; ++u) acc = fma(to_acc<AT>(v[u]), (AT)xx[u], acc);
+            }
         }
-        __syncwarp();
-        const int32_t lo = (my_lo > c0) ? my_lo : c0;
-        const int32_t hi = (my_hi < c0 + cn) ? my_hi : c0 + cn;
-        for (int32_t k = lo; k < hi; ++k) acc = fma(sv[k - c0], sx[k - c0], acc);
-        __syncwarp();
+        part[p] = acc;
     }
-    return acc;
+    // transpose-reduce over the group: after xor 1 a lane keeps passes
+    // {2b, 2b+1} (b = j & 1), after xor 2 pass q = 2b + ((j >> 1) & 1)
+    const int b = j & 1, h = (j >> 1) & 1;
+    const AT s0 = __shfl_xor_sync(0xffffffffu, b ? part[0] : part[2], 1);
+    const AT s1 = __shfl_xor_sync(0xffffffffu, b ? part[1] : part[3], 1);
+    const AT k0 = (b ? part[2] : part[0]) + s0;
+    const AT k1 = (b ? part[3] : part[1]) + s1;
+    const AT t = __shfl_xor_sync(0xffffffffu, h ? k0 : k1, 2);
+    const AT row_sum = (h ? k1 : k0) + t;     // sum of row 8 q + g, q = 2b + h
+    // lane L takes row L = 8 q + g from lane 4 g + j with q(j) = L / 8
+    const int q = lane >> 3;
+    const int src = 4 * (lane & 7) + ((q & 1) << 1) + (q >> 1);
+    return __shfl_sync(0xffffffffu, row_sum, src);
 }
 
 template <int FMT, class VT, class XT, class AT, bool kReadOnlyX>
-__device__ __forceinline__ AT slice_spmv(const fe_matrix &A, int64_t s, int lane,
-                                         const XT *x, AT *sv, AT *sx) {
-    if constexpr (FMT == FE_FMT_CSR) return slice_spmv_csr<VT, XT, AT, kReadOnlyX>(A, s, lane, x, sv, sx);
+__device__ __forceinline__ AT slice_spmv(const fe_matrix &A, int64_t s, int lane, const XT *x) {
+    if constexpr (FMT == FE_FMT_CSR) return slice_spmv_csr<VT, XT, AT, kReadOnlyX>(A, s, lane, x);
     else if constexpr (FMT == FE_FMT_SELL) return slice_spmv_sell<VT, XT, AT, kReadOnlyX>(A, s, lane, x);
     else return slice_spmv_bcrs3<VT, XT, AT, kReadOnlyX>(A, s, lane, x);
-}
-
-// Dynamic shared memory a block of `warps` warps needs for format FMT.
-template <int FMT, class AT> constexpr size_t spmv_smem_bytes(int warps) {
-    return FMT == FE_FMT_CSR ? (size_t)warps * 2 * kCsrStage * sizeof(AT) : 0;
 }
 
 }  // namespace fe

@@ -11,13 +11,10 @@ constexpr int kSpmvWarps = 8;
 template <int FMT, class VT, class XT, class AT>
 __global__ void __launch_bounds__(kSpmvWarps * 32)
 k_spmv(const fe_matrix A, const XT *__restrict__ x, XT *__restrict__ y) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    AT *sv = reinterpret_cast<AT *>(smem_raw) + (size_t)warp * 2 * kCsrStage;
-    AT *sx = sv + kCsrStage;
     const int64_t tw = (int64_t)gridDim.x * kSpmvWarps;
     for (int64_t s = (int64_t)blockIdx.x * kSpmvWarps + warp; s < A.n_slices; s += tw) {
-        const AT v = slice_spmv<FMT, VT, XT, AT, true>(A, s, lane, x, sv, sx);
+        const AT v = slice_spmv<FMT, VT, XT, AT, true>(A, s, lane, x);
         const int64_t row = s * kSlice + lane;
         if (row < A.n_rows) y[row] = (XT)v;
     }
@@ -26,15 +23,13 @@ k_spmv(const fe_matrix A, const XT *__restrict__ x, XT *__restrict__ y) {
 template <int FMT, class VT, class XT, class AT>
 static fe_status launch(const fe_matrix &A, const XT *x, XT *y, cudaStream_t s) {
     auto kern = k_spmv<FMT, VT, XT, AT>;
-    const size_t smem = spmv_smem_bytes<FMT, AT>(kSpmvWarps);
-    if (smem > 48 * 1024) FE_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
-    FE_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kSpmvWarps * 32, smem));
+    FE_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kSpmvWarps * 32, 0));
     if (per_sm < 1) per_sm = 1;
     int64_t blocks = (A.n_slices + kSpmvWarps - 1) / kSpmvWarps;
     const int64_t cap = (int64_t)sm_count() * per_sm;
     if (cap > 0 && blocks > cap) blocks = cap;
-    kern<<<(int)blocks, kSpmvWarps * 32, smem, s>>>(A, x, y);
+    kern<<<(int)blocks, kSpmvWarps * 32, 0, s>>>(A, x, y);
     FE_TRY_LAUNCH();
     return FE_OK;
 }

@@ -4,8 +4,9 @@
 
 Builds the N x N x N problem through the C ABI (mesh, assembly, conversion to
 --format), then runs, as asked: one stand-alone SpMV (--spmv), the fused FP64
-CG for --cg-steps steps (tol 0, or to --tol when --cg-steps is 0), and the
-mixed-precision reliable-update solve for --mixed-steps FP32 steps.  With
+CG for --cg-steps steps (tol 0, or to --tol when --cg-steps is 0), the
+single-reduction CG for --sr-steps steps, and the mixed-precision
+reliable-update solve for --mixed-steps FP32 steps.  With
 --drop-csr the CSR arrays are released after conversion (smaller footprint
 for profiler captures that save and restore device memory).  Prints one line
 per step taken.
@@ -26,6 +27,8 @@ def main():
     ap.add_argument("--spmv", action="store_true")
     ap.add_argument("--cg-steps", type=int, default=20)
     ap.add_argument("--tol", type=float, default=1e-10)
+    ap.add_argument("--sr-steps", type=int, default=0,
+                    help="steps of the single-reduction CG (tol 0); 0: skip")
     ap.add_argument("--mixed-steps", type=int, default=0)
     ap.add_argument("--mixed-values", choices=["f32", "bf16"], default="f32")
     ap.add_argument("--drop-csr", action="store_true")
@@ -47,6 +50,10 @@ def main():
         tol, steps = (0.0, a.cg_steps) if a.cg_steps > 0 else (a.tol, 100000)
         r = fe.fe_cg_solve(A.desc, s.b, x, tol, steps, fe.cg_workspace(A), check=False)
         print(f"cg: status {r.status} steps {r.iterations} relres {r.relres:.3e}")
+    if a.sr_steps > 0:
+        x.zero_()
+        r = fe.fe_cg_solve_sr(A.desc, s.b, x, 0.0, a.sr_steps, fe.sr_workspace(A), check=False)
+        print(f"cg_sr: status {r.status} steps {r.iterations} relres {r.relres:.3e}")
     if Alo is not None:
         x.zero_()
         r = fe.fe_cg_solve_mixed(A.desc, Alo.desc, s.b, x, a.tol, fe.FE_MIXED_RELIABLE, 200, 0.1,
