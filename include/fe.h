@@ -382,6 +382,29 @@ fe_status fe_nn_conv3d(int mode, const float *d_in, int cin, const int *h_dims_i
  * layout; transpose=1 writes [cout][27][cin] (taps reversed if flip=1). */
 fe_status fe_nn_pack_weights(const float *d_w, int cin, int cout, int transpose, int flip,
                              void *d_out, fe_stream_t stream);
+/* Stride-1 3x3x3 convolution on the tensor cores (tcgen05.mma, FP32
+ * accumulators in tensor memory); not in the paper, part of the warm start.
+ * Same definition as fe_nn_conv3d(FE_NN_S1, ...), dims_out = dims_in, except
+ * that the activations are rounded to BF16 (nearest even) before the
+ * products: |out - exact| <= (2^-8 + 2 K 2^-24) sum |w| |x|, K = 27 cin + 1.
+ *   d_img: the weights as fe_nn_pack_weights_mma laid them out
+ *   (fe_nn_mma_image_bytes bytes, 16-byte aligned); cout must be 16, 32 or 64.
+ *   d_bias may be NULL; relu != 0 applies ReLU.  Allocates nothing; enqueues
+ *   one kernel on `stream`.  A block whose bounded wait for the tensor cores
+ *   runs out (1 s) stops and raises a flag that fe_nn_tc_check reports. */
+fe_status fe_nn_mma_image_bytes(int cin, int cout, size_t *h_bytes);
+/* Lay out BF16 weights [cin][27][cout] (from fe_nn_pack_weights, either copy)
+ * as the tensor-core operand image: per 16-channel chunk kc, per tap t, the
+ * 8-channel groups kg as cout rows of 16 bytes (channels past cin are 0). */
+fe_status fe_nn_pack_weights_mma(const void *d_w16, int cin, int cout, void *d_img,
+                                 fe_stream_t stream);
+fe_status fe_nn_conv3d_s1_tc(const float *d_in, int cin, const int *h_dims, const void *d_img,
+                             const float *d_bias, float *d_out, int cout, int relu,
+                             fe_stream_t stream);
+/* Synchronises the device; *h_flag = 1 if a tensor-core kernel gave up a wait
+ * since the last call (then clears the flag), else 0. */
+fe_status fe_nn_tc_check(int *h_flag);
+
 /* Scratch of fe_nn_conv3d_weight_grad: per-split partial sums; h_splits gets
  * the split count.  stride 1 or 2; (ca, dims_a) describe the correlation's
  * first operand (dY for S1/S2, X for T2). */

@@ -1,0 +1,369 @@
+// fe_nn_tc.cu -- stride-1 3x3x3 convolution of the warm-start network on the
+// fifth-generation tensor cores (tcgen05.mma, accumulators in tensor memory).
+//
+// out[co][u] = bias[co] + sum_ci sum_t W[ci][t][co] in[ci][u + d_t - 1]  (tap t = 9dz + 3dy + dx)
+//
+// As a GEMM: D[u][co] = sum_k A[u][k] B[co][k] with k = (ci, t).  No im2col
+// copy is made.  A block owns TY output lines of one z-plane; for each chunk
+// of 16 input channels it stages the halo box (3 planes x (TY + 2) lines x
+// (W + 2) points) in shared memory as rows of 16 bytes (one voxel, 8 BF16
+// channels), two 8-channel groups one after the other.  In that layout the
+// operand A of tap t is the same matrix shifted by a whole number of rows,
+// shift(t) = (dz - 1)(TY + 2)(W + 2) + (dy - 1)(W + 2) + (dx - 1), so every
+// tap is one tcgen05.mma whose A descriptor starts shift(t) rows further.
+// The output rows of the tile are a contiguous run of halo rows (the halo
+// columns between lines are computed and dropped), covered by nw windows of
+// 128 rows (M = 128).  B (the chunk's weights, N = cout) is a pre-packed
+// image copied as is.  One thread issues the nw x 27 MMAs of a chunk and
+// commits them to an mbarrier; the FP32 accumulators of the nw windows live
+// in tensor memory until the epilogue reads them (tcgen05.ld), adds the bias,
+// applies ReLU and writes FP32 [C][D][H][W].
+//
+// Operands: activations rounded to BF16 (nearest even), weights BF16, FP32
+// accumulation.  Shared-memory matrix layout: no swizzle, K-major core
+// matrices of 8 rows x 16 bytes; leading offset = distance between the two
+// 8-channel groups, stride offset = 128 bytes (rows are contiguous).
+// Every wait is bounded; a block that gives up sets the error flag read by
+// fe_nn_tc_check, frees its tensor memory and returns.
+#include <cuda_bf16.h>
+
+#include "fe_common.cuh"
+
+namespace fe {
+
+constexpr int kTcThreads = 256;
+constexpr int kTcMaxTY = 8;
+constexpr size_t kTcSmemCap = 200 * 1024;
+
+static __device__ int g_tc_err;
+
+struct TcDims {
+    int d, h, w;
+};
+
+// Tile geometry (host-chosen): TY output lines per tile, W2 = W + 2 halo row
+// length, rows = staged halo rows, rows_pad = rows incl. the zero rows the
+// last window may read, base = halo row of output (y0, x 0), nw = windows.
+struct TcGeom {
+    int ty, w2, rows, rows_pad, base, nw, tmem_cols, ctas_per_sm;
+    size_t smem;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint64_t umma_smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = (uint64_t)((addr >> 4) & 0x3FFF);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;  // descriptor version; base offset 0, no swizzle
+    return d;
+}
+
+// kind::f16 instruction descriptor: D FP32, A and B BF16, both K-major, M x N.
+__host__ __device__ constexpr uint32_t umma_idesc_bf16(int m, int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ long long tc_now() {
+    long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait for phase `parity` of an mbarrier; false if it gave up (1 s).
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+    const long long t0 = tc_now();
+    for (unsigned it = 0; it < (1u << 26); ++it) {
+        uint32_t done;
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(done)
+                     : "r"(mbar), "r"(parity)
+                     : "memory");
+        if (done) return true;
+        if ((it & 255u) == 255u && tc_now() - t0 > 1000000000LL) return false;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t addr, float *v) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                   "=r"(r[7])
+                 : "r"(addr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1)
+k_conv_s1_tc(const float *__restrict__ in, int cin, TcDims dm, const __nv_bfloat16 *__restrict__ wimg,
+             const float *__restrict__ bias, float *__restrict__ out, int cout, int relu, TcGeom g) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_base;
+    __shared__ int s_ok;
+    __shared__ uint64_t s_adesc[27], s_bdesc[27];   // per-tap operand descriptors, window 0
+    unsigned char *sA = smem;                                  // [2][rows_pad][8] bf16
+    unsigned char *sB = smem + (size_t)2 * g.rows_pad * 16;    // [27][2][cout][8] bf16
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int W = dm.w, H = dm.h, D = dm.d, W2 = g.w2, TY = g.ty;
+    const size_t plane = (size_t)D * H * W;
+    const int nty = (H + TY - 1) / TY;
+    const int ntiles = D * nty;
+    const int nkc = (cin + 15) / 16;
+    const size_t chunk_bytes = (size_t)27 * 2 * cout * 16;
+    const uint32_t mbar_a = smem_u32(&mbar);
+
+    if (tid < 27) {
+        const int t = tid, dz = t / 9, dy = (t / 3) % 3, dx = t % 3;
+        const int shift = (dz - 1) * (TY + 2) * W2 + (dy - 1) * W2 + (dx - 1);
+        s_adesc[t] = umma_smem_desc(smem_u32(sA) + (uint32_t)(g.base + shift) * 16, (uint32_t)g.rows_pad * 16, 128);
+        s_bdesc[t] = umma_smem_desc(smem_u32(sB) + (uint32_t)(t * 2 * cout * 16), (uint32_t)cout * 16, 128);
+    }
+    if (tid == 0) {
+        s_ok = 1;
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar_a), "r"(1));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                     "r"(g.tmem_cols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;
+    const uint32_t idesc = umma_idesc_bf16(128, cout);
+    uint32_t phase = 0;
+    bool ok = true;
+
+    for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        const int z = tile / nty, y0 = (tile % nty) * TY;
+        for (int kc = 0; kc < nkc && ok; ++kc) {
+            // stage the halo box of channels kc*16 .. kc*16+15 (zero outside the
+            // grid): four rows per thread per trip, all 64 loads issued first
+            for (int r0 = tid; r0 < g.rows_pad; r0 += 4 * kTcThreads) {
+                float v[4][16];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int r = r0 + i * kTcThreads;
+                    bool inb = false;
+                    size_t gidx = 0;
+                    if (r < g.rows) {
+                        const int pz = r / ((TY + 2) * W2), rem = r % ((TY + 2) * W2);
+                        const int ly = rem / W2, lx = rem % W2;
+                        const int gz = z - 1 + pz, gy = y0 - 1 + ly, gx = lx - 1;
+                        inb = gz >= 0 && gz < D && gy >= 0 && gy < H && gx >= 0 && gx < W;
+                        gidx = inb ? ((size_t)gz * H + gy) * W + gx : 0;
+                    }
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) {
+                        const int ch = kc * 16 + c;
+                        v[i][c] = (inb && ch < cin) ? in[(size_t)ch * plane + gidx] : 0.0f;
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int r = r0 + i * kTcThreads;
+                    if (r >= g.rows_pad) break;
+#pragma unroll
+                    for (int kg = 0; kg < 2; ++kg) {
+                        __nv_bfloat162 h[4];
+#pragma unroll
+                        for (int j = 0; j < 4; ++j)
+                            h[j] = __floats2bfloat162_rn(v[i][8 * kg + 2 * j], v[i][8 * kg + 2 * j + 1]);
+                        *reinterpret_cast<uint4 *>(sA + ((size_t)kg * g.rows_pad + r) * 16) =
+                            *reinterpret_cast<const uint4 *>(h);
+                    }
+                }
+            }
+            // the chunk's weight image
+            const uint4 *src = reinterpret_cast<const uint4 *>(
+                reinterpret_cast<const unsigned char *>(wimg) + (size_t)kc * chunk_bytes);
+            for (size_t i = tid; i < chunk_bytes / 16; i += kTcThreads)
+                reinterpret_cast<uint4 *>(sB)[i] = src[i];
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncthreads();
+            if (tid == 0) {
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                // descriptors advance by one unit per 16-byte row: window w, tap t
+                // is the window-0 descriptor of t plus 128 w (no field overflows:
+                // shared addresses stay below 256 KB)
+                for (int w = 0; w < g.nw; ++w) {
+                    const uint32_t d_tmem = tmem + (uint32_t)(w * cout);
+                    for (int t = 0; t < 27; ++t) {
+                        const uint64_t da = s_adesc[t] + (uint64_t)(128 * w);
+                        const uint32_t acc = (kc > 0 || t > 0) ? 1u : 0u;
+                        asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                                     "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+                                     "l"(da), "l"(s_bdesc[t]), "r"(idesc), "r"(acc));
+                    }
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 mbar_a)
+                             : "memory");
+            }
+            // the MMAs have read the staged chunk (and written D) once this phase completes
+            if (!mbar_wait(mbar_a, phase & 1u)) {
+                atomicExch(&g_tc_err, 1);
+                s_ok = 0;
+            }
+            phase += 1;
+            __syncthreads();
+            ok = s_ok != 0;
+        }
+        if (!ok) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // epilogue: warp q (mod 4) reads TMEM lanes 32q..32q+31; the two warpgroups split the columns
+        const int q = warp & 3, half = warp >> 2;
+        const int c_lo = half * (cout / 2), c_hi = c_lo + cout / 2;
+        for (int w = 0; w < g.nw; ++w) {
+            const int rel = 128 * w + 32 * q + lane;      // row offset from `base`
+            const int yi = rel / W2, x = rel % W2;
+            const int y = y0 + yi;
+            const bool valid = x < W && yi < TY && y < H;
+            const size_t o = ((size_t)z * H + y) * W + x;
+            for (int c0 = c_lo; c0 < c_hi; c0 += 8) {
+                float v[8];
+                tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(w * cout + c0), v);
+                if (valid) {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        float y_ = v[j] + (bias ? bias[c0 + j] : 0.0f);
+                        if (relu) y_ = y_ > 0.0f ? y_ : 0.0f;
+                        out[(size_t)(c0 + j) * plane + o] = y_;
+                    }
+                }
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(g.tmem_cols));
+}
+
+// image[kc][t][kg][n][c] = W[ci = 16 kc + 8 kg + c][t][n] (0 past cin), from
+// the BF16 weights [cin][27][cout].
+__global__ void k_pack_mma(const __nv_bfloat16 *__restrict__ w16, int cin, int cout,
+                           __nv_bfloat16 *__restrict__ img, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const int c = (int)(i % 8);
+        size_t r = i / 8;
+        const int nn = (int)(r % cout);
+        r /= cout;
+        const int kg = (int)(r % 2);
+        r /= 2;
+        const int t = (int)(r % 27);
+        const int kc = (int)(r / 27);
+        const int ci = 16 * kc + 8 * kg + c;
+        img[i] = ci < cin ? w16[((size_t)ci * 27 + t) * cout + nn] : __float2bfloat16(0.0f);
+    }
+}
+
+static int pow2_at_least(int v) {
+    int p = 32;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+// Tile height TY for a W-wide grid: the largest share of useful rows in the
+// 128-row windows, among the shapes whose shared memory and tensor memory fit.
+static bool choose_geom(int w, int h, int cout, TcGeom *out) {
+    bool found = false;
+    double best = -1.0;
+    for (int ty = 1; ty <= kTcMaxTY && ty <= h; ++ty) {
+        TcGeom g;
+        g.ty = ty;
+        g.w2 = w + 2;
+        g.rows = 3 * (ty + 2) * g.w2;
+        g.base = (ty + 2) * g.w2 + g.w2 + 1;
+        g.nw = (ty * g.w2 - 2 + 127) / 128;
+        const int shift_max = (ty + 2) * g.w2 + g.w2 + 1;
+        int need = g.base + 128 * g.nw + shift_max;
+        g.rows_pad = ((need > g.rows ? need : g.rows) + 7) & ~7;
+        g.smem = (size_t)2 * g.rows_pad * 16 + (size_t)27 * 2 * cout * 16;
+        g.tmem_cols = pow2_at_least(g.nw * cout);
+        if (g.smem > kTcSmemCap || g.tmem_cols > 512) continue;
+        int by_smem = (int)((227 * 1024) / (g.smem + 1024));
+        int by_tmem = 512 / g.tmem_cols;
+        g.ctas_per_sm = by_smem < by_tmem ? by_smem : by_tmem;
+        if (g.ctas_per_sm < 1) continue;
+        const double eff = (double)ty * w / (g.nw * 128.0) * (g.ctas_per_sm >= 2 ? 1.0 : 0.85);
+        if (eff > best + 1e-9) {
+            best = eff;
+            *out = g;
+            found = true;
+        }
+    }
+    return found;
+}
+
+}  // namespace fe
+
+using namespace fe;
+
+extern "C" {
+
+fe_status fe_nn_mma_image_bytes(int cin, int cout, size_t *h_bytes) {
+    if (cin < 1 || cout < 1 || !h_bytes) return FE_ERR_ARG;
+    *h_bytes = (size_t)((cin + 15) / 16) * 27 * 2 * cout * 16;
+    return FE_OK;
+}
+
+fe_status fe_nn_pack_weights_mma(const void *d_w16, int cin, int cout, void *d_img, fe_stream_t stream) {
+    if (!d_w16 || !d_img || cin < 1 || cout < 1 || !aligned(d_img, 16)) return FE_ERR_ARG;
+    const size_t n = (size_t)((cin + 15) / 16) * 27 * 2 * cout * 8;
+    const int blocks = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+    k_pack_mma<<<blocks, 256, 0, (cudaStream_t)stream>>>((const __nv_bfloat16 *)d_w16, cin, cout,
+                                                         (__nv_bfloat16 *)d_img, n);
+    FE_TRY_LAUNCH();
+    return FE_OK;
+}
+
+fe_status fe_nn_conv3d_s1_tc(const float *d_in, int cin, const int *h_dims, const void *d_img,
+                             const float *d_bias, float *d_out, int cout, int relu, fe_stream_t stream) {
+    if (!d_in || !d_img || !d_out || cin < 1 || !h_dims || h_dims[0] < 1 || h_dims[1] < 1 || h_dims[2] < 1)
+        return FE_ERR_ARG;
+    if (cout != 16 && cout != 32 && cout != 64) return FE_ERR_ARG;
+    if (!aligned(d_img, 16)) return FE_ERR_ARG;
+    TcGeom g;
+    if (!choose_geom(h_dims[2], h_dims[1], cout, &g)) return FE_ERR_ARG;
+    // request enough shared memory that no more than ctas_per_sm blocks share
+    // an SM, so their tensor-memory allocations always fit together
+    size_t smem = g.smem;
+    const size_t floor_bytes = (size_t)233472 / (size_t)(g.ctas_per_sm + 1) - 1024 + 16;
+    if (smem < floor_bytes) smem = floor_bytes;
+    if (smem > (size_t)232448) smem = 232448;
+    FE_TRY_CUDA(cudaFuncSetAttribute(k_conv_s1_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    FE_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_conv_s1_tc, kTcThreads, smem));
+    if (per_sm < 1) return FE_ERR_CUDA;
+    if (per_sm > g.ctas_per_sm) return FE_ERR_CUDA;       // tensor memory would be oversubscribed
+    const long long ntiles = (long long)h_dims[0] * ((h_dims[1] + g.ty - 1) / g.ty);
+    long long grid = (long long)sm_count() * per_sm;
+    if (grid > ntiles) grid = ntiles;
+    TcDims dm{h_dims[0], h_dims[1], h_dims[2]};
+    k_conv_s1_tc<<<(int)grid, kTcThreads, smem, (cudaStream_t)stream>>>(
+        d_in, cin, dm, (const __nv_bfloat16 *)d_img, d_bias, d_out, cout, relu, g);
+    FE_TRY_LAUNCH();
+    return FE_OK;
+}
+
+fe_status fe_nn_tc_check(int *h_flag) {
+    if (!h_flag) return FE_ERR_ARG;
+    int zero = 0;
+    FE_TRY_CUDA(cudaMemcpyFromSymbol(h_flag, g_tc_err, sizeof(int)));
+    FE_TRY_CUDA(cudaMemcpyToSymbol(g_tc_err, &zero, sizeof(int)));
+    return FE_OK;
+}
+
+}  // extern "C"

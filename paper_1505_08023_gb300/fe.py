@@ -119,6 +119,11 @@ SIGNATURES = {
     "fe_nn_conv3d": (_I32, [ctypes.c_int, _VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _VP, _VP, _VP,
                             ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int, _VP]),
     "fe_nn_pack_weights": (_I32, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, _VP]),
+    "fe_nn_mma_image_bytes": (_I32, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(_SZ)]),
+    "fe_nn_pack_weights_mma": (_I32, [_VP, ctypes.c_int, ctypes.c_int, _VP, _VP]),
+    "fe_nn_conv3d_s1_tc": (_I32, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _VP, _VP, _VP,
+                                  ctypes.c_int, ctypes.c_int, _VP]),
+    "fe_nn_tc_check": (_I32, [ctypes.POINTER(ctypes.c_int)]),
     "fe_nn_corr_workspace": (_I32, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
                                     ctypes.POINTER(_SZ), ctypes.POINTER(ctypes.c_int)]),
     "fe_nn_conv3d_weight_grad": (_I32, [ctypes.c_int, _VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _VP,
@@ -384,6 +389,37 @@ def fe_nn_conv3d(mode, x, cin, dims_in, w_bf16, bias, y, cout, dims_out, relu, s
     return _check("fe_nn_conv3d", load().fe_nn_conv3d(
         int(mode), _ptr(x), int(cin), _dims(dims_in), _ptr(w_bf16), _ptr(bias), _ptr(y), int(cout),
         _dims(dims_out), int(relu), _stream(stream)))
+
+
+TC_COUT = (16, 32, 64)
+
+
+def fe_nn_mma_image_bytes(cin, cout) -> int:
+    n = ctypes.c_size_t(0)
+    _check("fe_nn_mma_image_bytes", load().fe_nn_mma_image_bytes(int(cin), int(cout), ctypes.byref(n)))
+    return n.value
+
+
+def fe_nn_pack_weights_mma(w_bf16, cin, cout, img, stream=None):
+    return _check("fe_nn_pack_weights_mma", load().fe_nn_pack_weights_mma(
+        _ptr(w_bf16), int(cin), int(cout), _ptr(img), _stream(stream)))
+
+
+def fe_nn_conv3d_s1_tc(x, cin, dims, img, bias, y, cout, relu, stream=None):
+    return _check("fe_nn_conv3d_s1_tc", load().fe_nn_conv3d_s1_tc(
+        _ptr(x), int(cin), _dims(dims), _ptr(img), _ptr(bias), _ptr(y), int(cout), int(relu),
+        _stream(stream)))
+
+
+def fe_nn_tc_check() -> int:
+    f = ctypes.c_int(0)
+    _check("fe_nn_tc_check", load().fe_nn_tc_check(ctypes.byref(f)))
+    return f.value
+
+
+def mma_image(cin, cout, device="cuda") -> torch.Tensor:
+    """Buffer for a tensor-core weight image (16-byte aligned)."""
+    return _alloc_bytes(fe_nn_mma_image_bytes(cin, cout), device)
 
 
 def fe_nn_pack_weights(w, cin, cout, transpose, flip, out, stream=None):

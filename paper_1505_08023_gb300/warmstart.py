@@ -46,9 +46,11 @@ def level_dims(n_nodes: int, levels: int = 4):
 
 class Conv:
     """One 3x3x3 layer: FP32 master weights [cin][27][cout], bias, Adam moments,
-    BF16 forward copy and BF16 copy for the data gradient."""
+    BF16 forward copy and BF16 copy for the data gradient; for stride-1 layers
+    also their tensor-core operand images (when the output channel counts
+    allow: 16, 32 or 64)."""
 
-    def __init__(self, name, mode, cin, cout, dev, gen):
+    def __init__(self, name, mode, cin, cout, dev, gen, tensor_cores=True):
         self.name, self.mode, self.cin, self.cout = name, mode, cin, cout
         fan_in = cin * 27
         std = math.sqrt(2.0 / fan_in)
@@ -60,11 +62,21 @@ class Conv:
         self.mb, self.vb = torch.zeros_like(self.b), torch.zeros_like(self.b)
         self.w16 = torch.empty(cin * 27 * cout, dtype=torch.bfloat16, device=dev)
         self.wt16 = torch.empty(cin * 27 * cout, dtype=torch.bfloat16, device=dev)
+        # tensor cores where both channel counts allow it: N (output channels)
+        # 16, 32 or 64, and at least one full 16-channel K chunk (the 2-channel
+        # input layer stays on the CUDA cores, where it is faster)
+        s1 = mode == "s1" and tensor_cores
+        self.img = fe.mma_image(cin, cout, dev) if s1 and cout in fe.TC_COUT and cin >= 16 else None
+        self.imgt = fe.mma_image(cout, cin, dev) if s1 and cin in fe.TC_COUT and cout >= 16 else None
 
     def pack(self):
         fe.fe_nn_pack_weights(self.w, self.cin, self.cout, 0, 0, self.w16)
         flip = 1 if self.mode == "s1" else 0
         fe.fe_nn_pack_weights(self.w, self.cin, self.cout, 1, flip, self.wt16)
+        if self.img is not None:
+            fe.fe_nn_pack_weights_mma(self.w16, self.cin, self.cout, self.img)
+        if self.imgt is not None:
+            fe.fe_nn_pack_weights_mma(self.wt16, self.cout, self.cin, self.imgt)
 
     def params(self):
         return [(self.w, self.gw, self.mw, self.vw), (self.b, self.gb, self.mb, self.vb)]
@@ -74,13 +86,18 @@ ADJOINT = {"s1": "s1", "s2": "t2", "t2": "s2"}
 
 
 class WarmStartNet:
-    def __init__(self, n_nodes: int, channels=CHANNELS, device="cuda", seed: int = 0):
+    """The encoder-decoder.  tensor_cores=True runs the stride-1 layers (and
+    their data gradients) on tcgen05 with BF16 activations; False keeps every
+    layer on the FP32 CUDA-core kernels."""
+
+    def __init__(self, n_nodes: int, channels=CHANNELS, device="cuda", seed: int = 0,
+                 tensor_cores: bool = True):
         self.dev = torch.device(device)
         self.dims = [(d, d, d) for d in level_dims(n_nodes)]
         c0, c1, c2, c3 = channels
         self.ch = channels
         gen = torch.Generator().manual_seed(seed)
-        L = lambda name, mode, ci, co: Conv(name, mode, ci, co, self.dev, gen)
+        L = lambda name, mode, ci, co: Conv(name, mode, ci, co, self.dev, gen, tensor_cores)
         self.layers = {
             "e0": L("e0", "s1", 2, c0), "d1": L("d1", "s2", c0, c1), "e1": L("e1", "s1", c1, c1),
             "d2": L("d2", "s2", c1, c2), "e2": L("e2", "s1", c2, c2), "d3": L("d3", "s2", c2, c3),
@@ -116,8 +133,11 @@ class WarmStartNet:
 
     def conv(self, lname, x, lin, y, lout, relu):
         l = self.layers[lname]
-        fe.fe_nn_conv3d(fe.NN_MODES[l.mode], x, l.cin, self.dims[lin], l.w16, l.b, y, l.cout,
-                        self.dims[lout], relu)
+        if l.img is not None:
+            fe.fe_nn_conv3d_s1_tc(x, l.cin, self.dims[lin], l.img, l.b, y, l.cout, relu)
+        else:
+            fe.fe_nn_conv3d(fe.NN_MODES[l.mode], x, l.cin, self.dims[lin], l.w16, l.b, y, l.cout,
+                            self.dims[lout], relu)
 
     def conv_bwd(self, lname, x, lin, dy, lout, dx):
         """Weight/bias gradients of layer lname; data gradient into dx (if given)."""
@@ -133,8 +153,11 @@ class WarmStartNet:
                                     self.dims[lout], l.gw, self.corr_work)
         fe.fe_nn_channel_sum(dy, l.cout, self.dims[lout], l.gb)
         if dx is not None:
-            fe.fe_nn_conv3d(fe.NN_MODES[ADJOINT[l.mode]], dy, l.cout, self.dims[lout], l.wt16, None,
-                            dx, l.cin, self.dims[lin], 0)
+            if l.imgt is not None:
+                fe.fe_nn_conv3d_s1_tc(dy, l.cout, self.dims[lout], l.imgt, None, dx, l.cin, 0)
+            else:
+                fe.fe_nn_conv3d(fe.NN_MODES[ADJOINT[l.mode]], dy, l.cout, self.dims[lout], l.wt16, None,
+                                dx, l.cin, self.dims[lin], 0)
 
     # ------------------------------------------------------------ forward / backward
     def forward(self, x):

@@ -100,12 +100,64 @@ def test_conv_weight_gradient(fe, mode, cin, cout, dims):
                        rtol=1e-5, atol=1e-4)
 
 
+TC_CASES = [(2, 16, (9, 7, 11)), (16, 32, (17, 17, 17)), (32, 64, (5, 4, 6)), (64, 16, (3, 3, 3)),
+            (16, 16, (4, 3, 129)), (20, 32, (6, 33, 65)), (16, 16, (1, 1, 1))]
+
+
+@pytest.mark.parametrize("cin,cout,dims", TC_CASES)
+def test_conv_s1_tensor_cores(fe, cin, cout, dims):
+    """Stride-1 conv on tcgen05 against the FP64 oracle.  The kernel rounds
+    activations to BF16 (relative error <= 2^-8 per product, nearest even)
+    and accumulates in FP32, so |y - exact| <= (2^-8 + 2 K 2^-24) sum|w||x|.
+    Cases cover partial 16-channel chunks, every allowed cout, grid widths
+    of 129 and 65 (windows that straddle lines), and a single voxel."""
+    x, W, b = layer_setup("s1", cin, cout, dims, 11)
+    w32 = cuda32(W)
+    w16 = torch.empty(cin * 27 * cout, dtype=torch.bfloat16, device="cuda")
+    fe.fe_nn_pack_weights(w32, cin, cout, 0, 0, w16)
+    img = fe.mma_image(cin, cout)
+    fe.fe_nn_pack_weights_mma(w16, cin, cout, img)
+    bound = onn.conv("s1", np.abs(x).astype(np.float64), np.abs(W), np.abs(b))
+    ref = onn.conv("s1", x.astype(np.float64), W, b)
+    K = cin * 27 + 1
+    tol = (2.0 ** -8 + 2 * K * U32) * bound + 1e-30
+    y = torch.full((cout,) + dims, float("nan"), dtype=torch.float32, device="cuda")
+    for relu in (0, 1):
+        fe.fe_nn_conv3d_s1_tc(cuda32(x), cin, dims, img, cuda32(b), y, cout, relu)
+        want = np.maximum(ref, 0) if relu else ref
+        got = y.cpu().numpy()
+        assert np.all(np.isfinite(got))
+        assert np.all(np.abs(got - want) <= tol), float(np.max(np.abs(got - want) / tol))
+    assert fe.fe_nn_tc_check() == 0
+    # the data-gradient copy (transposed, flipped taps) runs through the same kernel
+    if cout in fe.TC_COUT and cin in fe.TC_COUT:
+        dy = np.random.default_rng(12).standard_normal((cout,) + dims).astype(np.float32)
+        wt16 = torch.empty(cin * 27 * cout, dtype=torch.bfloat16, device="cuda")
+        fe.fe_nn_pack_weights(w32, cin, cout, 1, 1, wt16)
+        imgt = fe.mma_image(cout, cin)
+        fe.fe_nn_pack_weights_mma(wt16, cout, cin, imgt)
+        dx = torch.empty((cin,) + dims, dtype=torch.float32, device="cuda")
+        fe.fe_nn_conv3d_s1_tc(cuda32(dy), cout, dims, imgt, None, dx, cin, 0)
+        refx = onn.conv_grad_x("s1", dy.astype(np.float64), W, dims)
+        bx = onn.conv_grad_x("s1", np.abs(dy).astype(np.float64), np.abs(W), dims)
+        tolx = (2.0 ** -8 + 2 * cout * 27 * U32) * bx + 1e-30
+        assert np.all(np.abs(dx.cpu().numpy() - refx) <= tolx)
+
+
+def test_conv_s1_tensor_cores_rejects_bad_cout(fe):
+    x = torch.zeros((16, 3, 3, 3), device="cuda")
+    img = fe.mma_image(16, 24)
+    y = torch.zeros((24, 3, 3, 3), device="cuda")
+    with pytest.raises(fe.FeError):
+        fe.fe_nn_conv3d_s1_tc(x, 16, (3, 3, 3), img, None, y, 24, 0)
+
+
 def test_network_gradients_match_oracle(fe):
     from paper_1505_08023_gb300 import warmstart as ws
     n = 9
     ch = (3, 4, 4, 5)
     g = np.random.default_rng(6)
-    net = ws.WarmStartNet(n, channels=ch)
+    net = ws.WarmStartNet(n, channels=ch, tensor_cores=False)
     params = {}
     for name, l in net.layers.items():
         W = bf16(0.3 * g.standard_normal((l.cin, 27, l.cout)))
