@@ -401,6 +401,19 @@ fe_status fe_nn_pack_weights_mma(const void *d_w16, int cin, int cout, void *d_i
 fe_status fe_nn_conv3d_s1_tc(const float *d_in, int cin, const int *h_dims, const void *d_img,
                              const float *d_bias, float *d_out, int cout, int relu,
                              fe_stream_t stream);
+/* Transposed stride-2 convolution (fe_nn_conv3d(FE_NN_T2, ...)) on the tensor
+ * cores, same contract and bound as fe_nn_conv3d_s1_tc; h_dims_out must be
+ * 2 (h_dims_in - 1) + 1.  The eight output parity classes are separate
+ * accumulators; each (class, tap) pair is one MMA on the shifted input box. */
+fe_status fe_nn_conv3d_t2_tc(const float *d_in, int cin, const int *h_dims_in, const void *d_img,
+                             const float *d_bias, float *d_out, int cout, const int *h_dims_out,
+                             int relu, fe_stream_t stream);
+/* Stride-2 convolution (fe_nn_conv3d(FE_NN_S2, ...)) on the tensor cores,
+ * same contract and bound; h_dims_out must be (h_dims_in - 1) / 2 + 1.  The
+ * fine input box is staged as eight parity sub-boxes on the coarse lattice. */
+fe_status fe_nn_conv3d_s2_tc(const float *d_in, int cin, const int *h_dims_in, const void *d_img,
+                             const float *d_bias, float *d_out, int cout, const int *h_dims_out,
+                             int relu, fe_stream_t stream);
 /* Synchronises the device; *h_flag = 1 if a tensor-core kernel gave up a wait
  * since the last call (then clears the flag), else 0. */
 fe_status fe_nn_tc_check(int *h_flag);

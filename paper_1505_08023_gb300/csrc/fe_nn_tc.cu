@@ -1,5 +1,6 @@
-// fe_nn_tc.cu -- stride-1 3x3x3 convolution of the warm-start network on the
-// fifth-generation tensor cores (tcgen05.mma, accumulators in tensor memory).
+// fe_nn_tc.cu -- the 3x3x3 convolutions of the warm-start network (stride 1,
+// stride 2, transposed stride 2) on the fifth-generation tensor cores
+// (tcgen05.mma, accumulators in tensor memory).
 //
 // out[co][u] = bias[co] + sum_ci sum_t W[ci][t][co] in[ci][u + d_t - 1]  (tap t = 9dz + 3dy + dx)
 //
@@ -46,6 +47,8 @@ struct TcDims {
 // last window may read, base = halo row of output (y0, x 0), nw = windows.
 struct TcGeom {
     int ty, w2, rows, rows_pad, base, nw, tmem_cols, ctas_per_sm;
+    int hlo, ly, pz;   // halo below the tile (1: stride 1, 0: transposed), lines and planes staged
+    int rsub;          // stride 2: rows of one of the eight parity sub-boxes
     size_t smem;
 };
 
@@ -99,30 +102,78 @@ __device__ __forceinline__ void tmem_ld8(uint32_t addr, float *v) {
     for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
 }
 
+// Stride 2 (FE_NN_S2) stages the fine input box as eight parity sub-boxes
+// on the coarse output lattice, so that each tap again reads one sub-box at
+// a uniform shift.
+// MODE = FE_NN_S1 (one class, all 27 taps, dout = din) or FE_NN_T2 (the
+// transposed stride-2 layer: eight output parity classes p, output 2v + p of
+// input position v; per axis p = 0 takes tap d = 1 at offset 0, p = 1 takes
+// d = 0 at offset +1 and d = 2 at offset 0 -- 27 (class, tap) pairs in all,
+// each an MMA on the input box shifted by its offsets; class c accumulates
+// in its own tensor-memory columns).
+template <int MODE>
 __global__ void __launch_bounds__(kTcThreads, 1)
-k_conv_s1_tc(const float *__restrict__ in, int cin, TcDims dm, const __nv_bfloat16 *__restrict__ wimg,
-             const float *__restrict__ bias, float *__restrict__ out, int cout, int relu, TcGeom g) {
+k_conv_tc(const float *__restrict__ in, int cin, TcDims dm, const __nv_bfloat16 *__restrict__ wimg,
+          const float *__restrict__ bias, float *__restrict__ out, int cout, TcDims dout, int relu, TcGeom g) {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_base;
     __shared__ int s_ok;
-    __shared__ uint64_t s_adesc[27], s_bdesc[27];   // per-tap operand descriptors, window 0
+    __shared__ uint64_t s_adesc[27], s_bdesc[27];   // per (class, tap) operand descriptors, window 0
+    __shared__ int s_col[27];                       // tensor-memory column of the entry's class
+    __shared__ int s_first[27];                     // 1 for the first entry of a class
     unsigned char *sA = smem;                                  // [2][rows_pad][8] bf16
     unsigned char *sB = smem + (size_t)2 * g.rows_pad * 16;    // [27][2][cout][8] bf16
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int W = dm.w, H = dm.h, D = dm.d, W2 = g.w2, TY = g.ty;
+    const int W = dm.w, H = dm.h, D = dm.d, W2 = g.w2, TY = g.ty, LY = g.ly, HLO = g.hlo;
     const size_t plane = (size_t)D * H * W;
-    const int nty = (H + TY - 1) / TY;
-    const int ntiles = D * nty;
+    const size_t oplane = (size_t)dout.d * dout.h * dout.w;
+    // tiles run over the grid whose positions the MMA rows stand for: the
+    // output grid for stride 2, the input grid otherwise
+    const int TD = MODE == FE_NN_S2 ? dout.d : D, TH = MODE == FE_NN_S2 ? dout.h : H;
+    const int TW = MODE == FE_NN_S2 ? dout.w : W;
+    const int nty = (TH + TY - 1) / TY;
+    const int ntiles = TD * nty;
     const int nkc = (cin + 15) / 16;
     const size_t chunk_bytes = (size_t)27 * 2 * cout * 16;
     const uint32_t mbar_a = smem_u32(&mbar);
 
-    if (tid < 27) {
-        const int t = tid, dz = t / 9, dy = (t / 3) % 3, dx = t % 3;
-        const int shift = (dz - 1) * (TY + 2) * W2 + (dy - 1) * W2 + (dx - 1);
-        s_adesc[t] = umma_smem_desc(smem_u32(sA) + (uint32_t)(g.base + shift) * 16, (uint32_t)g.rows_pad * 16, 128);
-        s_bdesc[t] = umma_smem_desc(smem_u32(sB) + (uint32_t)(t * 2 * cout * 16), (uint32_t)cout * 16, 128);
+    if (tid == 0) {
+        int e = 0;
+        const int ncls = MODE == FE_NN_T2 ? 8 : 1;
+        for (int c = 0; c < ncls; ++c) {
+            const int pz = (c >> 2) & 1, py = (c >> 1) & 1, px = c & 1;
+            const int nz = MODE == FE_NN_T2 ? (pz ? 2 : 1) : 3;
+            const int ny = MODE == FE_NN_T2 ? (py ? 2 : 1) : 3;
+            const int nx = MODE == FE_NN_T2 ? (px ? 2 : 1) : 3;
+            for (int iz = 0; iz < nz; ++iz)
+                for (int iy = 0; iy < ny; ++iy)
+                    for (int ix = 0; ix < nx; ++ix) {
+                        int dz, dy, dx, oz, oy, ox, sub = 0;
+                        if (MODE == FE_NN_S2) {
+                            // fine input 2v + d - 1: d = 1 is the even point v,
+                            // d = 0 the odd point v - 1, d = 2 the odd point v
+                            dz = iz; dy = iy; dx = ix;
+                            oz = iz == 0 ? -1 : 0; oy = iy == 0 ? -1 : 0; ox = ix == 0 ? -1 : 0;
+                            sub = ((iz != 1) << 2) | ((iy != 1) << 1) | (ix != 1);
+                        } else if (MODE == FE_NN_T2) {
+                            dz = pz ? 2 * iz : 1; oz = pz ? 1 - iz : 0;
+                            dy = py ? 2 * iy : 1; oy = py ? 1 - iy : 0;
+                            dx = px ? 2 * ix : 1; ox = px ? 1 - ix : 0;
+                        } else {
+                            dz = iz; dy = iy; dx = ix;
+                            oz = iz - 1; oy = iy - 1; ox = ix - 1;
+                        }
+                        const int t = 9 * dz + 3 * dy + dx;
+                        const int shift = sub * g.rsub + oz * LY * W2 + oy * W2 + ox;
+                        s_adesc[e] = umma_smem_desc(smem_u32(sA) + (uint32_t)(g.base + shift) * 16,
+                                                    (uint32_t)g.rows_pad * 16, 128);
+                        s_bdesc[e] = umma_smem_desc(smem_u32(sB) + (uint32_t)(t * 2 * cout * 16), (uint32_t)cout * 16, 128);
+                        s_col[e] = c * g.nw * cout;
+                        s_first[e] = (iz == 0 && iy == 0 && ix == 0) ? 1 : 0;
+                        ++e;
+                    }
+        }
     }
     if (tid == 0) {
         s_ok = 1;
@@ -155,9 +206,23 @@ k_conv_s1_tc(const float *__restrict__ in, int cin, TcDims dm, const __nv_bfloat
                     bool inb = false;
                     size_t gidx = 0;
                     if (r < g.rows) {
-                        const int pz = r / ((TY + 2) * W2), rem = r % ((TY + 2) * W2);
-                        const int ly = rem / W2, lx = rem % W2;
-                        const int gz = z - 1 + pz, gy = y0 - 1 + ly, gx = lx - 1;
+                        int gz, gy, gx;
+                        if (MODE == FE_NN_S2) {
+                            // parity sub-box s holds the fine points 2c + parity(s)
+                            // of coarse positions c = tile origin - 1 + (a, b, x)
+                            const int sb = r / g.rsub, rr = r % g.rsub;
+                            const int a = rr / (LY * W2), rem = rr % (LY * W2);
+                            const int b = rem / W2, xx = rem % W2;
+                            gz = 2 * (z - 1 + a) + ((sb >> 2) & 1);
+                            gy = 2 * (y0 - 1 + b) + ((sb >> 1) & 1);
+                            gx = 2 * (xx - 1) + (sb & 1);
+                        } else {
+                            const int pz = r / (LY * W2), rem = r % (LY * W2);
+                            const int ly = rem / W2, lx = rem % W2;
+                            gz = z - HLO + pz;
+                            gy = y0 - HLO + ly;
+                            gx = lx - HLO;
+                        }
                         inb = gz >= 0 && gz < D && gy >= 0 && gy < H && gx >= 0 && gx < W;
                         gidx = inb ? ((size_t)gz * H + gy) * W + gx : 0;
                     }
@@ -195,14 +260,15 @@ k_conv_s1_tc(const float *__restrict__ in, int cin, TcDims dm, const __nv_bfloat
                 // descriptors advance by one unit per 16-byte row: window w, tap t
                 // is the window-0 descriptor of t plus 128 w (no field overflows:
                 // shared addresses stay below 256 KB)
-                for (int w = 0; w < g.nw; ++w) {
-                    const uint32_t d_tmem = tmem + (uint32_t)(w * cout);
-                    for (int t = 0; t < 27; ++t) {
-                        const uint64_t da = s_adesc[t] + (uint64_t)(128 * w);
-                        const uint32_t acc = (kc > 0 || t > 0) ? 1u : 0u;
+                for (int e = 0; e < 27; ++e) {
+                    const uint32_t acc = (kc > 0 || !s_first[e]) ? 1u : 0u;
+                    const uint64_t db = s_bdesc[e];
+                    for (int w = 0; w < g.nw; ++w) {
+                        const uint32_t d_tmem = tmem + (uint32_t)(s_col[e] + w * cout);
+                        const uint64_t da = s_adesc[e] + (uint64_t)(128 * w);
                         asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
                                      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-                                     "l"(da), "l"(s_bdesc[t]), "r"(idesc), "r"(acc));
+                                     "l"(da), "l"(db), "r"(idesc), "r"(acc));
                     }
                 }
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -223,21 +289,32 @@ k_conv_s1_tc(const float *__restrict__ in, int cin, TcDims dm, const __nv_bfloat
         // epilogue: warp q (mod 4) reads TMEM lanes 32q..32q+31; the two warpgroups split the columns
         const int q = warp & 3, half = warp >> 2;
         const int c_lo = half * (cout / 2), c_hi = c_lo + cout / 2;
-        for (int w = 0; w < g.nw; ++w) {
-            const int rel = 128 * w + 32 * q + lane;      // row offset from `base`
-            const int yi = rel / W2, x = rel % W2;
-            const int y = y0 + yi;
-            const bool valid = x < W && yi < TY && y < H;
-            const size_t o = ((size_t)z * H + y) * W + x;
-            for (int c0 = c_lo; c0 < c_hi; c0 += 8) {
-                float v[8];
-                tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(w * cout + c0), v);
-                if (valid) {
+        const int ncls = MODE == FE_NN_T2 ? 8 : 1;
+        for (int cls = 0; cls < ncls; ++cls) {
+            const int pz = (cls >> 2) & 1, py = (cls >> 1) & 1, px = cls & 1;
+            for (int w = 0; w < g.nw; ++w) {
+                const int rel = 128 * w + 32 * q + lane;      // row offset from `base`
+                const int yi = rel / W2, x = rel % W2;
+                const int y = y0 + yi;
+                bool valid = x < TW && yi < TY && y < TH;
+                int oz = z, oy = y, ox = x;                    // output position
+                if (MODE == FE_NN_T2) {
+                    oz = 2 * z + pz;
+                    oy = 2 * y + py;
+                    ox = 2 * x + px;
+                    valid = valid && oz < dout.d && oy < dout.h && ox < dout.w;
+                }
+                const size_t o = ((size_t)oz * dout.h + oy) * dout.w + ox;
+                for (int c0 = c_lo; c0 < c_hi; c0 += 8) {
+                    float v[8];
+                    tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)((cls * g.nw + w) * cout + c0), v);
+                    if (valid) {
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        float y_ = v[j] + (bias ? bias[c0 + j] : 0.0f);
-                        if (relu) y_ = y_ > 0.0f ? y_ : 0.0f;
-                        out[(size_t)(c0 + j) * plane + o] = y_;
+                        for (int j = 0; j < 8; ++j) {
+                            float y_ = v[j] + (bias ? bias[c0 + j] : 0.0f);
+                            if (relu) y_ = y_ > 0.0f ? y_ : 0.0f;
+                            out[(size_t)(c0 + j) * oplane + o] = y_;
+                        }
                     }
                 }
             }
@@ -275,23 +352,44 @@ static int pow2_at_least(int v) {
     return p;
 }
 
-// Tile height TY for a W-wide grid: the largest share of useful rows in the
-// 128-row windows, among the shapes whose shared memory and tensor memory fit.
-static bool choose_geom(int w, int h, int cout, TcGeom *out) {
+// Tile height TY for a W-wide input grid: the largest share of useful rows
+// in the 128-row windows, among the shapes whose shared memory and tensor
+// memory fit.  Stride 1 stages a halo of one point on each side; the
+// transposed layer only reads offsets 0 and +1, so its box starts at the tile.
+static bool choose_geom(int mode, int w, int h, int cout, TcGeom *out) {
     bool found = false;
     double best = -1.0;
+    const int classes = mode == FE_NN_T2 ? 8 : 1;
     for (int ty = 1; ty <= kTcMaxTY && ty <= h; ++ty) {
         TcGeom g;
         g.ty = ty;
-        g.w2 = w + 2;
-        g.rows = 3 * (ty + 2) * g.w2;
-        g.base = (ty + 2) * g.w2 + g.w2 + 1;
-        g.nw = (ty * g.w2 - 2 + 127) / 128;
-        const int shift_max = (ty + 2) * g.w2 + g.w2 + 1;
-        int need = g.base + 128 * g.nw + shift_max;
+        int shift_max;
+        if (mode == FE_NN_S2) {
+            // eight parity sub-boxes, each 2 planes x (TY + 1) lines x (W + 1)
+            // coarse positions starting one before the tile
+            g.hlo = 1;
+            g.ly = ty + 1;
+            g.pz = 2;
+            g.w2 = w + 1;
+            g.rsub = g.pz * g.ly * g.w2;
+            g.rows = 8 * g.rsub;
+            g.base = g.ly * g.w2 + g.w2 + 1;
+            shift_max = 7 * g.rsub;
+        } else {
+            g.hlo = mode == FE_NN_S1 ? 1 : 0;
+            g.ly = ty + 1 + g.hlo;
+            g.pz = 2 + g.hlo;
+            g.w2 = w + 1 + g.hlo;
+            g.rows = g.pz * g.ly * g.w2;
+            g.rsub = g.rows;
+            g.base = g.hlo * (g.ly * g.w2 + g.w2 + 1);
+            shift_max = g.ly * g.w2 + g.w2 + 1;
+        }
+        g.nw = ((ty - 1) * g.w2 + w + 127) / 128;
+        const int need = g.base + 128 * g.nw + shift_max;
         g.rows_pad = ((need > g.rows ? need : g.rows) + 7) & ~7;
         g.smem = (size_t)2 * g.rows_pad * 16 + (size_t)27 * 2 * cout * 16;
-        g.tmem_cols = pow2_at_least(g.nw * cout);
+        g.tmem_cols = pow2_at_least(classes * g.nw * cout);
         if (g.smem > kTcSmemCap || g.tmem_cols > 512) continue;
         int by_smem = (int)((227 * 1024) / (g.smem + 1024));
         int by_tmem = 512 / g.tmem_cols;
@@ -305,6 +403,38 @@ static bool choose_geom(int w, int h, int cout, TcGeom *out) {
         }
     }
     return found;
+}
+
+template <int MODE>
+static fe_status launch_tc(const float *d_in, int cin, const int *h_dims, const void *d_img, const float *d_bias,
+                           float *d_out, int cout, const int *h_dims_out, int relu, cudaStream_t stream) {
+    if (cout != 16 && cout != 32 && cout != 64) return FE_ERR_ARG;
+    if (!aligned(d_img, 16)) return FE_ERR_ARG;
+    // the MMA rows stand for output positions (stride 2) or input positions
+    const int *tdims = MODE == FE_NN_S2 ? h_dims_out : h_dims;
+    TcGeom g;
+    if (!choose_geom(MODE, tdims[2], tdims[1], cout, &g)) return FE_ERR_ARG;
+    // request enough shared memory that no more than ctas_per_sm blocks share
+    // an SM, so their tensor-memory allocations always fit together
+    size_t smem = g.smem;
+    const size_t floor_bytes = (size_t)233472 / (size_t)(g.ctas_per_sm + 1) - 1024 + 16;
+    if (smem < floor_bytes) smem = floor_bytes;
+    if (smem > (size_t)232448) smem = 232448;
+    auto kern = k_conv_tc<MODE>;
+    FE_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    FE_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTcThreads, smem));
+    if (per_sm < 1) return FE_ERR_CUDA;
+    if (per_sm > g.ctas_per_sm) return FE_ERR_CUDA;       // tensor memory would be oversubscribed
+    const long long ntiles = (long long)tdims[0] * ((tdims[1] + g.ty - 1) / g.ty);
+    long long grid = (long long)sm_count() * per_sm;
+    if (grid > ntiles) grid = ntiles;
+    TcDims dm{h_dims[0], h_dims[1], h_dims[2]};
+    TcDims dout{h_dims_out[0], h_dims_out[1], h_dims_out[2]};
+    kern<<<(int)grid, kTcThreads, smem, stream>>>(d_in, cin, dm, (const __nv_bfloat16 *)d_img, d_bias, d_out,
+                                                   cout, dout, relu, g);
+    FE_TRY_LAUNCH();
+    return FE_OK;
 }
 
 }  // namespace fe
@@ -333,29 +463,27 @@ fe_status fe_nn_conv3d_s1_tc(const float *d_in, int cin, const int *h_dims, cons
                              const float *d_bias, float *d_out, int cout, int relu, fe_stream_t stream) {
     if (!d_in || !d_img || !d_out || cin < 1 || !h_dims || h_dims[0] < 1 || h_dims[1] < 1 || h_dims[2] < 1)
         return FE_ERR_ARG;
-    if (cout != 16 && cout != 32 && cout != 64) return FE_ERR_ARG;
-    if (!aligned(d_img, 16)) return FE_ERR_ARG;
-    TcGeom g;
-    if (!choose_geom(h_dims[2], h_dims[1], cout, &g)) return FE_ERR_ARG;
-    // request enough shared memory that no more than ctas_per_sm blocks share
-    // an SM, so their tensor-memory allocations always fit together
-    size_t smem = g.smem;
-    const size_t floor_bytes = (size_t)233472 / (size_t)(g.ctas_per_sm + 1) - 1024 + 16;
-    if (smem < floor_bytes) smem = floor_bytes;
-    if (smem > (size_t)232448) smem = 232448;
-    FE_TRY_CUDA(cudaFuncSetAttribute(k_conv_s1_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int per_sm = 0;
-    FE_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_conv_s1_tc, kTcThreads, smem));
-    if (per_sm < 1) return FE_ERR_CUDA;
-    if (per_sm > g.ctas_per_sm) return FE_ERR_CUDA;       // tensor memory would be oversubscribed
-    const long long ntiles = (long long)h_dims[0] * ((h_dims[1] + g.ty - 1) / g.ty);
-    long long grid = (long long)sm_count() * per_sm;
-    if (grid > ntiles) grid = ntiles;
-    TcDims dm{h_dims[0], h_dims[1], h_dims[2]};
-    k_conv_s1_tc<<<(int)grid, kTcThreads, smem, (cudaStream_t)stream>>>(
-        d_in, cin, dm, (const __nv_bfloat16 *)d_img, d_bias, d_out, cout, relu, g);
-    FE_TRY_LAUNCH();
-    return FE_OK;
+    return launch_tc<FE_NN_S1>(d_in, cin, h_dims, d_img, d_bias, d_out, cout, h_dims, relu, (cudaStream_t)stream);
+}
+
+fe_status fe_nn_conv3d_t2_tc(const float *d_in, int cin, const int *h_dims_in, const void *d_img,
+                             const float *d_bias, float *d_out, int cout, const int *h_dims_out, int relu,
+                             fe_stream_t stream) {
+    if (!d_in || !d_img || !d_out || cin < 1 || !h_dims_in || !h_dims_out) return FE_ERR_ARG;
+    for (int i = 0; i < 3; ++i)
+        if (h_dims_in[i] < 1 || h_dims_out[i] != 2 * (h_dims_in[i] - 1) + 1) return FE_ERR_ARG;
+    return launch_tc<FE_NN_T2>(d_in, cin, h_dims_in, d_img, d_bias, d_out, cout, h_dims_out, relu,
+                               (cudaStream_t)stream);
+}
+
+fe_status fe_nn_conv3d_s2_tc(const float *d_in, int cin, const int *h_dims_in, const void *d_img,
+                             const float *d_bias, float *d_out, int cout, const int *h_dims_out, int relu,
+                             fe_stream_t stream) {
+    if (!d_in || !d_img || !d_out || cin < 1 || !h_dims_in || !h_dims_out) return FE_ERR_ARG;
+    for (int i = 0; i < 3; ++i)
+        if (h_dims_in[i] < 1 || h_dims_out[i] != (h_dims_in[i] - 1) / 2 + 1) return FE_ERR_ARG;
+    return launch_tc<FE_NN_S2>(d_in, cin, h_dims_in, d_img, d_bias, d_out, cout, h_dims_out, relu,
+                               (cudaStream_t)stream);
 }
 
 fe_status fe_nn_tc_check(int *h_flag) {

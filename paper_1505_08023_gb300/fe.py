@@ -123,6 +123,10 @@ SIGNATURES = {
     "fe_nn_pack_weights_mma": (_I32, [_VP, ctypes.c_int, ctypes.c_int, _VP, _VP]),
     "fe_nn_conv3d_s1_tc": (_I32, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _VP, _VP, _VP,
                                   ctypes.c_int, ctypes.c_int, _VP]),
+    "fe_nn_conv3d_t2_tc": (_I32, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _VP, _VP, _VP,
+                                  ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int, _VP]),
+    "fe_nn_conv3d_s2_tc": (_I32, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _VP, _VP, _VP,
+                                  ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int, _VP]),
     "fe_nn_tc_check": (_I32, [ctypes.POINTER(ctypes.c_int)]),
     "fe_nn_corr_workspace": (_I32, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
                                     ctypes.POINTER(_SZ), ctypes.POINTER(ctypes.c_int)]),
@@ -409,6 +413,27 @@ def fe_nn_conv3d_s1_tc(x, cin, dims, img, bias, y, cout, relu, stream=None):
     return _check("fe_nn_conv3d_s1_tc", load().fe_nn_conv3d_s1_tc(
         _ptr(x), int(cin), _dims(dims), _ptr(img), _ptr(bias), _ptr(y), int(cout), int(relu),
         _stream(stream)))
+
+
+def fe_nn_conv3d_t2_tc(x, cin, dims_in, img, bias, y, cout, dims_out, relu, stream=None):
+    return _check("fe_nn_conv3d_t2_tc", load().fe_nn_conv3d_t2_tc(
+        _ptr(x), int(cin), _dims(dims_in), _ptr(img), _ptr(bias), _ptr(y), int(cout), _dims(dims_out),
+        int(relu), _stream(stream)))
+
+
+def fe_nn_conv3d_s2_tc(x, cin, dims_in, img, bias, y, cout, dims_out, relu, stream=None):
+    return _check("fe_nn_conv3d_s2_tc", load().fe_nn_conv3d_s2_tc(
+        _ptr(x), int(cin), _dims(dims_in), _ptr(img), _ptr(bias), _ptr(y), int(cout), _dims(dims_out),
+        int(relu), _stream(stream)))
+
+
+def conv3d_tc(mode, x, cin, dims_in, img, bias, y, cout, dims_out, relu, stream=None):
+    """The tensor-core convolution of `mode` ("s1", "s2" or "t2")."""
+    if mode == "s1":
+        return fe_nn_conv3d_s1_tc(x, cin, dims_in, img, bias, y, cout, relu, stream)
+    if mode == "s2":
+        return fe_nn_conv3d_s2_tc(x, cin, dims_in, img, bias, y, cout, dims_out, relu, stream)
+    return fe_nn_conv3d_t2_tc(x, cin, dims_in, img, bias, y, cout, dims_out, relu, stream)
 
 
 def fe_nn_tc_check() -> int:

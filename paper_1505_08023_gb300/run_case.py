@@ -6,7 +6,9 @@ Builds the N x N x N problem through the C ABI (mesh, assembly, conversion to
 --format), then runs, as asked: one stand-alone SpMV (--spmv), the fused FP64
 CG for --cg-steps steps (tol 0, or to --tol when --cg-steps is 0), the
 single-reduction CG for --sr-steps steps, and the mixed-precision
-reliable-update solve for --mixed-steps FP32 steps.  With
+reliable-update solve for --mixed-steps FP32 steps; or, with --conv, one
+stride-1 convolution of the warm-start network (tensor-core and CUDA-core
+kernels).  With
 --drop-csr the CSR arrays are released after conversion (smaller footprint
 for profiler captures that save and restore device memory).  Prints one line
 per step taken.
@@ -32,7 +34,13 @@ def main():
     ap.add_argument("--mixed-steps", type=int, default=0)
     ap.add_argument("--mixed-values", choices=["f32", "bf16"], default="f32")
     ap.add_argument("--drop-csr", action="store_true")
+    ap.add_argument("--conv", type=int, nargs=3, metavar=("CIN", "COUT", "N"), default=None,
+                    help="instead of the solver: one stride-1 conv of the warm-start network on an "
+                         "N^3 grid, tensor-core kernel then CUDA-core kernel")
     a = ap.parse_args()
+    if a.conv is not None:
+        run_conv(*a.conv)
+        return
 
     s = fe.System(a.n).build()
     A = s.matrix(a.format, "f64")
@@ -61,6 +69,25 @@ def main():
         print(f"mixed: status {r.status} fp32 steps {r.inner_iterations} "
               f"refinements {r.outer_iterations} relres {r.relres:.3e}")
     torch.cuda.synchronize()
+
+
+def run_conv(cin: int, cout: int, n: int):
+    dims = (n, n, n)
+    g = torch.Generator(device="cuda").manual_seed(0)
+    x = torch.randn((cin,) + dims, device="cuda", generator=g)
+    w = torch.randn(cin, 27, cout, device="cuda", generator=g) * 0.1
+    w16 = torch.empty(cin * 27 * cout, dtype=torch.bfloat16, device="cuda")
+    fe.fe_nn_pack_weights(w, cin, cout, 0, 0, w16)
+    b = torch.zeros(cout, device="cuda")
+    y = torch.empty((cout,) + dims, device="cuda")
+    if cout in fe.TC_COUT:
+        img = fe.mma_image(cin, cout)
+        fe.fe_nn_pack_weights_mma(w16, cin, cout, img)
+        fe.fe_nn_conv3d_s1_tc(x, cin, dims, img, b, y, cout, 1)
+        print(f"tensor-core conv {cin}->{cout} on {n}^3 done, wait flag {fe.fe_nn_tc_check()}")
+    fe.fe_nn_conv3d(fe.NN_MODES["s1"], x, cin, dims, w16, b, y, cout, dims, 1)
+    torch.cuda.synchronize()
+    print(f"CUDA-core conv {cin}->{cout} on {n}^3 done")
 
 
 if __name__ == "__main__":

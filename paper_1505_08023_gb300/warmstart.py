@@ -65,9 +65,10 @@ class Conv:
         # tensor cores where both channel counts allow it: N (output channels)
         # 16, 32 or 64, and at least one full 16-channel K chunk (the 2-channel
         # input layer stays on the CUDA cores, where it is faster)
-        s1 = mode == "s1" and tensor_cores
-        self.img = fe.mma_image(cin, cout, dev) if s1 and cout in fe.TC_COUT and cin >= 16 else None
-        self.imgt = fe.mma_image(cout, cin, dev) if s1 and cin in fe.TC_COUT and cout >= 16 else None
+        # every mode runs forward and data gradient (its adjoint mode) on tcgen05
+        fwd_tc = bwd_tc = tensor_cores
+        self.img = fe.mma_image(cin, cout, dev) if fwd_tc and cout in fe.TC_COUT and cin >= 16 else None
+        self.imgt = fe.mma_image(cout, cin, dev) if bwd_tc and cin in fe.TC_COUT and cout >= 16 else None
 
     def pack(self):
         fe.fe_nn_pack_weights(self.w, self.cin, self.cout, 0, 0, self.w16)
@@ -86,9 +87,10 @@ ADJOINT = {"s1": "s1", "s2": "t2", "t2": "s2"}
 
 
 class WarmStartNet:
-    """The encoder-decoder.  tensor_cores=True runs the stride-1 layers (and
-    their data gradients) on tcgen05 with BF16 activations; False keeps every
-    layer on the FP32 CUDA-core kernels."""
+    """The encoder-decoder.  tensor_cores=True runs every 3x3x3 layer with at
+    least 16 input and 16/32/64 output channels (forward and data gradient)
+    on tcgen05 with BF16 activations; False keeps every layer on the FP32
+    CUDA-core kernels."""
 
     def __init__(self, n_nodes: int, channels=CHANNELS, device="cuda", seed: int = 0,
                  tensor_cores: bool = True):
@@ -134,7 +136,7 @@ class WarmStartNet:
     def conv(self, lname, x, lin, y, lout, relu):
         l = self.layers[lname]
         if l.img is not None:
-            fe.fe_nn_conv3d_s1_tc(x, l.cin, self.dims[lin], l.img, l.b, y, l.cout, relu)
+            fe.conv3d_tc(l.mode, x, l.cin, self.dims[lin], l.img, l.b, y, l.cout, self.dims[lout], relu)
         else:
             fe.fe_nn_conv3d(fe.NN_MODES[l.mode], x, l.cin, self.dims[lin], l.w16, l.b, y, l.cout,
                             self.dims[lout], relu)
@@ -154,7 +156,8 @@ class WarmStartNet:
         fe.fe_nn_channel_sum(dy, l.cout, self.dims[lout], l.gb)
         if dx is not None:
             if l.imgt is not None:
-                fe.fe_nn_conv3d_s1_tc(dy, l.cout, self.dims[lout], l.imgt, None, dx, l.cin, 0)
+                fe.conv3d_tc(ADJOINT[l.mode], dy, l.cout, self.dims[lout], l.imgt, None, dx, l.cin,
+                             self.dims[lin], 0)
             else:
                 fe.fe_nn_conv3d(fe.NN_MODES[ADJOINT[l.mode]], dy, l.cout, self.dims[lout], l.wt16, None,
                                 dx, l.cin, self.dims[lin], 0)

@@ -144,6 +144,94 @@ def test_conv_s1_tensor_cores(fe, cin, cout, dims):
         assert np.all(np.abs(dx.cpu().numpy() - refx) <= tolx)
 
 
+T2_TC_CASES = [(16, 16, (5, 4, 6)), (32, 16, (9, 9, 9)), (64, 64, (3, 3, 3)), (20, 32, (6, 17, 33)),
+               (16, 32, (3, 5, 65)), (16, 16, (1, 1, 1))]
+
+
+@pytest.mark.parametrize("cin,cout,dims", T2_TC_CASES)
+def test_conv_t2_tensor_cores(fe, cin, cout, dims):
+    """Transposed stride-2 conv on tcgen05 against the FP64 oracle, same BF16
+    bound as the stride-1 kernel; also the stride-2 data gradient (the
+    transposed layer with transposed weights) through the same kernel."""
+    x, W, b = layer_setup("t2", cin, cout, dims, 13)
+    dout = onn.out_dims("t2", dims)
+    w32 = cuda32(W)
+    w16 = torch.empty(cin * 27 * cout, dtype=torch.bfloat16, device="cuda")
+    fe.fe_nn_pack_weights(w32, cin, cout, 0, 0, w16)
+    img = fe.mma_image(cin, cout)
+    fe.fe_nn_pack_weights_mma(w16, cin, cout, img)
+    ref = onn.conv("t2", x.astype(np.float64), W, b)
+    bound = onn.conv("t2", np.abs(x).astype(np.float64), np.abs(W), np.abs(b))
+    tol = (2.0 ** -8 + 2 * (cin * 27 + 1) * U32) * bound + 1e-30
+    y = torch.full((cout,) + dout, float("nan"), dtype=torch.float32, device="cuda")
+    for relu in (0, 1):
+        fe.fe_nn_conv3d_t2_tc(cuda32(x), cin, dims, img, cuda32(b), y, cout, dout, relu)
+        want = np.maximum(ref, 0) if relu else ref
+        got = y.cpu().numpy()
+        assert np.all(np.isfinite(got))
+        assert np.all(np.abs(got - want) <= tol), float(np.max(np.abs(got - want) / tol))
+    assert fe.fe_nn_tc_check() == 0
+    # data gradient of a stride-2 layer cin2 -> cout2 on the fine grid dout
+    if cin in fe.TC_COUT:
+        cin2, cout2 = cin, cout           # the stride-2 layer maps cin2 channels (fine) to cout2 (coarse)
+        W2 = bf16(0.2 * np.random.default_rng(14).standard_normal((cin2, 27, cout2)))
+        dy = np.random.default_rng(15).standard_normal((cout2,) + dims).astype(np.float32)
+        wt16 = torch.empty(cin2 * 27 * cout2, dtype=torch.bfloat16, device="cuda")
+        fe.fe_nn_pack_weights(cuda32(W2), cin2, cout2, 1, 0, wt16)
+        imgt = fe.mma_image(cout2, cin2)
+        fe.fe_nn_pack_weights_mma(wt16, cout2, cin2, imgt)
+        dx = torch.empty((cin2,) + dout, dtype=torch.float32, device="cuda")
+        fe.fe_nn_conv3d_t2_tc(cuda32(dy), cout2, dims, imgt, None, dx, cin2, dout, 0)
+        refx = onn.conv_grad_x("s2", dy.astype(np.float64), W2, dout)
+        bx = onn.conv_grad_x("s2", np.abs(dy).astype(np.float64), np.abs(W2), dout)
+        tolx = (2.0 ** -8 + 2 * cout2 * 27 * U32) * bx + 1e-30
+        assert np.all(np.abs(dx.cpu().numpy() - refx) <= tolx)
+
+
+S2_TC_CASES = [(16, 32, (9, 7, 11)), (32, 64, (17, 17, 17)), (64, 64, (5, 5, 5)), (20, 16, (33, 9, 129)),
+               (16, 16, (1, 1, 1)), (16, 16, (2, 3, 4))]
+
+
+@pytest.mark.parametrize("cin,cout,dims", S2_TC_CASES)
+def test_conv_s2_tensor_cores(fe, cin, cout, dims):
+    """Stride-2 conv on tcgen05 (parity sub-box staging) against the FP64
+    oracle, same BF16 bound; also the transposed layer's data gradient (the
+    stride-2 layer with transposed weights) through the same kernel."""
+    x, W, b = layer_setup("s2", cin, cout, dims, 16)
+    dout = onn.out_dims("s2", dims)
+    w32 = cuda32(W)
+    w16 = torch.empty(cin * 27 * cout, dtype=torch.bfloat16, device="cuda")
+    fe.fe_nn_pack_weights(w32, cin, cout, 0, 0, w16)
+    img = fe.mma_image(cin, cout)
+    fe.fe_nn_pack_weights_mma(w16, cin, cout, img)
+    ref = onn.conv("s2", x.astype(np.float64), W, b)
+    bound = onn.conv("s2", np.abs(x).astype(np.float64), np.abs(W), np.abs(b))
+    tol = (2.0 ** -8 + 2 * (cin * 27 + 1) * U32) * bound + 1e-30
+    y = torch.full((cout,) + dout, float("nan"), dtype=torch.float32, device="cuda")
+    for relu in (0, 1):
+        fe.fe_nn_conv3d_s2_tc(cuda32(x), cin, dims, img, cuda32(b), y, cout, dout, relu)
+        want = np.maximum(ref, 0) if relu else ref
+        got = y.cpu().numpy()
+        assert np.all(np.isfinite(got))
+        assert np.all(np.abs(got - want) <= tol), float(np.max(np.abs(got - want) / tol))
+    assert fe.fe_nn_tc_check() == 0
+    # data gradient of a transposed layer cin2 (coarse) -> cout2 (fine): dy on the fine grid
+    if cin in fe.TC_COUT and all((d - 1) % 2 == 0 for d in dims):
+        cin2, cout2 = cout, cin
+        W2 = bf16(0.2 * np.random.default_rng(17).standard_normal((cin2, 27, cout2)))
+        dy = np.random.default_rng(18).standard_normal((cout2,) + dims).astype(np.float32)
+        wt16 = torch.empty(cin2 * 27 * cout2, dtype=torch.bfloat16, device="cuda")
+        fe.fe_nn_pack_weights(cuda32(W2), cin2, cout2, 1, 0, wt16)
+        imgt = fe.mma_image(cout2, cin2)
+        fe.fe_nn_pack_weights_mma(wt16, cout2, cin2, imgt)
+        dx = torch.empty((cin2,) + dout, dtype=torch.float32, device="cuda")
+        fe.fe_nn_conv3d_s2_tc(cuda32(dy), cout2, dims, imgt, None, dx, cin2, dout, 0)
+        refx = onn.conv_grad_x("t2", dy.astype(np.float64), W2, dout)
+        bx = onn.conv_grad_x("t2", np.abs(dy).astype(np.float64), np.abs(W2), dout)
+        tolx = (2.0 ** -8 + 2 * cout2 * 27 * U32) * bx + 1e-30
+        assert np.all(np.abs(dx.cpu().numpy() - refx) <= tolx)
+
+
 def test_conv_s1_tensor_cores_rejects_bad_cout(fe):
     x = torch.zeros((16, 3, 3, 3), device="cuda")
     img = fe.mma_image(16, 24)
