@@ -58,10 +58,10 @@ MAXIT = 5000
 ITERS_TO_TOL = {256: 507}
 FP64_PEAK_TFLOPS = 1.25   # nominal dense FP64 of a GB300 (2 FMA/clk/SM x 152 SMs x ~2.06 GHz)
 # DRAM bytes (read + write) per row of k_cg<bcrs3,f64>: per CG step and for the
-# initial residual, from two ncu captures at N=180 where, as at N=256, the CG
+# initial residual plus the last x update, from two ncu captures at N=180 where, as at N=256, the CG
 # vectors exceed L2 (profiles/k_cg_n180_ncu_traffic.md).  Valid for the kernel
 # as captured; set to None when k_cg changes until it is captured again.
-K_CG_BCRS3_TRAFFIC_PER_ROW = {"step": 334.3, "init": 254.5}
+K_CG_BCRS3_TRAFFIC_PER_ROW = {"step": 324.4, "init": 262.7}
 
 
 def load_peaks():
@@ -153,8 +153,8 @@ def cg_iteration_model(fmt: str, m: int, n_slices: int, n_stored: int, nnz: int)
     Matrix: every stored index and value once (BCRS3: 4 B index + 3 x 8 B
     values per slot, slice pointers; CSR: 12 B per entry + row pointer).
     Vectors (8 B each per row): w = A p reads p once and writes w (16 B);
-    x += a p, r -= a w reads x, p, r, w and writes x, r (48 B); p = r + b p
-    reads r, p and writes p (24 B): 88 B per row.
+    r -= a w reads r, w and writes r (24 B); x += a p, p = r + b p read x, p,
+    r and write x, p (40 B): 80 B per row.
     FMAs: one per stored value (padding included) + 5 per row (p.w, x, r,
     r.r, p)."""
     if fmt == "bcrs3":
@@ -166,7 +166,7 @@ def cg_iteration_model(fmt: str, m: int, n_slices: int, n_stored: int, nnz: int)
     else:
         mat = 12 * nnz + 4 * (m + 1)
         fma = nnz
-    return mat + 88 * m, fma + 5 * m, mat
+    return mat + 80 * m, fma + 5 * m, mat
 
 
 def spmv_bytes(fmt: str, m: int, n_slices: int, n_stored: int, nnz: int, vec_bytes: int = 8):
@@ -376,7 +376,7 @@ def main():
     byte_it, fma_it, mat_bytes = cg_iteration_model(args.format, m, s.sizes.n_slices,
                                                      A.desc.n_stored, s.sizes.nnz)
     # one launch: the initial residual (one matrix pass + b, x, r, p) plus `it` steps
-    launch_bytes = it * byte_it + mat_bytes + 40 * m
+    launch_bytes = it * byte_it + mat_bytes + 40 * m + 24 * m   # + the last x update (x, p in, x out)
     launch_fma = it * fma_it + fma_it - 5 * m + 2 * m
     t_launch = cg_ms * 1e-3
     hbm_ach = launch_bytes / t_launch / 1e9

@@ -3,8 +3,9 @@
 //
 // Each CG step is three phases separated by grid barriers:
 //   A  w = A p over the block's slices, p.w accumulated in the SpMV epilogue
-//   B  x += alpha p, r -= alpha w, r.r accumulated in the same pass
-//   C  p = r + beta p
+//   B  r -= alpha w, r.r accumulated in the same pass
+//   C  x += alpha p, p = r + beta p (x is updated where p is read anyway; the
+//      last step's x update is applied after the loop)
 // A dot product is reduced warp (xor butterfly) -> block (fixed warp order)
 // -> one partial per block in global memory -> after the barrier every warp
 // of every block sums the partials in block order, so all blocks hold the
@@ -42,6 +43,8 @@ __global__ void __launch_bounds__(kCgThreads, cg_min_blocks<FMT>()) k_cg(const C
     __syncthreads();
     int status = FE_ERR_MAXIT;
     bool alive = true;
+    bool has_pending = false;   // block-uniform
+    XT pending = XT(0);
 
     // r = b - A x, p = r; r.r and b.b
     {
@@ -92,8 +95,9 @@ __global__ void __launch_bounds__(kCgThreads, cg_min_blocks<FMT>()) k_cg(const C
             double pw, unused;
             if (!(alive = grid_sum2(a, &st, (double)pw_part, 0.0, pw, unused))) break;
             if (!(pw > 0.0) || !(pw < INFINITY)) { status = FE_ERR_BREAKDOWN; break; }
-            // B: x += alpha p, r -= alpha w, r.r
-            const XT rr_part = update_xr<XT>(a.x, a.r, a.p, a.w, m, (XT)(st.rr / pw));
+            // B: r -= alpha w, r.r (x += alpha p is applied in C, where p is read anyway)
+            const XT alpha = (XT)(st.rr / pw);
+            const XT rr_part = update_r<XT>(a.r, a.w, m, alpha);
             double rr_new;
             if (!(alive = grid_sum2(a, &st, (double)rr_part, 0.0, rr_new, unused))) break;
             const double beta = rr_new / st.rr;
@@ -103,17 +107,30 @@ __global__ void __launch_bounds__(kCgThreads, cg_min_blocks<FMT>()) k_cg(const C
                 st.k += 1;
             }
             __syncthreads();
-            if (rr_new <= a.tol2 * st.bb) { status = FE_OK; break; }
-            if (st.k >= a.maxit) { status = FE_ERR_MAXIT; break; }
-            // C: p = r + beta p
-            update_p<XT>(a.p, a.r, m, (XT)beta);
+            if (rr_new <= a.tol2 * st.bb || st.k >= a.maxit) {
+                status = rr_new <= a.tol2 * st.bb ? FE_OK : FE_ERR_MAXIT;
+                pending = alpha;             // the last x update is still to be applied
+                has_pending = true;
+                break;
+            }
+            // C: x += alpha p, p = r + beta p
+            update_xp<XT>(a.x, a.p, a.r, m, alpha, (XT)beta);
             if (!(alive = grid_barrier(a.ctrl, &st, a.timeout_ns, a.stall_barrier))) break;
         }
     }
-    // refinement step of the mixed-precision form: x64 += x
-    if (a.x64 != nullptr && alive && (status == FE_OK || status == FE_ERR_MAXIT)) {
+    // last x update (row by row; no barrier needed: the fold below uses the
+    // same rows per thread), then the refinement step of the mixed-precision
+    // form: x64 += x
+    if (alive && (status == FE_OK || status == FE_ERR_MAXIT) && (has_pending || a.x64 != nullptr)) {
         const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
-        for (int row = tid; row < m; row += nth) a.x64[row] += (double)a.x[row];
+        for (int row = tid; row < m; row += nth) {
+            XT xi = a.x[row];
+            if (has_pending) {
+                xi = fma(pending, a.p[row], xi);
+                a.x[row] = xi;
+            }
+            if (a.x64 != nullptr) a.x64[row] += (double)xi;
+        }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         a.ctrl->status = alive ? status : FE_ERR_TIMEOUT;

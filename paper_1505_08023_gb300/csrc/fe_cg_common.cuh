@@ -206,6 +206,80 @@ __device__ __forceinline__ XT update_xr(XT *x, XT *r, const XT *p, const XT *w,
     return acc;
 }
 
+// B of k_cg: r -= alpha w; returns this thread's partial of r.r (x waits for C)
+template <class XT>
+__device__ __forceinline__ XT update_r(XT *r, const XT *w, int64_t m, XT alpha) {
+    using P = typename Pack16<XT>::T;
+    constexpr int V = Pack16<XT>::N;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+    const int64_t npk = m / V;
+    P *r4 = reinterpret_cast<P *>(r);
+    const P *w4 = reinterpret_cast<const P *>(w);
+    XT acc = XT(0);
+    for (int64_t q = tid; q < npk; q += 2 * nth) {
+        const int64_t q1 = q + nth;
+        const bool two = q1 < npk;
+        P rv[2], wv[2];
+        rv[0] = r4[q]; wv[0] = w4[q];
+        if (two) { rv[1] = r4[q1]; wv[1] = w4[q1]; }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            if (u == 1 && !two) break;
+#pragma unroll
+            for (int i = 0; i < V; ++i) {
+                const XT ri = fma(-alpha, lane_of<XT>(wv[u], i), lane_of<XT>(rv[u], i));
+                lane_of<XT>(rv[u], i) = ri;
+                acc = fma(ri, ri, acc);
+            }
+        }
+        r4[q] = rv[0];
+        if (two) r4[q1] = rv[1];
+    }
+    for (int64_t row = npk * V + tid; row < m; row += nth) {
+        const XT ri = fma(-alpha, w[row], r[row]);
+        r[row] = ri;
+        acc = fma(ri, ri, acc);
+    }
+    return acc;
+}
+
+// C of k_cg: x += alpha p with the step's old p, then p = r + beta p
+template <class XT>
+__device__ __forceinline__ void update_xp(XT *x, XT *p, const XT *r, int64_t m, XT alpha, XT beta) {
+    using P = typename Pack16<XT>::T;
+    constexpr int V = Pack16<XT>::N;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+    const int64_t npk = m / V;
+    P *x4 = reinterpret_cast<P *>(x), *p4 = reinterpret_cast<P *>(p);
+    const P *r4 = reinterpret_cast<const P *>(r);
+    for (int64_t q = tid; q < npk; q += 2 * nth) {
+        const int64_t q1 = q + nth;
+        const bool two = q1 < npk;
+        P xv[2], pv[2], rv[2];
+        xv[0] = x4[q]; pv[0] = p4[q]; rv[0] = r4[q];
+        if (two) { xv[1] = x4[q1]; pv[1] = p4[q1]; rv[1] = r4[q1]; }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            if (u == 1 && !two) break;
+#pragma unroll
+            for (int i = 0; i < V; ++i) {
+                const XT pi = lane_of<XT>(pv[u], i);
+                lane_of<XT>(xv[u], i) = fma(alpha, pi, lane_of<XT>(xv[u], i));
+                lane_of<XT>(pv[u], i) = fma(beta, pi, lane_of<XT>(rv[u], i));
+            }
+        }
+        x4[q] = xv[0]; p4[q] = pv[0];
+        if (two) { x4[q1] = xv[1]; p4[q1] = pv[1]; }
+    }
+    for (int64_t row = npk * V + tid; row < m; row += nth) {
+        const XT pi = p[row];
+        x[row] = fma(alpha, pi, x[row]);
+        p[row] = fma(beta, pi, r[row]);
+    }
+}
+
 // C: p = r + beta p
 template <class XT>
 __device__ __forceinline__ void update_p(XT *p, const XT *r, int64_t m,
