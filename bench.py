@@ -22,6 +22,8 @@ Reported (one JSON line on rank 0):
   mixed        the mixed-precision form on the same system (FP32 values,
                FP32 CG with FP64 reliable updates): time to 1e-10 and its
                speedup over the FP64 solve, with the solutions' difference
+  mixed_n400   the N = 400 configuration: FP64 CG vs the mixed solver with FP32
+               and with BF16 values, times, steps, true residuals and errors
   single_reduction  the Chronopoulos-Gear CG (one grid reduction per step) on
                the same system, and both CG forms on the N = 30 mesh
   cpu_baseline the CPU oracle, single core, on a bounded sample of the same
@@ -289,6 +291,7 @@ def main():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-sr", action="store_true", help="skip the single-reduction CG legs")
+    ap.add_argument("--no-n400", action="store_true", help="skip the N=400 mixed-precision leg")
     ap.add_argument("--batch-size", type=int, default=64)
     args = ap.parse_args()
 
@@ -491,6 +494,11 @@ def main():
     if not args.no_batched and world == 1:
         batched = run_batched(args, fe, torch, dev, EV)
 
+    # ---- the N = 400 mixed-precision configuration (FP32 and BF16 values)
+    n400 = None
+    if not args.no_n400 and world == 1:
+        n400 = run_n400(args, fe, torch, dev, EV)
+
     # ---- e2e: host boundary data in, host solution out, through the Python API
     e2e = None
     if True:
@@ -577,13 +585,73 @@ def main():
                 "iterations": it, "relres_true": tr, "status": sorted(statuses),
                 "cg_ms_per_iteration": round(cg_ms / max(it, 1), 4),
                 "phase_ms": {k: round(statistics.mean(v), 3) for k, v in phases.items()},
-                "roofline": roofline, "mixed": mixed, "single_reduction": single_red, "batched": batched, "spmv": spmv, "e2e": e2e,
+                "roofline": roofline, "mixed": mixed, "mixed_n400": n400, "single_reduction": single_red,
+                "batched": batched, "spmv": spmv, "e2e": e2e,
                 "cpu_baseline": cpu, "cpu_parallel": cpu_par,
                 "clocks": clocks, "gpu_launches": launches_per_step * args.steps,
                 "wall_s_timed_region": round(wall, 3)}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_n400(args, fe, torch, dev, EV, n: int = 400):
+    """Mixed precision at N = 400 (401^3 = 64.5M rows, 1.73B stored entries):
+    FP64 CG (BCRS3) to 1e-10, then the reliable-update mixed solver with FP32
+    and with BF16 values (BCRS3), each to a true relative residual of 1e-10;
+    one untimed and one timed solve each (the matrix alone exceeds L2 ~100x).
+    Errors are against the FP64 GPU solve (the same solver checked against
+    the oracle in the tests); the true residuals come from the FP64 residual
+    kernel."""
+    s = fe.System(n, device=dev).build()
+    A64 = s.matrix("bcrs3", "f64")
+    lo = {v: s.matrix("bcrs3", v) for v in ("f32", "bf16")}
+    s.cols = s.vals = None           # the CSR copy is no longer needed
+    s.coords = None
+    torch.cuda.empty_cache()
+    m = s.m
+    rwork = fe.resid_workspace(dev)
+    out = {"workload": f"MiniFE N={n} ({m:,} rows, {s.sizes.nnz:,} stored entries), BCRS3",
+           "unit": "s"}
+    x64 = torch.zeros(m, dtype=torch.float64, device=dev)
+    w64 = fe.cg_workspace(A64, dev)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        a, b = EV(), EV()
+        a.record()
+        r = fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) * 1e-3, r
+
+    def fp64():
+        x64.zero_()
+        return fe.fe_cg_solve(A64.desc, s.b, x64, TOL, 20000, w64, check=False)
+
+    t, r = timed(fp64)
+    out["fp64"] = {"value": round(t, 4), "iterations": r.iterations, "status": r.status,
+                   "relres_true": fe.fe_true_relres(A64.desc, s.b, x64, rwork)}
+    for v, Alo in lo.items():
+        xm = torch.zeros(m, dtype=torch.float64, device=dev)
+        mw = fe.mixed_workspace(Alo, dev)
+
+        def mixed():
+            xm.zero_()
+            return fe.fe_cg_solve_mixed(A64.desc, Alo.desc, s.b, xm, TOL, fe.FE_MIXED_RELIABLE, 200,
+                                        0.1, 20000, mw, check=False)
+
+        t, r = timed(mixed)
+        out[v] = {"value": round(t, 4), "status": r.status, "inner_iterations": r.inner_iterations,
+                  "refinement_steps": r.outer_iterations,
+                  "relres_true": fe.fe_true_relres(A64.desc, s.b, xm, rwork),
+                  "rel_error_vs_fp64": float(torch.linalg.norm(xm - x64) / torch.linalg.norm(x64)),
+                  "speedup_vs_fp64": round(out["fp64"]["value"] / t, 3)}
+        del xm, mw
+    del s, A64, lo, x64, w64
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_batched(args, fe, torch, dev, EV):

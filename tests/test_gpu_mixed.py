@@ -187,3 +187,51 @@ def test_reliable_step_count_near_fp64(fe):
         x, res = solve_mixed(fe, s, "bcrs3", value)
         assert res.status == fe.FE_OK
         assert res.inner_iterations <= factor * ref.iterations + 5, (value, res.inner_iterations, ref.iterations)
+
+
+@pytest.mark.slow
+def test_full_size_n400_mixed(fe):
+    """N = 400 (64.5M rows, the mixed-precision configuration): sampled assembled
+    rows against the oracle, then FP64 CG and the reliable mixed solver with
+    FP32 and BF16 values (BCRS3), each to a true relative residual <= 1.5e-10
+    (FP64 residual kernel, pinned against the oracle in test_gpu_cg.py).  Both
+    solutions then differ by at most 2 kappa 1.5e-10 relative, with kappa(A)
+    <= (16h/3) / (3 pi^2 h^3) = 16 / (9 pi^2 h^2) ~ 2.9e4 for this stencil
+    (Gershgorin bound over the smallest continuum eigenvalue times h^3):
+    <= 8.7e-6, asserted as 1e-5."""
+    import torch
+    from test_gpu_assembly import oracle_row
+    n = 400
+    s = fe.System(n).build()
+    m = s.m
+    g = np.random.default_rng(1)
+    rows = g.integers(0, m, size=24)
+    nn = n + 1
+    for i in rows:
+        a, b_ = int(s.row_ptr[int(i)]), int(s.row_ptr[int(i) + 1])
+        cols = s.cols[a:b_].cpu().numpy()
+        vals = s.vals[a:b_].cpu().numpy()
+        ref_cols, ref_vals = oracle_row((n, n, n), int(i))
+        assert np.array_equal(cols, ref_cols)
+        ix, iy, iz = i % nn, (i // nn) % nn, i // (nn * nn)
+        if min(ix, iy, iz) == 0 or max(ix, iy, iz) == n:
+            assert np.array_equal(vals, (ref_cols == i).astype(float))
+        else:
+            cx, cy, cz = ref_cols % nn, (ref_cols // nn) % nn, ref_cols // (nn * nn)
+            bnd = (np.minimum(np.minimum(cx, cy), cz) == 0) | (np.maximum(np.maximum(cx, cy), cz) == n)
+            ref_vals = np.where(bnd, 0.0, ref_vals)
+            assert np.abs(vals - ref_vals).max() <= 1e-14 * np.abs(ref_vals).max()
+    A64 = s.matrix("bcrs3", "f64")
+    rwork = fe.resid_workspace()
+    x64 = torch.zeros(m, dtype=torch.float64, device="cuda")
+    r = fe.fe_cg_solve(A64.desc, s.b, x64, 1e-10, 20000, fe.cg_workspace(A64))
+    assert r.status == fe.FE_OK and fe.fe_true_relres(A64.desc, s.b, x64, rwork) <= 1.5e-10
+    for v in ("f32", "bf16"):
+        Alo = s.matrix("bcrs3", v)
+        xm = torch.zeros_like(x64)
+        rm = fe.fe_cg_solve_mixed(A64.desc, Alo.desc, s.b, xm, 1e-10, fe.FE_MIXED_RELIABLE, 200, 0.1,
+                                  20000, fe.mixed_workspace(Alo), check=False)
+        assert rm.status == fe.FE_OK, v
+        assert fe.fe_true_relres(A64.desc, s.b, xm, rwork) <= 1.5e-10
+        assert torch.linalg.norm(xm - x64) <= 1e-5 * torch.linalg.norm(x64)
+        del Alo, xm
