@@ -248,8 +248,8 @@ typedef enum fe_mixed_mode {
 } fe_mixed_mode;
 
 /*
- * Mixed-precision form of the solve (not in the paper; the FP64 path is its
- * judge).  A_lo holds the matrix values in FP32 or BF16 (any format); the
+ * Mixed-precision form of the solve (not in the paper; it must reach the same
+ * FP64 true residual as the FP64 path).  A_lo holds the matrix values in FP32 or BF16 (any format); the
  * Krylov iteration runs in FP32 with FP32 accumulation on A_lo; the residual
  * recompute r = b - A64 x (A64: FP64 values, any format), the refinement
  * update x += d and every global dot product are FP64.  The stopping test is
@@ -305,7 +305,7 @@ fe_status fe_cg_solve_noalloc(const fe_matrix *A, const double *d_b, double *d_x
                               fe_stream_t stream);
 
 /*
- * Batched form (the benchmark spec form X2; the paper solves one system): many
+ * Batched form (an extension; the paper solves one system): many
  * independent CG solves -- meshes of different sizes, different boundary data
  * -- in one persistent cooperative launch.  System i is A[i] x_i = b_i; every
  * A[i] is FP64 with one common format (FE_FMT_BCRS3 or FE_FMT_SELL).  Systems
@@ -357,7 +357,7 @@ fe_status fe_cg_solve_batched(int n_systems, const fe_matrix *A, const double *c
                               fe_cg_result *h_results, fe_stream_t stream);
 
 /*
- * Learned warm start (the benchmark spec form X3; not in the paper).  Kernels of a
+ * Learned warm start (an extension, not in the paper).  Kernels of a
  * 3-D convolutional encoder-decoder that maps the boundary data of a mesh to
  * a CG start vector, and of its training.  Volumes are FP32 arrays
  * [C][D][H][W] (W fastest) on one sample; dims arrays are {D, H, W}.

@@ -1,5 +1,5 @@
 // fe_cg_mixed.cu -- mixed-precision form of the CG solve (not in the paper;
-// the FP64 path is its judge): matrix values stored in FP32 or BF16, the
+// it must meet the FP64 path's true-residual test): matrix values stored in FP32 or BF16, the
 // Krylov iteration in FP32 with FP32 accumulation, and the residual
 // recompute, the refinement update and every global dot product in FP64.
 //

@@ -1,6 +1,6 @@
 // fe_nn.cu -- kernels of the learned warm start (a 3-D convolutional
 // encoder-decoder that predicts the CG start vector from the Dirichlet face
-// data; not in the paper, the FP64 solve stays the judge).
+// data; not in the paper; the FP64 solve from that vector decides convergence).
 //
 // Activations are FP32 [C][D][H][W] volumes (W fastest), one sample at a time.
 // Every 3x3x3 convolution is written in one "gather" form

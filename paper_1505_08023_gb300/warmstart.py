@@ -1,4 +1,4 @@
-"""Learned warm start for the CG solve (the benchmark spec form X3; not in the paper).
+"""Learned warm start for the CG solve (an extension, not in the paper).
 
 A 3-D convolutional encoder-decoder maps a mesh's boundary data (two input
 channels on the (N+1)^3 node grid: boundary value, boundary flag) to a guess

@@ -1,5 +1,5 @@
 """Mixed-precision form (FP32 or BF16 matrix values, FP32 inner CG with FP32
-accumulation, FP64 residual, refinement and global dot products) judged
+accumulation, FP64 residual, refinement and global dot products) checked
 against the FP64 oracle, through the C ABI.
 
 Per-form tolerances:
