@@ -458,6 +458,32 @@ fe_status fe_warmstart_input(const uint8_t *d_bc_flag, const double *d_bc_val, s
 fe_status fe_warmstart_output(const float *d_pred, const uint8_t *d_bc_flag, const double *d_bc_val,
                               size_t n, double *d_x0, fe_stream_t stream);
 
+/*
+ * Warm-start inference in one call (an extension, not in the paper): the
+ * boundary data of an n_nodes^3 mesh (bc_flag, bc_val, as fe_generate_mesh
+ * writes them) in, the CG start vector d_x0 (n_nodes^3 doubles) out, through
+ * the 4-level encoder-decoder with channels h_channels[0..3]:
+ *   e0 = relu(S1(x)), d1 = relu(S2(e0)), e1 = relu(S1(d1)), ..., e3 = relu(S1(d3)),
+ *   s2 = relu(T2(e3) + e2), f2 = relu(S1(s2)), s1, f1, s0, f0 likewise,
+ *   pred = b_h + sum_c w_h[c] f0[c]; x0 = bc_val on boundary nodes, pred inside.
+ * n_nodes - 1 must be a multiple of 8 (levels n_l = (n_nodes - 1)/2^l + 1).
+ * d_blob (256-byte aligned) holds, in the layer order e0 d1 e1 d2 e2 d3 e3 u2
+ * f2 u1 f1 u0 f0, each layer's bias FP32 [cout] and weights BF16
+ * [cin][27][cout] (the fe_nn_pack_weights forward layout), then the head
+ * weights BF16 [c0] and bias FP32 [1]; fe_warmstart_blob_layout gives the 28
+ * section offsets (each 256-byte aligned) and the size.  tensor_cores != 0
+ * runs every layer with >= 16 input and 16/32/64 output channels on the
+ * tensor cores (BF16 activations), the others on CUDA cores.  d_work:
+ * fe_warmstart_workspace bytes, 256-byte aligned.  Enqueues on `stream`,
+ * allocates nothing.
+ */
+fe_status fe_warmstart_blob_layout(const int *h_channels, size_t *h_offsets /* 28 or NULL */,
+                                   size_t *h_bytes);
+fe_status fe_warmstart_workspace(int n_nodes, const int *h_channels, size_t *h_bytes);
+fe_status fe_warmstart_infer(int n_nodes, const int *h_channels, const void *d_blob,
+                             const uint8_t *d_bc_flag, const double *d_bc_val, double *d_x0,
+                             void *d_work, size_t work_bytes, int tensor_cores, fe_stream_t stream);
+
 /* Fault injection for tests of the barrier time limit: the next fe_cg_solve
  * or fe_cg_solve_sr on the calling thread has block 0 skip its arrival at grid barrier number
  * barrier_index (0 = the barrier after the initial residual), so every

@@ -128,6 +128,10 @@ SIGNATURES = {
     "fe_nn_conv3d_s2_tc": (_I32, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _VP, _VP, _VP,
                                   ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int, _VP]),
     "fe_nn_tc_check": (_I32, [ctypes.POINTER(ctypes.c_int)]),
+    "fe_warmstart_blob_layout": (_I32, [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_SZ), ctypes.POINTER(_SZ)]),
+    "fe_warmstart_workspace": (_I32, [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_SZ)]),
+    "fe_warmstart_infer": (_I32, [ctypes.c_int, ctypes.POINTER(ctypes.c_int), _VP, _VP, _VP, _VP, _VP, _SZ,
+                                  ctypes.c_int, _VP]),
     "fe_nn_corr_workspace": (_I32, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
                                     ctypes.POINTER(_SZ), ctypes.POINTER(ctypes.c_int)]),
     "fe_nn_conv3d_weight_grad": (_I32, [ctypes.c_int, _VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _VP,
@@ -440,6 +444,29 @@ def fe_nn_tc_check() -> int:
     f = ctypes.c_int(0)
     _check("fe_nn_tc_check", load().fe_nn_tc_check(ctypes.byref(f)))
     return f.value
+
+
+def fe_warmstart_blob_layout(channels):
+    """(offsets of the 28 sections, total bytes) of a warm-start weight blob."""
+    ch = (ctypes.c_int * 4)(*[int(c) for c in channels])
+    offs = (ctypes.c_size_t * 28)()
+    n = ctypes.c_size_t(0)
+    _check("fe_warmstart_blob_layout", load().fe_warmstart_blob_layout(ch, offs, ctypes.byref(n)))
+    return [offs[i] for i in range(28)], n.value
+
+
+def fe_warmstart_workspace(n_nodes, channels) -> int:
+    ch = (ctypes.c_int * 4)(*[int(c) for c in channels])
+    n = ctypes.c_size_t(0)
+    _check("fe_warmstart_workspace", load().fe_warmstart_workspace(int(n_nodes), ch, ctypes.byref(n)))
+    return n.value
+
+
+def fe_warmstart_infer(n_nodes, channels, blob, bc_flag, bc_val, x0, work, tensor_cores=True, stream=None):
+    ch = (ctypes.c_int * 4)(*[int(c) for c in channels])
+    return _check("fe_warmstart_infer", load().fe_warmstart_infer(
+        int(n_nodes), ch, _ptr(blob), _ptr(bc_flag), _ptr(bc_val), _ptr(x0), _ptr(work),
+        work.numel() * work.element_size(), int(bool(tensor_cores)), _stream(stream)))
 
 
 def mma_image(cin, cout, device="cuda") -> torch.Tensor:

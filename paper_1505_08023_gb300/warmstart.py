@@ -113,6 +113,10 @@ class WarmStartNet:
         self.mhb, self.vhb = torch.zeros_like(self.hb), torch.zeros_like(self.hb)
         self.hw16 = torch.empty(c0, dtype=torch.bfloat16, device=self.dev)
         self.step = 0
+        self.tensor_cores = tensor_cores
+        self.n_nodes = n_nodes
+        self._blob = None
+        self._infer_work = None
         self.buf = {}
         self.corr_work = None
         self.head_work = torch.empty((c0 + 1) * 64, dtype=torch.float32, device=self.dev)
@@ -124,6 +128,7 @@ class WarmStartNet:
         for l in self.layers.values():
             l.pack()
         self.hw16.copy_(self.hw.to(torch.bfloat16))
+        self._blob = None            # the inference blob follows the weights
 
     def vol(self, key, c, level):
         d = self.dims[level]
@@ -242,6 +247,25 @@ class WarmStartNet:
         fe.fe_nn_mse(pred, target, bc_flag, 1.0 / n_interior, dpred, self.loss_parts)
         return dpred
 
+    def blob(self) -> torch.Tensor:
+        """The weights as the fe_warmstart_infer blob (bias FP32 and BF16 weights
+        per layer in the order e0 d1 e1 d2 e2 d3 e3 u2 f2 u1 f1 u0 f0, then the
+        head), byte-for-byte the copies the layer kernels use."""
+        offs, nbytes = fe.fe_warmstart_blob_layout(self.ch)
+        out = torch.zeros(nbytes, dtype=torch.uint8, device=self.dev)
+        order = ["e0", "d1", "e1", "d2", "e2", "d3", "e3", "u2", "f2", "u1", "f1", "u0", "f0"]
+        for i, name in enumerate(order):
+            l = self.layers[name]
+            b = l.b.view(torch.uint8)
+            out[offs[2 * i]:offs[2 * i] + b.numel()].copy_(b)
+            w = l.w16.view(torch.uint8)
+            out[offs[2 * i + 1]:offs[2 * i + 1] + w.numel()].copy_(w)
+        hw = self.hw16.view(torch.uint8)
+        out[offs[26]:offs[26] + hw.numel()].copy_(hw)
+        hb = self.hb.view(torch.uint8)
+        out[offs[27]:offs[27] + hb.numel()].copy_(hb)
+        return out
+
     def state(self):
         d = {k: (l.w.cpu().numpy(), l.b.cpu().numpy()) for k, l in self.layers.items()}
         d["head"] = (self.hw.cpu().numpy(), self.hb.cpu().numpy())
@@ -340,8 +364,13 @@ def train(net: WarmStartNet, prob: Problem, faces, targets, epochs=1, lr=1e-3, l
 
 
 def predict_x0(net: WarmStartNet, prob: Problem, x0: torch.Tensor):
-    pred = net.forward(prob.x_in)
-    fe.fe_warmstart_output(pred, prob.sys.bc_flag, prob.sys.bc_val, x0)
+    """x0 from the mesh's boundary data: one fe_warmstart_infer call."""
+    if net._blob is None:
+        net._blob = net.blob()
+    if net._infer_work is None:
+        net._infer_work = fe._alloc_bytes(fe.fe_warmstart_workspace(net.n_nodes, net.ch), net.dev)
+    fe.fe_warmstart_infer(net.n_nodes, net.ch, net._blob, prob.sys.bc_flag, prob.sys.bc_val, x0,
+                          net._infer_work, net.tensor_cores)
 
 
 def evaluate(net: WarmStartNet, prob: Problem, faces, tol=1e-10):

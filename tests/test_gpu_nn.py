@@ -340,3 +340,56 @@ def test_residual_loss_gradient(fe):
     got = dpred.cpu().numpy().astype(np.float64)
     assert np.all(got[sysm["bc_flag"] != 0] == 0.0)
     assert np.linalg.norm(got - want) <= 1e-5 * np.linalg.norm(want)
+
+
+@pytest.mark.parametrize("tc", [True, False])
+def test_warmstart_infer_matches_layer_by_layer_forward(fe, tc):
+    """fe_warmstart_infer (one C call) gives bit for bit the start vector of the
+    layer-by-layer forward driven from Python, with and without tensor cores."""
+    from paper_1505_08023_gb300 import warmstart as ws
+    N = 16
+    prob = ws.Problem(N)
+    prob.set_faces(ws.face_set(400, 0, 1, N)[0])
+    net = ws.WarmStartNet(N + 1, channels=(16, 16, 32, 32), tensor_cores=tc, seed=3)
+    pred = net.forward(prob.x_in)
+    want = torch.empty(prob.sys.m, dtype=torch.float64, device="cuda")
+    fe.fe_warmstart_output(pred, prob.sys.bc_flag, prob.sys.bc_val, want)
+    got = torch.full_like(want, float("nan"))
+    ws.predict_x0(net, prob, got)
+    assert torch.equal(got, want)
+    assert fe.fe_nn_tc_check() == 0
+
+
+def test_warmstart_infer_matches_oracle_network(fe):
+    """fe_warmstart_infer on the CUDA-core path against the FP64 network oracle
+    (same BF16 weights): interior values within 1e-4 of the largest |pred|,
+    the compounded FP32 rounding of 14 layers; boundary values exact."""
+    from paper_1505_08023_gb300 import warmstart as ws
+    n = 9
+    ch = (3, 4, 4, 5)
+    prob = ws.Problem(n - 1)
+    prob.set_faces(ws.face_set(401, 0, 1, n - 1)[0])
+    g = np.random.default_rng(19)
+    net = ws.WarmStartNet(n, channels=ch, tensor_cores=False)
+    params = {}
+    for name, l in net.layers.items():
+        W = bf16(0.3 * g.standard_normal((l.cin, 27, l.cout)))
+        b = (0.1 * g.standard_normal(l.cout)).astype(np.float32)
+        l.w.copy_(cuda32(W))
+        l.b.copy_(cuda32(b))
+        params[name] = (W, b.astype(np.float64))
+    hw = bf16(0.5 * g.standard_normal(ch[0]))
+    net.hw.copy_(cuda32(hw))
+    net.hb.fill_(0.05)
+    params["head"] = (hw, float(np.float32(0.05)))
+    net.pack()
+    x0 = torch.empty(prob.sys.m, dtype=torch.float64, device="cuda")
+    ws.predict_x0(net, prob, x0)
+    flag = prob.sys.bc_flag.cpu().numpy().reshape((n,) * 3)
+    val = prob.sys.bc_val.cpu().numpy().reshape((n,) * 3)
+    xin = np.stack([np.where(flag != 0, val, 0.0), (flag != 0).astype(np.float64)])
+    pred = onn.unet_forward(params, xin.astype(np.float32).astype(np.float64))["pred"]
+    got = x0.cpu().numpy().reshape((n,) * 3)
+    assert np.array_equal(got[flag != 0], val[flag != 0])
+    inner = flag == 0
+    assert np.max(np.abs(got[inner] - pred[inner])) <= 1e-4 * np.max(np.abs(pred))
