@@ -228,11 +228,39 @@ __device__ bool batch_pass(const BatchArgs &a, BatchShared &sh, int pass) {
     const long long u_end = U > 0 ? block_start(U, blockIdx.x + 1, G) : 0;
     const int first_sys = (u_begin < u_end) ? a.chunks[chunk_of_unit(sh, a.n_chunks, u_begin)].first_sys : 0;
     if (pass == kInit || pass == kSpmv || pass == kSpmvR) {
-        // warp per slice; the chunk lookup is reused while the warp stays in one chunk
+        // warp per slice; the chunk lookup is reused while the warp stays in one
+        // chunk, and the dot-product partials stay in the lanes' registers until
+        // the warp leaves the chunk (then one butterfly per system and partial)
+        const bool two = pass != kSpmv;     // passes with a second dot product
         int c = -1;
         long long c_lo = 0, c_hi = 0;
+        double pd0[KRHS], pd1[KRHS];
+#pragma unroll
+        for (int j = 0; j < KRHS; ++j) pd0[j] = pd1[j] = 0.0;
+        // adds the warp's partials of chunk c to shared memory (fixed order)
+        auto flush = [&](int cc) {
+            if (cc < 0) return;
+            const BatchChunkDev &fc = a.chunks[cc];
+#pragma unroll
+            for (int j = 0; j < KRHS; ++j) {
+                if (j >= fc.n_rhs || !sh.mask[fc.first_sys + j]) continue;
+                const double d0 = warp_sum(pd0[j]);
+                const double d1 = two ? warp_sum(pd1[j]) : 0.0;
+                const int t = fc.first_sys + j - first_sys;
+                if (lane == 0) {
+                    if (t >= 0 && t < kBatchMaxTouch) {
+                        sh.wpart[0][warp][t] += d0;
+                        sh.wpart[1][warp][t] += d1;
+                    } else {
+                        sh.touch_overflow = 1;
+                    }
+                }
+                pd0[j] = pd1[j] = 0.0;
+            }
+        };
         for (long long u = u_begin + warp; u < u_end; u += kCgWarps) {
             if (u < c_lo || u >= c_hi) {
+                flush(c);
                 c = chunk_of_unit(sh, a.n_chunks, u);
                 c_lo = sh.unit_start[c];
                 c_hi = c_lo + a.chunks[c].n_slices;
@@ -256,45 +284,31 @@ __device__ bool batch_pass(const BatchArgs &a, BatchShared &sh, int pass) {
             slice_spmm<FMT, KRHS>(ch.A, slice, lane, xin, on, acc);
 #pragma unroll
             for (int j = 0; j < KRHS; ++j) {
-                if (!on[j]) continue;
-                const int s = ch.first_sys + j;
-                const BatchSysDev &sd = a.sys[s];
-                double d0 = 0.0, d1 = 0.0;
-                if (in) {
-                    if (pass == kInit) {
-                        const double bi = sd.b[row], ri = bi - acc[j];
-                        sd.r[row] = ri;
-                        if (SR) {
-                            sd.p[row] = 0.0;
-                            sd.s[row] = 0.0;
-                        } else {
-                            sd.p[row] = ri;
-                        }
-                        d0 = ri * ri;
-                        d1 = bi * bi;
-                    } else if (pass == kSpmvR) {
-                        const double ri = sd.r[row];
-                        sd.w[row] = acc[j];
-                        d0 = ri * ri;
-                        d1 = acc[j] * ri;
+                if (!on[j] || !in) continue;
+                const BatchSysDev &sd = a.sys[ch.first_sys + j];
+                if (pass == kInit) {
+                    const double bi = sd.b[row], ri = bi - acc[j];
+                    sd.r[row] = ri;
+                    if (SR) {
+                        sd.p[row] = 0.0;
+                        sd.s[row] = 0.0;
                     } else {
-                        sd.w[row] = acc[j];
-                        d0 = sd.p[row] * acc[j];
+                        sd.p[row] = ri;
                     }
-                }
-                d0 = warp_sum(d0);
-                d1 = warp_sum(d1);
-                const int t = s - first_sys;
-                if (lane == 0) {
-                    if (t >= 0 && t < kBatchMaxTouch) {
-                        sh.wpart[0][warp][t] += d0;
-                        sh.wpart[1][warp][t] += d1;
-                    } else {
-                        sh.touch_overflow = 1;
-                    }
+                    pd0[j] = fma(ri, ri, pd0[j]);
+                    pd1[j] = fma(bi, bi, pd1[j]);
+                } else if (pass == kSpmvR) {
+                    const double ri = sd.r[row];
+                    sd.w[row] = acc[j];
+                    pd0[j] = fma(ri, ri, pd0[j]);
+                    pd1[j] = fma(acc[j], ri, pd1[j]);
+                } else {
+                    sd.w[row] = acc[j];
+                    pd0[j] = fma(sd.p[row], acc[j], pd0[j]);
                 }
             }
         }
+        flush(c);
     } else {
         // streaming passes: the block's unit range is a contiguous row range of
         // each chunk it touches; all threads stream each system's rows there in
