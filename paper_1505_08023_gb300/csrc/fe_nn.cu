@@ -32,26 +32,22 @@ __host__ __device__ constexpr int tile_z() { return 4; }
 __host__ __device__ constexpr int tile_y() { return 8; }
 __host__ __device__ constexpr int tile_x() { return 8; }
 
-// input extent of a forward output tile, per axis
-template <int MODE> __host__ __device__ constexpr int in_extent(int t) {
-    return MODE == FE_NN_S1 ? t + 2 : (MODE == FE_NN_S2 ? 2 * t + 1 : t / 2 + 2);
-}
-template <int MODE> __device__ __forceinline__ int in_origin(int u0) {
-    if (MODE == FE_NN_S1) return u0 - 1;
-    if (MODE == FE_NN_S2) return 2 * u0 - 1;
-    return (u0 - 1) >> 1;   // floor((u0 - 1) / 2), u0 >= 0
-}
+// input extent and origin of a stride-2 output tile, per axis
+__host__ __device__ constexpr int s2_extent(int t) { return 2 * t + 1; }
+__device__ __forceinline__ int s2_origin(int u0) { return 2 * u0 - 1; }
 
 struct Dims {
     int d, h, w;
 };
 
-template <int MODE>
+// Stride-2 forward on CUDA cores (the FP32 reference path): thread = one
+// output voxel x 16 output channels, input halo tile and BF16 weights staged
+// in shared memory per 4-channel chunk.
 __global__ void __launch_bounds__(kNnThreads)
-k_conv_fwd(const float *__restrict__ in, int cin, Dims di, const __nv_bfloat16 *__restrict__ wt,
-           const float *__restrict__ bias, float *__restrict__ out, int cout, Dims dout, int relu) {
+k_conv_fwd_s2(const float *__restrict__ in, int cin, Dims di, const __nv_bfloat16 *__restrict__ wt,
+              const float *__restrict__ bias, float *__restrict__ out, int cout, Dims dout, int relu) {
     constexpr int TZ = tile_z(), TY = tile_y(), TX = tile_x();
-    constexpr int EZ = in_extent<MODE>(TZ), EY = in_extent<MODE>(TY), EX = in_extent<MODE>(TX);
+    constexpr int EZ = s2_extent(TZ), EY = s2_extent(TY), EX = s2_extent(TX);
     constexpr int EV = EZ * EY * EX;
     __shared__ float s_in[kCiChunk][EV];
     __shared__ __align__(16) float s_w[kCiChunk][27][kCoTile];
@@ -65,7 +61,7 @@ k_conv_fwd(const float *__restrict__ in, int cin, Dims di, const __nv_bfloat16 *
     const int co0 = blockIdx.y * kCoTile;
     const int tx = threadIdx.x % TX, ty = (threadIdx.x / TX) % TY, tz = threadIdx.x / (TX * TY);
     const int ux = bx * TX + tx, uy = by * TY + ty, uz = bz * TZ + tz;
-    const int oz = in_origin<MODE>(bz * TZ), oy = in_origin<MODE>(by * TY), ox = in_origin<MODE>(bx * TX);
+    const int oz = s2_origin(bz * TZ), oy = s2_origin(by * TY), ox = s2_origin(bx * TX);
 
     float acc[kCoTile];
 #pragma unroll
@@ -95,18 +91,7 @@ k_conv_fwd(const float *__restrict__ in, int cin, Dims di, const __nv_bfloat16 *
 #pragma unroll
             for (int tap = 0; tap < 27; ++tap) {
                 const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
-                int lz, ly, lx;
-                bool ok = true;
-                if (MODE == FE_NN_S1) {
-                    lz = tz + dz; ly = ty + dy; lx = tx + dx;
-                } else if (MODE == FE_NN_S2) {
-                    lz = 2 * tz + dz; ly = 2 * ty + dy; lx = 2 * tx + dx;
-                } else {
-                    const int pz = uz + 1 - dz, py = uy + 1 - dy, px = ux + 1 - dx;
-                    ok = ((pz | py | px) & 1) == 0;
-                    lz = (pz >> 1) - oz; ly = (py >> 1) - oy; lx = (px >> 1) - ox;
-                }
-                if (!ok) continue;
+                const int lz = 2 * tz + dz, ly = 2 * ty + dy, lx = 2 * tx + dx;
                 const float v = s_in[c][(lz * EY + ly) * EX + lx];
                 const float4 *w4 = reinterpret_cast<const float4 *>(&s_w[c][tap][0]);
 #pragma unroll
@@ -688,7 +673,7 @@ fe_status fe_nn_conv3d(int mode, const float *d_in, int cin, const int *dims_in,
         k_conv_fwd_s1v<<<dim3(tv, (cout + kCoTile - 1) / kCoTile), kNnThreads, 0, s>>>(
             d_in, cin, di, d_w, d_bias, d_out, cout, dout, relu);
     } else if (mode == FE_NN_S2) {
-        k_conv_fwd<FE_NN_S2><<<grid, kNnThreads, 0, s>>>(d_in, cin, di, d_w, d_bias, d_out, cout, dout, relu);
+        k_conv_fwd_s2<<<grid, kNnThreads, 0, s>>>(d_in, cin, di, d_w, d_bias, d_out, cout, dout, relu);
     } else {
         const int cz = (dout.d + 1) / 2, cy = (dout.h + 1) / 2, cx = (dout.w + 1) / 2;  // largest class
         const int tv = ((cx + kT2TX - 1) / kT2TX) * ((cy + kT2TY - 1) / kT2TY) * ((cz + kT2TZ - 1) / kT2TZ);

@@ -8,7 +8,7 @@ CG for --cg-steps steps (tol 0, or to --tol when --cg-steps is 0), the
 single-reduction CG for --sr-steps steps, and the mixed-precision
 reliable-update solve for --mixed-steps FP32 steps; or, with --conv, one
 stride-1 convolution of the warm-start network (tensor-core and CUDA-core
-kernels).  With
+kernels); or, with --batch, the batched solver on a seeded batch of meshes.  With
 --drop-csr the CSR arrays are released after conversion (smaller footprint
 for profiler captures that save and restore device memory).  Prints one line
 per step taken.
@@ -34,12 +34,18 @@ def main():
     ap.add_argument("--mixed-steps", type=int, default=0)
     ap.add_argument("--mixed-values", choices=["f32", "bf16"], default="f32")
     ap.add_argument("--drop-csr", action="store_true")
+    ap.add_argument("--batch", type=int, nargs=3, metavar=("COUNT", "LO", "HI"), default=None,
+                    help="instead of one mesh: COUNT cubic meshes N ~ U{LO..HI} (PCG64 seed 0) with "
+                         "random face data, --cg-steps steps of the batched solver (1 RHS per chunk)")
     ap.add_argument("--conv", type=int, nargs=3, metavar=("CIN", "COUT", "N"), default=None,
                     help="instead of the solver: one stride-1 conv of the warm-start network on an "
                          "N^3 grid, tensor-core kernel then CUDA-core kernel")
     a = ap.parse_args()
     if a.conv is not None:
         run_conv(*a.conv)
+        return
+    if a.batch is not None:
+        run_batch(*a.batch, fmt=a.format, steps=a.cg_steps)
         return
 
     s = fe.System(a.n).build()
@@ -69,6 +75,18 @@ def main():
         print(f"mixed: status {r.status} fp32 steps {r.inner_iterations} "
               f"refinements {r.outer_iterations} relres {r.relres:.3e}")
     torch.cuda.synchronize()
+
+
+def run_batch(count: int, lo: int, hi: int, fmt: str, steps: int):
+    import fe_inputs
+    sizes = [int(n) for n in fe_inputs.batched_sizes(0, count, lo=lo, hi=hi)]
+    faces = [fe_inputs.face_data(0, i, n, n, n) for i, n in enumerate(sizes)]
+    batch = fe.Batch(sizes, faces, fmt)
+    plan = fe.fe_cg_batched_plan(batch.mats, batch.b, batch.x, 1, batch.workspace())
+    fe.fe_cg_batched_launch(plan, 0.0, steps)
+    st, res = fe.fe_cg_batched_results(plan)
+    print(f"batched: {count} meshes, {sum((n + 1) ** 3 for n in sizes):,} rows, {steps} steps, "
+          f"statuses {sorted(set(r.status for r in res))}")
 
 
 def run_conv(cin: int, cout: int, n: int):
