@@ -51,6 +51,36 @@ __host__ __device__ constexpr RefGradTable make_ref_grad_table() {
 }
 __constant__ RefGradTable kRefGrad = make_ref_grad_table();
 
+// The Jacobian from edge vectors: d x / d xi_j is a weighted sum of the four
+// element edges along axis j, E_jk = X(corner with o_j = 1) - X(o_j = 0), with
+// weight (1 +- p_a1)(1 +- p_a2) / 8 from the Gauss point's other two
+// coordinates (k = c1 + 2 c2 picks the edge by its other-axis corner bits).
+struct EdgeWeightTable {
+    double w[8][3][4];  // [Gauss point][axis j][edge k]
+};
+__host__ __device__ constexpr EdgeWeightTable make_edge_weight_table() {
+    EdgeWeightTable t{};
+    constexpr double g = 0.57735026918962576451;  // 1/sqrt(3)
+    for (int q = 0; q < 8; ++q) {
+        const double pt[3] = {(q & 1) ? g : -g, ((q >> 1) & 1) ? g : -g, (q >> 2) ? g : -g};
+        for (int j = 0; j < 3; ++j) {
+            const int a1 = j == 0 ? 1 : 0, a2 = j == 2 ? 1 : 2;
+            for (int k = 0; k < 4; ++k) {
+                const double s1 = (k & 1) ? 1.0 : -1.0, s2 = (k >> 1) ? 1.0 : -1.0;
+                t.w[q][j][k] = 0.125 * (1.0 + s1 * pt[a1]) * (1.0 + s2 * pt[a2]);
+            }
+        }
+    }
+    return t;
+}
+__constant__ EdgeWeightTable kEdgeW = make_edge_weight_table();
+
+// corner of the edge k along axis j at end e (0 or 1)
+__host__ __device__ constexpr int edge_corner(int j, int k, int e) {
+    const int c1 = k & 1, c2 = k >> 1;
+    return j == 0 ? corner_of(e, c1, c2) : (j == 1 ? corner_of(c1, e, c2) : corner_of(c1, c2, e));
+}
+
 __global__ void __launch_bounds__(128)
 k_element_matrices(int nx, int ny, int nz, const double *__restrict__ coords,
                    double *__restrict__ work) {
@@ -76,13 +106,21 @@ k_element_matrices(int nx, int ny, int nz, const double *__restrict__ coords,
         for (int a = 7; a >= 0; --a)
 #pragma unroll
             for (int i = 0; i < 3; ++i) X[a][i] -= X[0][i];
+        // the twelve edge vectors (once per element)
+        double E[3][4][3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+#pragma unroll
+                for (int i = 0; i < 3; ++i) E[j][k][i] = X[edge_corner(j, k, 1)][i] - X[edge_corner(j, k, 0)][i];
         double K[36];
 #pragma unroll
         for (int k = 0; k < 36; ++k) K[k] = 0.0;
 
 #pragma unroll 1
         for (int q = 0; q < 8; ++q) {
-            // J[i][j] = d x_i / d xi_j
+            // J[i][j] = d x_i / d xi_j = sum over the four edges along j
             double J[3][3];
 #pragma unroll
             for (int i = 0; i < 3; ++i)
@@ -90,7 +128,7 @@ k_element_matrices(int nx, int ny, int nz, const double *__restrict__ coords,
                 for (int j = 0; j < 3; ++j) {
                     double s = 0.0;
 #pragma unroll
-                    for (int a = 0; a < 8; ++a) s = fma(X[a][i], kRefGrad.v[q][a][j], s);
+                    for (int k = 0; k < 4; ++k) s = fma(E[j][k][i], kEdgeW.w[q][j][k], s);
                     J[i][j] = s;
                 }
             const double c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];

@@ -150,3 +150,45 @@ def test_full_size_n256_sampled_rows(fe):
             scale = np.abs(ref_vals).max()
             ref_vals = np.where(on_boundary(ref_cols), 0.0, ref_vals)   # eliminated columns
             assert np.abs(vals - ref_vals).max() <= VAL_TOL * scale
+
+
+@pytest.mark.slow
+def test_largest_mesh_int32_limit(fe):
+    """N = 429, the largest mesh whose 27-point pattern fits int32 row pointers
+    ((3*429+1)^3 = 2,136,719,872 stored entries, 0.5 % below 2^31): the last row
+    pointer equals the closed form, sampled rows match the oracle, and the CSR
+    and BCRS3 SpMVs agree on sampled rows with the oracle's row dot products."""
+    n = 429
+    dims = (n, n, n)
+    s = gpu_system(fe, dims)
+    m = s.m
+    assert int(s.row_ptr[-1]) == (3 * n + 1) ** 3
+    g = np.random.default_rng(2)
+    rows = np.concatenate([[0, m - 1, m // 2 + 7], g.integers(0, m, size=12)])
+    x = torch.from_numpy(g.uniform(-1.0, 1.0, m)).cuda()
+    y_csr = torch.empty_like(x)
+    fe.fe_spmv(s.matrix("csr").desc, x, y_csr)
+    A3 = s.matrix("bcrs3", "f64")
+    y_b3 = torch.empty_like(x)
+    fe.fe_spmv(A3.desc, x, y_b3)
+    nn = n + 1
+    xh = x.cpu().numpy()
+    for i in rows:
+        i = int(i)
+        a, b_ = int(s.row_ptr[i]), int(s.row_ptr[i + 1])
+        cols = s.cols[a:b_].cpu().numpy()
+        vals = s.vals[a:b_].cpu().numpy()
+        ref_cols, ref_vals = oracle_row(dims, i)
+        assert np.array_equal(cols, ref_cols)
+        ix, iy, iz = i % nn, (i // nn) % nn, i // (nn * nn)
+        if min(ix, iy, iz) == 0 or max(ix, iy, iz) == n:
+            want = xh[i]
+        else:
+            cx, cy, cz = ref_cols % nn, (ref_cols // nn) % nn, ref_cols // (nn * nn)
+            bnd = (np.minimum(np.minimum(cx, cy), cz) == 0) | (np.maximum(np.maximum(cx, cy), cz) == n)
+            ref_vals = np.where(bnd, 0.0, ref_vals)
+            assert np.abs(vals - ref_vals).max() <= VAL_TOL * np.abs(ref_vals).max()
+            want = float(np.dot(vals, xh[cols]))
+        bound = 32 * 2.0 ** -53 * float(np.abs(vals) @ np.abs(xh[cols])) + 1e-300
+        assert abs(float(y_csr[i]) - want) <= bound
+        assert abs(float(y_b3[i]) - want) <= bound
