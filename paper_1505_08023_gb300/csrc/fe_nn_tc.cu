@@ -26,7 +26,12 @@
 // 8-channel groups, stride offset = 128 bytes (rows are contiguous).
 // Every wait is bounded; a block that gives up sets the error flag read by
 // fe_nn_tc_check, frees its tensor memory and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
+
+#include <cstring>
+#include <mutex>
 
 #include "fe_common.cuh"
 
@@ -49,6 +54,7 @@ struct TcGeom {
     int ty, w2, rows, rows_pad, base, nw, tmem_cols, ctas_per_sm;
     int hlo, ly, pz;   // halo below the tile (1: stride 1, 0: transposed), lines and planes staged
     int rsub;          // stride 2: rows of one of the eight parity sub-boxes
+    int tma_rows;      // rows one 8-channel group's box loads write (TMA staging)
     size_t smem;
 };
 
@@ -111,12 +117,21 @@ __device__ __forceinline__ void tmem_ld8(uint32_t addr, float *v) {
 // d = 0 at offset +1 and d = 2 at offset 0 -- 27 (class, tap) pairs in all,
 // each an MMA on the input box shifted by its offsets; class c accumulates
 // in its own tensor-memory columns).
-template <int MODE>
+//
+// TMA = true: the input comes as BF16 in the 8-channel-interleaved layout
+// [ceil(C/8)][D][H][W][8] (fe_nn_to_bf16i) and one thread stages each chunk
+// with tensor-map box loads (cp.async.bulk.tensor, zero fill outside the
+// grid; element stride 2 for the parity sub-boxes of the stride-2 layer) and
+// the chunk's weights with one bulk copy, all completing on an mbarrier.
+// TMA = false: every thread loads FP32 [C][D][H][W] and converts.
+template <int MODE, bool TMA>
 __global__ void __launch_bounds__(kTcThreads, 1)
 k_conv_tc(const float *__restrict__ in, int cin, TcDims dm, const __nv_bfloat16 *__restrict__ wimg,
-          const float *__restrict__ bias, float *__restrict__ out, int cout, TcDims dout, int relu, TcGeom g) {
+          const float *__restrict__ bias, float *__restrict__ out, int cout, TcDims dout, int relu, TcGeom g,
+          const __grid_constant__ CUtensorMap tmap) {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) uint64_t mbar;
+    __shared__ __align__(8) uint64_t mbar_ld;   // TMA staging
     __shared__ uint32_t tmem_base;
     __shared__ int s_ok;
     __shared__ uint64_t s_adesc[27], s_bdesc[27];   // per (class, tap) operand descriptors, window 0
@@ -178,7 +193,14 @@ k_conv_tc(const float *__restrict__ in, int cin, TcDims dm, const __nv_bfloat16 
     if (tid == 0) {
         s_ok = 1;
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar_a), "r"(1));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar_ld)), "r"(1));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (TMA) {
+        // rows the box loads never write (padding, sub-box gaps) stay zero
+        for (size_t i = tid; i < (size_t)2 * g.rows_pad; i += kTcThreads)
+            reinterpret_cast<uint4 *>(sA)[i] = make_uint4(0u, 0u, 0u, 0u);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
@@ -190,68 +212,108 @@ k_conv_tc(const float *__restrict__ in, int cin, TcDims dm, const __nv_bfloat16 
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_base;
     const uint32_t idesc = umma_idesc_bf16(128, cout);
-    uint32_t phase = 0;
+    uint32_t phase = 0, ld_phase = 0;
     bool ok = true;
 
     for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
         const int z = tile / nty, y0 = (tile % nty) * TY;
         for (int kc = 0; kc < nkc && ok; ++kc) {
-            // stage the halo box of channels kc*16 .. kc*16+15 (zero outside the
-            // grid): four rows per thread per trip, all 64 loads issued first
-            for (int r0 = tid; r0 < g.rows_pad; r0 += 4 * kTcThreads) {
-                float v[4][16];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int r = r0 + i * kTcThreads;
-                    bool inb = false;
-                    size_t gidx = 0;
-                    if (r < g.rows) {
-                        int gz, gy, gx;
-                        if (MODE == FE_NN_S2) {
-                            // parity sub-box s holds the fine points 2c + parity(s)
-                            // of coarse positions c = tile origin - 1 + (a, b, x)
-                            const int sb = r / g.rsub, rr = r % g.rsub;
-                            const int a = rr / (LY * W2), rem = rr % (LY * W2);
-                            const int b = rem / W2, xx = rem % W2;
-                            gz = 2 * (z - 1 + a) + ((sb >> 2) & 1);
-                            gy = 2 * (y0 - 1 + b) + ((sb >> 1) & 1);
-                            gx = 2 * (xx - 1) + (sb & 1);
-                        } else {
-                            const int pz = r / (LY * W2), rem = r % (LY * W2);
-                            const int ly = rem / W2, lx = rem % W2;
-                            gz = z - HLO + pz;
-                            gy = y0 - HLO + ly;
-                            gx = lx - HLO;
-                        }
-                        inb = gz >= 0 && gz < D && gy >= 0 && gy < H && gx >= 0 && gx < W;
-                        gidx = inb ? ((size_t)gz * H + gy) * W + gx : 0;
-                    }
-#pragma unroll
-                    for (int c = 0; c < 16; ++c) {
-                        const int ch = kc * 16 + c;
-                        v[i][c] = (inb && ch < cin) ? in[(size_t)ch * plane + gidx] : 0.0f;
-                    }
-                }
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int r = r0 + i * kTcThreads;
-                    if (r >= g.rows_pad) break;
-#pragma unroll
+            if (TMA) {
+                // one thread issues the chunk's box loads and the weight copy
+                if (tid == 0) {
+                    const uint32_t mb = smem_u32(&mbar_ld);
+                    const uint32_t tx = (uint32_t)(2 * g.tma_rows * 16) + (uint32_t)chunk_bytes;
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(tx) : "memory");
+                    const uint64_t tm = reinterpret_cast<uint64_t>(&tmap);
                     for (int kg = 0; kg < 2; ++kg) {
-                        __nv_bfloat162 h[4];
-#pragma unroll
-                        for (int j = 0; j < 4; ++j)
-                            h[j] = __floats2bfloat162_rn(v[i][8 * kg + 2 * j], v[i][8 * kg + 2 * j + 1]);
-                        *reinterpret_cast<uint4 *>(sA + ((size_t)kg * g.rows_pad + r) * 16) =
-                            *reinterpret_cast<const uint4 *>(h);
+                        const int grp = 2 * kc + kg;
+                        const int nsub = MODE == FE_NN_S2 ? 8 : 1;
+                        for (int sb = 0; sb < nsub; ++sb) {
+                            int cx, cy, cz;
+                            if (MODE == FE_NN_S2) {
+                                cx = -2 + (sb & 1);
+                                cy = 2 * (y0 - 1) + ((sb >> 1) & 1);
+                                cz = 2 * (z - 1) + ((sb >> 2) & 1);
+                            } else {
+                                cx = -HLO;
+                                cy = y0 - HLO;
+                                cz = z - HLO;
+                            }
+                            const uint32_t dst = smem_u32(sA) + (uint32_t)(((size_t)kg * g.rows_pad + (size_t)sb * g.rsub) * 16);
+                            asm volatile(
+                                "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes "
+                                "[%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(dst),
+                                "l"(tm), "r"(0), "r"(cx), "r"(cy), "r"(cz), "r"(grp), "r"(mb)
+                                : "memory");
+                        }
+                    }
+                    const unsigned char *src = reinterpret_cast<const unsigned char *>(wimg) + (size_t)kc * chunk_bytes;
+                    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                                 ::"r"(smem_u32(sB)), "l"(src), "r"((uint32_t)chunk_bytes), "r"(mb) : "memory");
+                }
+                if (!mbar_wait(smem_u32(&mbar_ld), ld_phase & 1u)) {
+                    atomicExch(&g_tc_err, 1);
+                    s_ok = 0;
+                }
+                ld_phase += 1;
+            } else {
+                // stage the halo box of channels kc*16 .. kc*16+15 (zero outside the
+                // grid): four rows per thread per trip, all 64 loads issued first
+                for (int r0 = tid; r0 < g.rows_pad; r0 += 4 * kTcThreads) {
+                    float v[4][16];
+    #pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int r = r0 + i * kTcThreads;
+                        bool inb = false;
+                        size_t gidx = 0;
+                        if (r < g.rows) {
+                            int gz, gy, gx;
+                            if (MODE == FE_NN_S2) {
+                                // parity sub-box s holds the fine points 2c + parity(s)
+                                // of coarse positions c = tile origin - 1 + (a, b, x)
+                                const int sb = r / g.rsub, rr = r % g.rsub;
+                                const int a = rr / (LY * W2), rem = rr % (LY * W2);
+                                const int b = rem / W2, xx = rem % W2;
+                                gz = 2 * (z - 1 + a) + ((sb >> 2) & 1);
+                                gy = 2 * (y0 - 1 + b) + ((sb >> 1) & 1);
+                                gx = 2 * (xx - 1) + (sb & 1);
+                            } else {
+                                const int pz = r / (LY * W2), rem = r % (LY * W2);
+                                const int ly = rem / W2, lx = rem % W2;
+                                gz = z - HLO + pz;
+                                gy = y0 - HLO + ly;
+                                gx = lx - HLO;
+                            }
+                            inb = gz >= 0 && gz < D && gy >= 0 && gy < H && gx >= 0 && gx < W;
+                            gidx = inb ? ((size_t)gz * H + gy) * W + gx : 0;
+                        }
+    #pragma unroll
+                        for (int c = 0; c < 16; ++c) {
+                            const int ch = kc * 16 + c;
+                            v[i][c] = (inb && ch < cin) ? in[(size_t)ch * plane + gidx] : 0.0f;
+                        }
+                    }
+    #pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int r = r0 + i * kTcThreads;
+                        if (r >= g.rows_pad) break;
+    #pragma unroll
+                        for (int kg = 0; kg < 2; ++kg) {
+                            __nv_bfloat162 h[4];
+    #pragma unroll
+                            for (int j = 0; j < 4; ++j)
+                                h[j] = __floats2bfloat162_rn(v[i][8 * kg + 2 * j], v[i][8 * kg + 2 * j + 1]);
+                            *reinterpret_cast<uint4 *>(sA + ((size_t)kg * g.rows_pad + r) * 16) =
+                                *reinterpret_cast<const uint4 *>(h);
+                        }
                     }
                 }
+                // the chunk's weight image
+                const uint4 *src = reinterpret_cast<const uint4 *>(
+                    reinterpret_cast<const unsigned char *>(wimg) + (size_t)kc * chunk_bytes);
+                for (size_t i = tid; i < chunk_bytes / 16; i += kTcThreads)
+                    reinterpret_cast<uint4 *>(sB)[i] = src[i];
             }
-            // the chunk's weight image
-            const uint4 *src = reinterpret_cast<const uint4 *>(
-                reinterpret_cast<const unsigned char *>(wimg) + (size_t)kc * chunk_bytes);
-            for (size_t i = tid; i < chunk_bytes / 16; i += kTcThreads)
-                reinterpret_cast<uint4 *>(sB)[i] = src[i];
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncthreads();
@@ -356,7 +418,7 @@ static int pow2_at_least(int v) {
 // in the 128-row windows, among the shapes whose shared memory and tensor
 // memory fit.  Stride 1 stages a halo of one point on each side; the
 // transposed layer only reads offsets 0 and +1, so its box starts at the tile.
-static bool choose_geom(int mode, int w, int h, int cout, TcGeom *out) {
+static bool choose_geom(int mode, int w, int h, int cout, TcGeom *out, bool tma = false) {
     bool found = false;
     double best = -1.0;
     const int classes = mode == FE_NN_T2 ? 8 : 1;
@@ -371,8 +433,9 @@ static bool choose_geom(int mode, int w, int h, int cout, TcGeom *out) {
             g.ly = ty + 1;
             g.pz = 2;
             g.w2 = w + 1;
-            g.rsub = g.pz * g.ly * g.w2;
+            g.rsub = (g.pz * g.ly * g.w2 + 7) & ~7;   // sub-box regions start on 128-byte boundaries
             g.rows = 8 * g.rsub;
+            g.tma_rows = 8 * g.pz * g.ly * g.w2;
             g.base = g.ly * g.w2 + g.w2 + 1;
             shift_max = 7 * g.rsub;
         } else {
@@ -382,6 +445,7 @@ static bool choose_geom(int mode, int w, int h, int cout, TcGeom *out) {
             g.w2 = w + 1 + g.hlo;
             g.rows = g.pz * g.ly * g.w2;
             g.rsub = g.rows;
+            g.tma_rows = g.rows;
             g.base = g.hlo * (g.ly * g.w2 + g.w2 + 1);
             shift_max = g.ly * g.w2 + g.w2 + 1;
         }
@@ -391,6 +455,10 @@ static bool choose_geom(int mode, int w, int h, int cout, TcGeom *out) {
         g.smem = (size_t)2 * g.rows_pad * 16 + (size_t)27 * 2 * cout * 16;
         g.tmem_cols = pow2_at_least(classes * g.nw * cout);
         if (g.smem > kTcSmemCap || g.tmem_cols > 512) continue;
+        if (tma) {   // box dimensions (elements traversed) are at most 256
+            const int bx = mode == FE_NN_S2 ? 2 * g.w2 : g.w2, by = mode == FE_NN_S2 ? 2 * g.ly : g.ly;
+            if (bx > 256 || by > 256) continue;
+        }
         int by_smem = (int)((227 * 1024) / (g.smem + 1024));
         int by_tmem = 512 / g.tmem_cols;
         g.ctas_per_sm = by_smem < by_tmem ? by_smem : by_tmem;
@@ -405,22 +473,65 @@ static bool choose_geom(int mode, int w, int h, int cout, TcGeom *out) {
     return found;
 }
 
-template <int MODE>
-static fe_status launch_tc(const float *d_in, int cin, const int *h_dims, const void *d_img, const float *d_bias,
-                           float *d_out, int cout, const int *h_dims_out, int relu, cudaStream_t stream) {
+typedef CUresult (*TensorMapEncodeFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                      const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                      CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (looked up once)
+static TensorMapEncodeFn tensor_map_encoder() {
+    static std::once_flag once;
+    static TensorMapEncodeFn fn = nullptr;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (TensorMapEncodeFn)p;
+    });
+    return fn;
+}
+
+// Tensor map of a BF16 8-channel-interleaved volume [G][D][H][W][8] with the
+// staging box of `mode` (elements traversed; element stride 2 on the spatial
+// axes for the stride-2 parity sub-boxes).
+static bool encode_input_map(CUtensorMap *tm, int mode, const void *d_in16, int cin, const int *dims,
+                             const TcGeom &g) {
+    TensorMapEncodeFn enc = tensor_map_encoder();
+    if (!enc) return false;
+    const cuuint64_t W = (cuuint64_t)dims[2], H = (cuuint64_t)dims[1], D = (cuuint64_t)dims[0];
+    const cuuint64_t G = (cuuint64_t)((cin + 7) / 8);
+    const cuuint64_t gdim[5] = {8, W, H, D, G};
+    const cuuint64_t gstr[4] = {16, 16 * W, 16 * W * H, 16 * W * H * D};
+    const bool s2 = mode == FE_NN_S2;
+    const cuuint32_t box[5] = {8, (cuuint32_t)(s2 ? 2 * g.w2 : g.w2), (cuuint32_t)(s2 ? 2 * g.ly : g.ly),
+                               (cuuint32_t)(s2 ? 2 * g.pz : g.pz), 1};
+    const cuuint32_t es[5] = {1, s2 ? 2u : 1u, s2 ? 2u : 1u, s2 ? 2u : 1u, 1};
+    return enc(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void *>(d_in16), gdim, gstr, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int MODE, bool TMA>
+static fe_status launch_tc(const float *d_in, const void *d_in16, int cin, const int *h_dims, const void *d_img,
+                           const float *d_bias, float *d_out, int cout, const int *h_dims_out, int relu,
+                           cudaStream_t stream) {
     if (cout != 16 && cout != 32 && cout != 64) return FE_ERR_ARG;
     if (!aligned(d_img, 16)) return FE_ERR_ARG;
     // the MMA rows stand for output positions (stride 2) or input positions
     const int *tdims = MODE == FE_NN_S2 ? h_dims_out : h_dims;
     TcGeom g;
-    if (!choose_geom(MODE, tdims[2], tdims[1], cout, &g)) return FE_ERR_ARG;
+    if (!choose_geom(MODE, tdims[2], tdims[1], cout, &g, TMA)) return FE_ERR_ARG;
+    CUtensorMap tm;
+    memset(&tm, 0, sizeof(tm));
+    if (TMA && !encode_input_map(&tm, MODE, d_in16, cin, h_dims, g)) return FE_ERR_CUDA;
     // request enough shared memory that no more than ctas_per_sm blocks share
     // an SM, so their tensor-memory allocations always fit together
     size_t smem = g.smem;
     const size_t floor_bytes = (size_t)233472 / (size_t)(g.ctas_per_sm + 1) - 1024 + 16;
     if (smem < floor_bytes) smem = floor_bytes;
     if (smem > (size_t)232448) smem = 232448;
-    auto kern = k_conv_tc<MODE>;
+    auto kern = k_conv_tc<MODE, TMA>;
     FE_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     FE_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTcThreads, smem));
@@ -432,9 +543,28 @@ static fe_status launch_tc(const float *d_in, int cin, const int *h_dims, const 
     TcDims dm{h_dims[0], h_dims[1], h_dims[2]};
     TcDims dout{h_dims_out[0], h_dims_out[1], h_dims_out[2]};
     kern<<<(int)grid, kTcThreads, smem, stream>>>(d_in, cin, dm, (const __nv_bfloat16 *)d_img, d_bias, d_out,
-                                                   cout, dout, relu, g);
+                                                   cout, dout, relu, g, tm);
     FE_TRY_LAUNCH();
     return FE_OK;
+}
+
+// FP32 [C][V] -> BF16 [ceil(C/8)][V][8] (channels past C are 0)
+__global__ void k_to_bf16i(const float *__restrict__ in, int c, size_t v, __nv_bfloat16 *__restrict__ out) {
+    const int groups = (c + 7) / 8;
+    const size_t n = (size_t)groups * v;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const int gq = (int)(i / v);
+        const size_t vi = i % v;
+        __nv_bfloat162 h[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int c0 = 8 * gq + 2 * j;
+            const float a = c0 < c ? in[(size_t)c0 * v + vi] : 0.0f;
+            const float b = c0 + 1 < c ? in[(size_t)(c0 + 1) * v + vi] : 0.0f;
+            h[j] = __floats2bfloat162_rn(a, b);
+        }
+        reinterpret_cast<uint4 *>(out)[i] = *reinterpret_cast<const uint4 *>(h);
+    }
 }
 
 }  // namespace fe
@@ -463,7 +593,8 @@ fe_status fe_nn_conv3d_s1_tc(const float *d_in, int cin, const int *h_dims, cons
                              const float *d_bias, float *d_out, int cout, int relu, fe_stream_t stream) {
     if (!d_in || !d_img || !d_out || cin < 1 || !h_dims || h_dims[0] < 1 || h_dims[1] < 1 || h_dims[2] < 1)
         return FE_ERR_ARG;
-    return launch_tc<FE_NN_S1>(d_in, cin, h_dims, d_img, d_bias, d_out, cout, h_dims, relu, (cudaStream_t)stream);
+    return launch_tc<FE_NN_S1, false>(d_in, nullptr, cin, h_dims, d_img, d_bias, d_out, cout, h_dims, relu,
+                                      (cudaStream_t)stream);
 }
 
 fe_status fe_nn_conv3d_t2_tc(const float *d_in, int cin, const int *h_dims_in, const void *d_img,
@@ -472,8 +603,8 @@ fe_status fe_nn_conv3d_t2_tc(const float *d_in, int cin, const int *h_dims_in, c
     if (!d_in || !d_img || !d_out || cin < 1 || !h_dims_in || !h_dims_out) return FE_ERR_ARG;
     for (int i = 0; i < 3; ++i)
         if (h_dims_in[i] < 1 || h_dims_out[i] != 2 * (h_dims_in[i] - 1) + 1) return FE_ERR_ARG;
-    return launch_tc<FE_NN_T2>(d_in, cin, h_dims_in, d_img, d_bias, d_out, cout, h_dims_out, relu,
-                               (cudaStream_t)stream);
+    return launch_tc<FE_NN_T2, false>(d_in, nullptr, cin, h_dims_in, d_img, d_bias, d_out, cout, h_dims_out, relu,
+                                      (cudaStream_t)stream);
 }
 
 fe_status fe_nn_conv3d_s2_tc(const float *d_in, int cin, const int *h_dims_in, const void *d_img,
@@ -482,8 +613,46 @@ fe_status fe_nn_conv3d_s2_tc(const float *d_in, int cin, const int *h_dims_in, c
     if (!d_in || !d_img || !d_out || cin < 1 || !h_dims_in || !h_dims_out) return FE_ERR_ARG;
     for (int i = 0; i < 3; ++i)
         if (h_dims_in[i] < 1 || h_dims_out[i] != (h_dims_in[i] - 1) / 2 + 1) return FE_ERR_ARG;
-    return launch_tc<FE_NN_S2>(d_in, cin, h_dims_in, d_img, d_bias, d_out, cout, h_dims_out, relu,
-                               (cudaStream_t)stream);
+    return launch_tc<FE_NN_S2, false>(d_in, nullptr, cin, h_dims_in, d_img, d_bias, d_out, cout, h_dims_out, relu,
+                                      (cudaStream_t)stream);
+}
+
+fe_status fe_nn_bf16i_bytes(int c, const int *h_dims, size_t *h_bytes) {
+    if (c < 1 || !h_dims || !h_bytes || h_dims[0] < 1 || h_dims[1] < 1 || h_dims[2] < 1) return FE_ERR_ARG;
+    *h_bytes = (size_t)((c + 7) / 8) * h_dims[0] * h_dims[1] * h_dims[2] * 16;
+    return FE_OK;
+}
+
+fe_status fe_nn_to_bf16i(const float *d_in, int c, const int *h_dims, void *d_out, fe_stream_t stream) {
+    if (!d_in || !d_out || c < 1 || !h_dims || h_dims[0] < 1 || h_dims[1] < 1 || h_dims[2] < 1) return FE_ERR_ARG;
+    if (!aligned(d_out, 16)) return FE_ERR_ARG;
+    const size_t v = (size_t)h_dims[0] * h_dims[1] * h_dims[2];
+    const size_t n = (size_t)((c + 7) / 8) * v;
+    const int blocks = (int)((n + 255) / 256 < 8192 ? (n + 255) / 256 : 8192);
+    k_to_bf16i<<<blocks, 256, 0, (cudaStream_t)stream>>>(d_in, c, v, (__nv_bfloat16 *)d_out);
+    FE_TRY_LAUNCH();
+    return FE_OK;
+}
+
+fe_status fe_nn_conv3d_tc_bf16i(int mode, const void *d_in16, int cin, const int *h_dims_in, const void *d_img,
+                                const float *d_bias, float *d_out, int cout, const int *h_dims_out, int relu,
+                                fe_stream_t stream) {
+    if (!d_in16 || !d_img || !d_out || cin < 1 || !h_dims_in || !h_dims_out) return FE_ERR_ARG;
+    if (!aligned(d_in16, 16)) return FE_ERR_ARG;
+    for (int i = 0; i < 3; ++i) {
+        if (h_dims_in[i] < 1) return FE_ERR_ARG;
+        const int want = mode == FE_NN_S1 ? h_dims_in[i]
+                                          : (mode == FE_NN_S2 ? (h_dims_in[i] - 1) / 2 + 1 : 2 * (h_dims_in[i] - 1) + 1);
+        if (h_dims_out[i] != want) return FE_ERR_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (mode == FE_NN_S1)
+        return launch_tc<FE_NN_S1, true>(nullptr, d_in16, cin, h_dims_in, d_img, d_bias, d_out, cout, h_dims_out, relu, s);
+    if (mode == FE_NN_S2)
+        return launch_tc<FE_NN_S2, true>(nullptr, d_in16, cin, h_dims_in, d_img, d_bias, d_out, cout, h_dims_out, relu, s);
+    if (mode == FE_NN_T2)
+        return launch_tc<FE_NN_T2, true>(nullptr, d_in16, cin, h_dims_in, d_img, d_bias, d_out, cout, h_dims_out, relu, s);
+    return FE_ERR_ARG;
 }
 
 fe_status fe_nn_tc_check(int *h_flag) {

@@ -127,6 +127,10 @@ SIGNATURES = {
                                   ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int, _VP]),
     "fe_nn_conv3d_s2_tc": (_I32, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _VP, _VP, _VP,
                                   ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int, _VP]),
+    "fe_nn_bf16i_bytes": (_I32, [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_SZ)]),
+    "fe_nn_to_bf16i": (_I32, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _VP, _VP]),
+    "fe_nn_conv3d_tc_bf16i": (_I32, [ctypes.c_int, _VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _VP, _VP, _VP,
+                                     ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int, _VP]),
     "fe_nn_tc_check": (_I32, [ctypes.POINTER(ctypes.c_int)]),
     "fe_warmstart_blob_layout": (_I32, [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_SZ), ctypes.POINTER(_SZ)]),
     "fe_warmstart_workspace": (_I32, [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_SZ)]),
@@ -438,6 +442,29 @@ def conv3d_tc(mode, x, cin, dims_in, img, bias, y, cout, dims_out, relu, stream=
     if mode == "s2":
         return fe_nn_conv3d_s2_tc(x, cin, dims_in, img, bias, y, cout, dims_out, relu, stream)
     return fe_nn_conv3d_t2_tc(x, cin, dims_in, img, bias, y, cout, dims_out, relu, stream)
+
+
+def fe_nn_bf16i_bytes(c, dims) -> int:
+    n = ctypes.c_size_t(0)
+    _check("fe_nn_bf16i_bytes", load().fe_nn_bf16i_bytes(int(c), _dims(dims), ctypes.byref(n)))
+    return n.value
+
+
+def fe_nn_to_bf16i(x, c, dims, out, stream=None):
+    return _check("fe_nn_to_bf16i", load().fe_nn_to_bf16i(_ptr(x), int(c), _dims(dims), _ptr(out),
+                                                          _stream(stream)))
+
+
+def fe_nn_conv3d_tc_bf16i(mode, x16, cin, dims_in, img, bias, y, cout, dims_out, relu, stream=None):
+    m = NN_MODES[mode] if isinstance(mode, str) else int(mode)
+    return _check("fe_nn_conv3d_tc_bf16i", load().fe_nn_conv3d_tc_bf16i(
+        m, _ptr(x16), int(cin), _dims(dims_in), _ptr(img), _ptr(bias), _ptr(y), int(cout), _dims(dims_out),
+        int(relu), _stream(stream)))
+
+
+def bf16i_buffer(c, dims, device="cuda") -> torch.Tensor:
+    """Buffer for a BF16 8-channel-interleaved volume."""
+    return _alloc_bytes(fe_nn_bf16i_bytes(c, dims), device)
 
 
 def fe_nn_tc_check() -> int:

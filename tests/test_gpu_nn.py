@@ -393,3 +393,51 @@ def test_warmstart_infer_matches_oracle_network(fe):
     assert np.array_equal(got[flag != 0], val[flag != 0])
     inner = flag == 0
     assert np.max(np.abs(got[inner] - pred[inner])) <= 1e-4 * np.max(np.abs(pred))
+
+
+def test_to_bf16i_layout(fe):
+    """fe_nn_to_bf16i: [ceil(C/8)][V][8] BF16, nearest even, channels past C zero."""
+    g = np.random.default_rng(20)
+    c, dims = 11, (3, 4, 5)
+    x = g.standard_normal((c,) + dims).astype(np.float32)
+    buf = fe.bf16i_buffer(c, dims)
+    fe.fe_nn_to_bf16i(cuda32(x), c, dims, buf)
+    got = buf.view(torch.bfloat16).float().cpu().numpy().reshape(2, -1, 8)
+    want = np.zeros((2, 60, 8))
+    want[0] = bf16(x[:8].reshape(8, -1)).T
+    want[1, :, :3] = bf16(x[8:].reshape(3, -1)).T
+    assert np.array_equal(got, want)
+
+
+TMA_CASES = [("s1", 16, 32, (9, 7, 11)), ("s1", 20, 16, (4, 3, 129)), ("s1", 64, 64, (5, 5, 5)),
+             ("s2", 16, 32, (9, 7, 11)), ("s2", 20, 16, (33, 9, 129)), ("s2", 32, 64, (17, 17, 17)),
+             ("t2", 16, 16, (5, 4, 6)), ("t2", 64, 32, (9, 9, 9)), ("t2", 16, 32, (3, 5, 65)),
+             ("s1", 16, 16, (1, 1, 1)), ("s2", 16, 16, (2, 3, 4))]
+
+
+@pytest.mark.parametrize("mode,cin,cout,dims", TMA_CASES)
+def test_conv_tensor_cores_tma_staging(fe, mode, cin, cout, dims):
+    """The TMA-staged tensor-core kernels (BF16 interleaved input) against the
+    FP64 oracle with the BF16 bound, and bit for bit against the FP32-input
+    tensor-core kernels (both round the same values to BF16 and run the same
+    MMAs in the same order)."""
+    x, W, b = layer_setup(mode, cin, cout, dims, 21)
+    dout = onn.out_dims(mode, dims)
+    w16 = torch.empty(cin * 27 * cout, dtype=torch.bfloat16, device="cuda")
+    fe.fe_nn_pack_weights(cuda32(W), cin, cout, 0, 0, w16)
+    img = fe.mma_image(cin, cout)
+    fe.fe_nn_pack_weights_mma(w16, cin, cout, img)
+    x16 = fe.bf16i_buffer(cin, dims)
+    fe.fe_nn_to_bf16i(cuda32(x), cin, dims, x16)
+    y = torch.full((cout,) + dout, float("nan"), dtype=torch.float32, device="cuda")
+    fe.fe_nn_conv3d_tc_bf16i(mode, x16, cin, dims, img, cuda32(b), y, cout, dout, 1)
+    ref = np.maximum(onn.conv(mode, x.astype(np.float64), W, b), 0)
+    bound = onn.conv(mode, np.abs(x).astype(np.float64), np.abs(W), np.abs(b))
+    tol = (2.0 ** -8 + 2 * (cin * 27 + 1) * U32) * bound + 1e-30
+    got = y.cpu().numpy()
+    assert np.all(np.isfinite(got))
+    assert np.all(np.abs(got - ref) <= tol), float(np.max(np.abs(got - ref) / tol))
+    y2 = torch.empty_like(y)
+    fe.conv3d_tc(mode, cuda32(x), cin, dims, img, cuda32(b), y2, cout, dout, 1)
+    assert torch.equal(y, y2)
+    assert fe.fe_nn_tc_check() == 0
