@@ -414,6 +414,19 @@ fe_status fe_nn_conv3d_t2_tc(const float *d_in, int cin, const int *h_dims_in, c
 fe_status fe_nn_conv3d_s2_tc(const float *d_in, int cin, const int *h_dims_in, const void *d_img,
                              const float *d_bias, float *d_out, int cout, const int *h_dims_out,
                              int relu, fe_stream_t stream);
+/* Tensor-core convolution (mode FE_NN_S1, FE_NN_S2 or FE_NN_T2) reading its
+ * input as BF16 in the 8-channel-interleaved layout [ceil(cin/8)][D][H][W][8]
+ * that fe_nn_to_bf16i writes (fe_nn_bf16i_bytes bytes, 16-byte aligned).  The
+ * input box of each 16-channel chunk is staged by tensor-map (TMA) loads with
+ * zero fill outside the grid; otherwise as fe_nn_conv3d_{s1,s2,t2}_tc (same
+ * result bits: the FP32 kernels round the same values to BF16).  The fine
+ * box of a stride-2 layer must be at most 256 points per row after the
+ * stride (output width <= 127). */
+fe_status fe_nn_bf16i_bytes(int c, const int *h_dims, size_t *h_bytes);
+fe_status fe_nn_to_bf16i(const float *d_in, int c, const int *h_dims, void *d_out, fe_stream_t stream);
+fe_status fe_nn_conv3d_tc_bf16i(int mode, const void *d_in16, int cin, const int *h_dims_in, const void *d_img,
+                                const float *d_bias, float *d_out, int cout, const int *h_dims_out, int relu,
+                                fe_stream_t stream);
 /* Synchronises the device; *h_flag = 1 if a tensor-core kernel gave up a wait
  * since the last call (then clears the flag), else 0. */
 fe_status fe_nn_tc_check(int *h_flag);
@@ -473,8 +486,9 @@ fe_status fe_warmstart_output(const float *d_pred, const uint8_t *d_bc_flag, con
  * weights BF16 [c0] and bias FP32 [1]; fe_warmstart_blob_layout gives the 28
  * section offsets (each 256-byte aligned) and the size.  tensor_cores != 0
  * runs every layer with >= 16 input and 16/32/64 output channels on the
- * tensor cores (BF16 activations), the others on CUDA cores.  d_work:
- * fe_warmstart_workspace bytes, 256-byte aligned.  Enqueues on `stream`,
+ * tensor cores (BF16 activations: each such layer's input is converted by
+ * fe_nn_to_bf16i into a scratch area of the workspace and staged by TMA), the
+ * others on CUDA cores.  d_work: fe_warmstart_workspace bytes, 256-byte aligned.  Enqueues on `stream`,
  * allocates nothing.
  */
 fe_status fe_warmstart_blob_layout(const int *h_channels, size_t *h_offsets /* 28 or NULL */,

@@ -59,7 +59,7 @@ static size_t ws_blob_offsets(const int *c, size_t *off) {
 }
 
 struct WsWork {
-    size_t x_in, vol[15], pred, img[13], total;
+    size_t x_in, vol[15], pred, img[13], bf16i, total;
 };
 
 // activation buffers: x_in, e0 d1 e1 d2 e2 d3 e3 s2 f2 s1 f1 s0 f0 (13 volumes), pred; tensor-core images
@@ -83,10 +83,17 @@ static bool ws_work_layout(int n0, const int *c, WsWork *w) {
     o += al256(nl[0] * 4);
     WsLayer L[13];
     ws_layers(c, L);
+    size_t b16 = 0;   // largest BF16 interleaved layer input
     for (int i = 0; i < 13; ++i) {
         w->img[i] = o;
-        if (ws_tc_ok(L[i])) o += al256((size_t)((L[i].cin + 15) / 16) * 27 * 2 * L[i].cout * 16);
+        if (ws_tc_ok(L[i])) {
+            o += al256((size_t)((L[i].cin + 15) / 16) * 27 * 2 * L[i].cout * 16);
+            const size_t need = (size_t)((L[i].cin + 7) / 8) * nl[L[i].lin] * 16;
+            if (need > b16) b16 = need;
+        }
     }
+    w->bf16i = o;
+    o += al256(b16);
     w->total = o;
     return true;
 }
@@ -156,13 +163,11 @@ fe_status fe_warmstart_infer(int n_nodes, const int *h_channels, const void *d_b
         const WsLayer &l = L[i];
         float *dst = vol(i);
         if (tc && ws_tc_ok(l)) {
-            if (l.mode == FE_NN_S1)
-                return fe_nn_conv3d_s1_tc(src, l.cin, dims[l.lin], ws + w.img[i], bias(i), dst, l.cout, relu, stream);
-            if (l.mode == FE_NN_S2)
-                return fe_nn_conv3d_s2_tc(src, l.cin, dims[l.lin], ws + w.img[i], bias(i), dst, l.cout,
-                                          dims[l.lout], relu, stream);
-            return fe_nn_conv3d_t2_tc(src, l.cin, dims[l.lin], ws + w.img[i], bias(i), dst, l.cout, dims[l.lout],
-                                      relu, stream);
+            // BF16 interleaved copy of the input, staged by TMA in the conv
+            const fe_status cs = fe_nn_to_bf16i(src, l.cin, dims[l.lin], ws + w.bf16i, stream);
+            if (cs != FE_OK) return cs;
+            return fe_nn_conv3d_tc_bf16i(l.mode, ws + w.bf16i, l.cin, dims[l.lin], ws + w.img[i], bias(i), dst,
+                                         l.cout, dims[l.lout], relu, stream);
         }
         return fe_nn_conv3d(l.mode, src, l.cin, dims[l.lin], wts(i), bias(i), dst, l.cout, dims[l.lout], relu,
                             stream);

@@ -138,10 +138,22 @@ class WarmStartNet:
             self.buf[key] = t
         return t
 
+    def bf16i(self, x, c, level):
+        """x as BF16 8-channel-interleaved (the TMA-staged kernels' input)."""
+        key = ("bf16i", c, level)
+        buf = self.buf.get(key)
+        if buf is None:
+            buf = fe.bf16i_buffer(c, self.dims[level], self.dev)
+            self.buf[key] = buf
+        fe.fe_nn_to_bf16i(x, c, self.dims[level], buf)
+        return buf
+
     def conv(self, lname, x, lin, y, lout, relu):
         l = self.layers[lname]
         if l.img is not None:
-            fe.conv3d_tc(l.mode, x, l.cin, self.dims[lin], l.img, l.b, y, l.cout, self.dims[lout], relu)
+            x16 = self.bf16i(x, l.cin, lin)
+            fe.fe_nn_conv3d_tc_bf16i(l.mode, x16, l.cin, self.dims[lin], l.img, l.b, y, l.cout, self.dims[lout],
+                                     relu)
         else:
             fe.fe_nn_conv3d(fe.NN_MODES[l.mode], x, l.cin, self.dims[lin], l.w16, l.b, y, l.cout,
                             self.dims[lout], relu)
@@ -161,8 +173,9 @@ class WarmStartNet:
         fe.fe_nn_channel_sum(dy, l.cout, self.dims[lout], l.gb)
         if dx is not None:
             if l.imgt is not None:
-                fe.conv3d_tc(ADJOINT[l.mode], dy, l.cout, self.dims[lout], l.imgt, None, dx, l.cin,
-                             self.dims[lin], 0)
+                dy16 = self.bf16i(dy, l.cout, lout)
+                fe.fe_nn_conv3d_tc_bf16i(ADJOINT[l.mode], dy16, l.cout, self.dims[lout], l.imgt, None, dx, l.cin,
+                                         self.dims[lin], 0)
             else:
                 fe.fe_nn_conv3d(fe.NN_MODES[ADJOINT[l.mode]], dy, l.cout, self.dims[lout], l.wt16, None,
                                 dx, l.cin, self.dims[lin], 0)
