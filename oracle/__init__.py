@@ -23,6 +23,9 @@ Parity pins (each checked by ``tests/test_oracle_*.py``):
                             steps), textbook CG's iterates step by step,
                             dense direct solve, status codes
   * whole solve          -- series solution: centre value 1/6, O(h^2) error
+  * matrix-free operator -- the assembled (element-integral) operator and
+                            right-hand side on cubes and bricks; the closed-form
+                            cube stencil; dense 1D Kronecker sums
 """
 from __future__ import annotations
 
@@ -97,6 +100,14 @@ def _load():
         lib.orc_cg_sr.argtypes = lib.orc_cg.argtypes
         lib.orc_true_relres.restype = f64
         lib.orc_true_relres.argtypes = [i64, _i32p, _i32p, _f64p, _f64p, _f64p]
+        lib.orc_stencil_coeffs.restype = None
+        lib.orc_stencil_coeffs.argtypes = [i32, i32, i32, _f64p]
+        lib.orc_stencil_row.restype = f64
+        lib.orc_stencil_row.argtypes = [i32, i32, i32, i64, _f64p]
+        lib.orc_stencil_spmv.restype = None
+        lib.orc_stencil_spmv.argtypes = [i32, i32, i32, _f64p, _f64p]
+        lib.orc_stencil_rhs.restype = None
+        lib.orc_stencil_rhs.argtypes = [i32, i32, i32, _f64p, _f64p]
         _lib = lib
         return lib
 
@@ -259,6 +270,46 @@ def solve(nx: int, ny: int, nz: int, tol=1e-10, maxit=1000, face_vals=None, x0=N
     sysm = build_system(nx, ny, nz, face_vals)
     x, it, rel, st = cg(sysm["row_ptr"], sysm["cols"], sysm["vals"], sysm["b"], x0, tol, maxit)
     return sysm, x, it, rel, st
+
+
+# ----------------------------------------------------------------------------
+# matrix-free form of the same system (Kronecker-sum stencil of the brick
+# element; boundary rows identity, boundary columns eliminated)
+# ----------------------------------------------------------------------------
+
+def stencil_coeffs(nx: int, ny: int, nz: int) -> np.ndarray:
+    """Interior stencil a[dz+1, dy+1, dx+1] of the assembled operator."""
+    a = np.empty(27, dtype=np.float64)
+    _load().orc_stencil_coeffs(nx, ny, nz, a)
+    return a.reshape(3, 3, 3)
+
+
+def stencil_spmv(nx: int, ny: int, nz: int, x) -> np.ndarray:
+    """y = A x of the Dirichlet system without a stored matrix."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    if x.shape[0] != num_nodes(nx, ny, nz):
+        raise ValueError("x has the wrong length")
+    y = np.empty_like(x)
+    _load().orc_stencil_spmv(nx, ny, nz, x, y)
+    return y
+
+
+def stencil_row(nx: int, ny: int, nz: int, i: int, x) -> float:
+    """(A x)_i for one row, matrix-free (for sampled checks on large meshes)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    if x.shape[0] != num_nodes(nx, ny, nz) or not 0 <= i < x.shape[0]:
+        raise ValueError("bad row or vector length")
+    return _load().orc_stencil_row(nx, ny, nz, int(i), x)
+
+
+def stencil_rhs(nx: int, ny: int, nz: int, bc_val) -> np.ndarray:
+    """Right-hand side of the eliminated system from the boundary values."""
+    g = np.ascontiguousarray(bc_val, dtype=np.float64)
+    if g.shape[0] != num_nodes(nx, ny, nz):
+        raise ValueError("bc_val has the wrong length")
+    b = np.empty_like(g)
+    _load().orc_stencil_rhs(nx, ny, nz, g, b)
+    return b
 
 
 def dense(row_ptr, cols, vals) -> np.ndarray:

@@ -565,3 +565,104 @@ double orc_true_relres(int64_t m, const int32_t *row_ptr, const int32_t *cols,
         return sqrt(rn);
     return sqrt(rn / bn);
 }
+
+/* ------------------------------------------------------------------------ */
+/* Matrix-free form of the same Dirichlet system (an extension beside the    */
+/* paper's stored CRS/BCRS formats: the operator applied without a matrix).  */
+/*                                                                          */
+/* On the box mesh every element is the same axis-aligned brick, and the     */
+/* stiffness of the trilinear brick is a Kronecker sum of 1D operators:      */
+/*   K = Lx (x) My (x) Mz  +  Mx (x) Ly (x) Mz  +  Mx (x) My (x) Lz,          */
+/* with the 1D linear-element mass M = h [1/3 1/6; 1/6 1/3] and stiffness    */
+/* L = (1/h) [1 -1; -1 1].  The elements form a Cartesian product, so the    */
+/* assembled matrix is the same Kronecker sum of the assembled 1D matrices.  */
+/* At a node with neighbours on both sides along every axis (an interior     */
+/* node) those are M(0) = 2h/3, M(+-1) = h/6, L(0) = 2/h, L(+-1) = -1/h, so  */
+/* its row holds, at offset (dx, dy, dz) in {-1, 0, 1}^3,                    */
+/*   a(dx,dy,dz) = Lx(dx) My(dy) Mz(dz) + Mx(dx) Ly(dy) Mz(dz)                */
+/*               + Mx(dx) My(dy) Lz(dz),   h_axis = 1 / n_axis.              */
+/* On a cube this is 8h/3 at the centre, 0 at the 6 faces, -h/6 at the 12    */
+/* edges and -h/12 at the 8 corners (the assembled stencil the element       */
+/* integral gives).  The Dirichlet elimination (orc_dirichlet) turns         */
+/* boundary rows into identity rows and drops boundary columns.              */
+/* a[(dz+1)*9 + (dy+1)*3 + (dx+1)] = a(dx, dy, dz).                          */
+/* ------------------------------------------------------------------------ */
+void orc_stencil_coeffs(int nx, int ny, int nz, double a[27])
+{
+    double h[3] = {1.0 / (double)nx, 1.0 / (double)ny, 1.0 / (double)nz};
+    double M[3][3], L[3][3];   /* [axis][offset + 1] */
+    for (int ax = 0; ax < 3; ++ax) {
+        M[ax][0] = h[ax] / 6.0;
+        M[ax][1] = 2.0 * h[ax] / 3.0;
+        M[ax][2] = h[ax] / 6.0;
+        L[ax][0] = -1.0 / h[ax];
+        L[ax][1] = 2.0 / h[ax];
+        L[ax][2] = -1.0 / h[ax];
+    }
+    for (int dz = 0; dz < 3; ++dz)
+        for (int dy = 0; dy < 3; ++dy)
+            for (int dx = 0; dx < 3; ++dx)
+                a[dz * 9 + dy * 3 + dx] = L[0][dx] * M[1][dy] * M[2][dz]
+                                        + M[0][dx] * L[1][dy] * M[2][dz]
+                                        + M[0][dx] * M[1][dy] * L[2][dz];
+}
+
+static int is_boundary_node(int nx, int ny, int nz, int ix, int iy, int iz)
+{
+    return ix == 0 || ix == nx || iy == 0 || iy == ny || iz == 0 || iz == nz;
+}
+
+/* (A x)_i of the Dirichlet system for one row i, matrix-free. */
+double orc_stencil_row(int nx, int ny, int nz, int64_t i, const double *x)
+{
+    double a[27];
+    orc_stencil_coeffs(nx, ny, nz, a);
+    int64_t sx = nx + 1, sxy = (int64_t)(nx + 1) * (ny + 1);
+    int ix = (int)(i % sx), iy = (int)((i / sx) % (ny + 1)), iz = (int)(i / sxy);
+    if (is_boundary_node(nx, ny, nz, ix, iy, iz))
+        return x[i];                                   /* identity row */
+    double s = 0.0;
+    for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                if (is_boundary_node(nx, ny, nz, ix + dx, iy + dy, iz + dz))
+                    continue;                          /* eliminated column */
+                s += a[(dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)] *
+                     x[node_id(nx, ny, ix + dx, iy + dy, iz + dz)];
+            }
+    return s;
+}
+
+/* y = A x over all rows, matrix-free. */
+void orc_stencil_spmv(int nx, int ny, int nz, const double *x, double *y)
+{
+    int64_t m = orc_num_nodes(nx, ny, nz);
+    for (int64_t i = 0; i < m; ++i)
+        y[i] = orc_stencil_row(nx, ny, nz, i, x);
+}
+
+/* Right-hand side of the eliminated system, matrix-free: b_i = g_i on a     */
+/* boundary node; elsewhere b_i = 0 - sum over boundary neighbours j of       */
+/* a(j - i) g_j (zero source term, the boundary columns moved to the right). */
+void orc_stencil_rhs(int nx, int ny, int nz, const double *bc_val, double *b)
+{
+    double a[27];
+    orc_stencil_coeffs(nx, ny, nz, a);
+    for (int iz = 0; iz <= nz; ++iz)
+        for (int iy = 0; iy <= ny; ++iy)
+            for (int ix = 0; ix <= nx; ++ix) {
+                int64_t i = node_id(nx, ny, ix, iy, iz);
+                if (is_boundary_node(nx, ny, nz, ix, iy, iz)) {
+                    b[i] = bc_val[i];
+                    continue;
+                }
+                double s = 0.0;
+                for (int dz = -1; dz <= 1; ++dz)
+                    for (int dy = -1; dy <= 1; ++dy)
+                        for (int dx = -1; dx <= 1; ++dx)
+                            if (is_boundary_node(nx, ny, nz, ix + dx, iy + dy, iz + dz))
+                                s += a[(dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)] *
+                                     bc_val[node_id(nx, ny, ix + dx, iy + dy, iz + dz)];
+                b[i] = 0.0 - s;
+            }
+}
