@@ -26,6 +26,10 @@ Reported (one JSON line on rank 0):
                and with BF16 values, times, steps, true residuals and errors
   single_reduction  the Chronopoulos-Gear CG (one grid reduction per step) on
                the same system, and both CG forms on the N = 30 mesh
+  matrix_free  the same system and CG with the operator applied from the
+               brick element's Kronecker structure (no stored matrix): time to
+               1e-10, steps, difference from the assembled solution, and the
+               stand-alone operator pass against the FP64 pipe
   cpu_baseline the CPU oracle, single core, on a bounded sample of the same
                workload (a few CG iterations of the N = 256 system), scaled
                to the solve's iteration count
@@ -292,6 +296,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-sr", action="store_true", help="skip the single-reduction CG legs")
     ap.add_argument("--no-n400", action="store_true", help="skip the N=400 mixed-precision leg")
+    ap.add_argument("--no-matrix-free", action="store_true", help="skip the matrix-free leg")
     ap.add_argument("--batch-size", type=int, default=64)
     args = ap.parse_args()
 
@@ -489,6 +494,11 @@ def main():
         del small, As, xsm
         torch.cuda.empty_cache()
 
+    # ---- matrix-free operator: the same system and CG without a stored matrix
+    matrix_free = None
+    if not args.no_matrix_free:
+        matrix_free = run_matrix_free(args, fe, torch, dev, EV, n, s, x, cg_ms)
+
     # ---- batched form: 64 cubic meshes N ~ U{32..128}, random face data
     batched = None
     if not args.no_batched and world == 1:
@@ -586,6 +596,7 @@ def main():
                 "cg_ms_per_iteration": round(cg_ms / max(it, 1), 4),
                 "phase_ms": {k: round(statistics.mean(v), 3) for k, v in phases.items()},
                 "roofline": roofline, "mixed": mixed, "mixed_n400": n400, "single_reduction": single_red,
+                "matrix_free": matrix_free,
                 "batched": batched, "spmv": spmv, "e2e": e2e,
                 "cpu_baseline": cpu, "cpu_parallel": cpu_par,
                 "clocks": clocks, "gpu_launches": launches_per_step * args.steps,
@@ -593,6 +604,77 @@ def main():
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def matrix_free_ops(n: int):
+    """FP64 pipe operations (add, mul and FMA one each) of the matrix-free
+    path on the N^3 cube: the operator takes 11 per interior row (plane sums
+    Sx, Sy, D: 5; P = c3 (Sx + Sy) + c7 D: 3; c0 X + c3 D + P(z-1) + P(z+1):
+    3); a CG step adds the p.w product, the x update and the staging of
+    p = r + beta p in phase A (3 per interior row; 3 per boundary row in all)
+    and r -= alpha w, r.r in phase B (2 per row).  Halo recomputation (the
+    2 extra planes per column segment, the 1.33x staged p) is not counted."""
+    m = (n + 1) ** 3
+    inner = (n - 1) ** 3
+    bc = m - inner
+    return {"spmv": 11 * inner, "step": 14 * inner + 3 * bc + 2 * m, "init": 12 * inner + 2 * m}
+
+
+def run_matrix_free(args, fe, torch, dev, EV, n: int, s, x_assembled, cg_ms: float):
+    """The N^3 system without a stored matrix: right-hand side from the
+    boundary values, CG to 1e-10 (CUDA events around fe_stencil_cg_solve,
+    one launch of k_cg_stencil), its difference from the assembled solve, and
+    the stand-alone operator pass (L2 flushed between passes)."""
+    mf = fe.StencilSystem(n, device=dev).build()
+    rhs_diff = float((mf.b - s.b).abs().max())
+    xm = torch.zeros(mf.m, dtype=torch.float64, device=dev)
+    ts = []
+    for i in range(args.warmup + args.steps):
+        xm.zero_()
+        a, b = EV(), EV()
+        a.record()
+        r = mf.solve(xm, TOL, MAXIT, check=False)
+        b.record()
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            ts.append(a.elapsed_time(b))
+    t_ms = statistics.mean(ts)
+    ops = matrix_free_ops(n)
+    fp64_ops_peak = FP64_PEAK_TFLOPS * 1e12 / 2       # pipe operations per second
+    step_ops = ops["init"] + r.iterations * ops["step"]
+    out = {"value": round(t_ms * 1e-3, 6), "unit": "s", "iterations": r.iterations, "status": r.status,
+           "ms_per_iteration": round(t_ms / max(r.iterations, 1), 4),
+           "speedup_vs_assembled": round(cg_ms / t_ms, 3),
+           "rel_diff_vs_assembled_solution": float(torch.linalg.norm(xm - x_assembled) /
+                                                   torch.linalg.norm(x_assembled)),
+           "max_abs_rhs_diff_vs_assembled": rhs_diff,
+           "relres_true": mf.true_relres(xm),
+           "roofline": {"bound": "alu", "achieved": round(step_ops / (t_ms * 1e-3) / 1e9, 1),
+                        "peak": round(fp64_ops_peak / 1e9, 1), "unit": "GFP64op/s",
+                        "frac": round(step_ops / (t_ms * 1e-3) / fp64_ops_peak, 4),
+                        "ops_per_interior_row_step": 14, "vector_bytes_per_row_step": 72}}
+    yv = torch.empty_like(xm)
+    xv = torch.rand(mf.m, dtype=torch.float64, device=dev)
+    flush = torch.empty(512 * 2 ** 20, dtype=torch.uint8, device=dev)
+    sp = []
+    for i in range(7):
+        flush.zero_()
+        a, b = EV(), EV()
+        a.record()
+        mf.spmv(xv, yv)
+        b.record()
+        torch.cuda.synchronize()
+        if i >= 2:
+            sp.append(a.elapsed_time(b))
+    t = statistics.median(sp)
+    out["spmv"] = {"ms": round(t, 4), "fp64_ops_per_row": 11,
+                   "gops": round(ops["spmv"] / t / 1e6, 1),
+                   "frac_fp64": round(ops["spmv"] / (t * 1e-3) / fp64_ops_peak, 4),
+                   "algorithmic_gb": round(16 * mf.m / 1e9, 4),
+                   "gbs": round(16 * mf.m / t / 1e6, 1)}
+    del mf, xm, yv, xv, flush
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_n400(args, fe, torch, dev, EV, n: int = 400):

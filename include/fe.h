@@ -110,8 +110,12 @@ fe_status fe_problem_sizes(int nx, int ny, int nz, fe_sizes *h_out);
  *                an x face is indexed iy + (ny+1) iz, a y face ix + (nx+1) iz,
  *                a z face ix + (nx+1) iy; a later face overwrites an earlier
  *                one on a shared edge.
- *   d_coords     [m][3] double;  d_bc_flag [m] uint8;  d_bc_val [m] double.
+ *   d_coords     [m][3] double, or NULL (not written: the matrix-free path
+ *                needs no coordinates);  d_bc_flag [m] uint8;  d_bc_val [m] double.
  *   d_conn       optional [n_elems][8] int32 element node ids, or NULL.
+ * The mesh has no nnz limit (the matrix-free path takes meshes past the CSR
+ * form's int32 limit); FE_ERR_OVERFLOW only if d_conn is requested and m
+ * exceeds INT32_MAX.
  */
 fe_status fe_generate_mesh(int nx, int ny, int nz, const double *d_face_vals,
                            double *d_coords, uint8_t *d_bc_flag, double *d_bc_val,
@@ -511,6 +515,45 @@ fe_status fe_inject_barrier_stall(int barrier_index);
 #define FE_RESID_WORK_BYTES (65536 + 64)
 fe_status fe_true_relres(const fe_matrix *A, const double *d_b, const double *d_x,
                          void *d_work, size_t work_bytes, double *h_relres, fe_stream_t stream);
+
+/*
+ * Matrix-free operator (an extension beside the paper's stored CRS/BCRS
+ * formats, Sec. 3.1): the same Dirichlet system as fe_assemble_csr on the
+ * nx x ny x nz box mesh, applied without a stored matrix.  The trilinear
+ * brick's stiffness is the Kronecker sum Lx(x)My(x)Mz + Mx(x)Ly(x)Mz +
+ * Mx(x)My(x)Lz of 1D linear-element mass and stiffness, and so is the
+ * assembled matrix; a row whose node is not on a face holds, at offset
+ * (dx, dy, dz) in {-1,0,1}^3,
+ *   a = Lx(dx) My(dy) Mz(dz) + Mx(dx) Ly(dy) Mz(dz) + Mx(dx) My(dy) Lz(dz),
+ *   M(0) = 2h/3, M(+-1) = h/6, L(0) = 2/h, L(+-1) = -1/h, h = 1/n per axis
+ * (on a cube: 8h/3 centre, 0 faces, -h/6 edges, -h/12 corners).  Rows of
+ * boundary nodes are identity rows; boundary columns are eliminated.  The
+ * values equal the element-integral ones up to rounding (the stored matrix
+ * also holds ~1e-18 quadrature residues where the exact value is 0).
+ * Node ids as fe_generate_mesh; m = (nx+1)(ny+1)(nz+1) may exceed the int32
+ * limit of the CSR form (indices are 64-bit).  Vectors are m doubles,
+ * 8-byte aligned; FE_ERR_ARG on bad sizes, null or aliased pointers.
+ *
+ * fe_stencil_spmv: d_y = A d_x (d_y must not alias d_x).
+ * fe_stencil_rhs:  d_b = the right-hand side of the eliminated system: the
+ *   prescribed value on boundary nodes, 0 - sum_j a_ij g_j over boundary
+ *   neighbours j elsewhere (zero source term).  d_bc_val: fe_generate_mesh's.
+ * fe_stencil_cg_solve: textbook CG on A x = b, stopping rule, status codes,
+ *   result and bounded barriers as fe_cg_solve; d_x holds the start vector.
+ *   d_work: fe_stencil_cg_workspace bytes (four m-vectors plus the reduction
+ *   block), 256-byte aligned.  Synchronises `stream`.
+ * fe_stencil_true_relres: ||b - A x|| / ||b|| (||b - A x|| if b = 0) with the
+ *   matrix-free A; d_work as fe_stencil_cg_solve (its contents are scratch).
+ */
+fe_status fe_stencil_spmv(int nx, int ny, int nz, const double *d_x, double *d_y, fe_stream_t stream);
+fe_status fe_stencil_rhs(int nx, int ny, int nz, const double *d_bc_val, double *d_b, fe_stream_t stream);
+fe_status fe_stencil_cg_workspace(int nx, int ny, int nz, size_t *h_bytes);
+fe_status fe_stencil_cg_solve(int nx, int ny, int nz, const double *d_b, double *d_x, double tol,
+                              int maxit, double timeout_s, void *d_work, size_t work_bytes,
+                              fe_cg_result *h_result, fe_stream_t stream);
+fe_status fe_stencil_true_relres(int nx, int ny, int nz, const double *d_b, const double *d_x,
+                                 void *d_work, size_t work_bytes, double *h_relres,
+                                 fe_stream_t stream);
 
 /* CUDA error code of the last FE_ERR_CUDA on this thread (0 if none). */
 int fe_last_cuda_error(void);

@@ -612,11 +612,9 @@ static int is_boundary_node(int nx, int ny, int nz, int ix, int iy, int iz)
     return ix == 0 || ix == nx || iy == 0 || iy == ny || iz == 0 || iz == nz;
 }
 
-/* (A x)_i of the Dirichlet system for one row i, matrix-free. */
-double orc_stencil_row(int nx, int ny, int nz, int64_t i, const double *x)
+/* (A x)_i for one row i with the stencil a of orc_stencil_coeffs. */
+static double stencil_row(int nx, int ny, int nz, const double a[27], int64_t i, const double *x)
 {
-    double a[27];
-    orc_stencil_coeffs(nx, ny, nz, a);
     int64_t sx = nx + 1, sxy = (int64_t)(nx + 1) * (ny + 1);
     int ix = (int)(i % sx), iy = (int)((i / sx) % (ny + 1)), iz = (int)(i / sxy);
     if (is_boundary_node(nx, ny, nz, ix, iy, iz))
@@ -633,12 +631,22 @@ double orc_stencil_row(int nx, int ny, int nz, int64_t i, const double *x)
     return s;
 }
 
+/* (A x)_i of the Dirichlet system for one row i, matrix-free. */
+double orc_stencil_row(int nx, int ny, int nz, int64_t i, const double *x)
+{
+    double a[27];
+    orc_stencil_coeffs(nx, ny, nz, a);
+    return stencil_row(nx, ny, nz, a, i, x);
+}
+
 /* y = A x over all rows, matrix-free. */
 void orc_stencil_spmv(int nx, int ny, int nz, const double *x, double *y)
 {
+    double a[27];
+    orc_stencil_coeffs(nx, ny, nz, a);
     int64_t m = orc_num_nodes(nx, ny, nz);
     for (int64_t i = 0; i < m; ++i)
-        y[i] = orc_stencil_row(nx, ny, nz, i, x);
+        y[i] = stencil_row(nx, ny, nz, a, i, x);
 }
 
 /* Right-hand side of the eliminated system, matrix-free: b_i = g_i on a     */

@@ -61,9 +61,11 @@ __global__ void k_mesh_nodes(int nx, int ny, int nz, const double *__restrict__ 
         const int64_t q = i / nxn;
         const int iy = (int)(q % nyn);
         const int iz = (int)(q / nyn);
-        coords[3 * i + 0] = (double)ix / (double)nx;
-        coords[3 * i + 1] = (double)iy / (double)ny;
-        coords[3 * i + 2] = (double)iz / (double)nz;
+        if (coords != nullptr) {
+            coords[3 * i + 0] = (double)ix / (double)nx;
+            coords[3 * i + 1] = (double)iy / (double)ny;
+            coords[3 * i + 2] = (double)iz / (double)nz;
+        }
         const bool bnd = ix == 0 || ix == nx || iy == 0 || iy == ny || iz == 0 || iz == nz;
         flag[i] = bnd ? 1 : 0;
         double g = 0.0;
@@ -141,9 +143,11 @@ fe_status fe_generate_mesh(int nx, int ny, int nz, const double *d_face_vals, do
                            fe_stream_t stream) {
     fe_sizes sz;
     fe_status st = fe_problem_sizes(nx, ny, nz, &sz);
+    // the CSR form's nnz limit does not bind the mesh; int32 node ids do
+    if (st == FE_ERR_OVERFLOW && (d_conn == nullptr || sz.n_rows <= INT32_MAX)) st = FE_OK;
     if (st != FE_OK) return st;
-    if (d_coords == nullptr || d_bc_flag == nullptr || d_bc_val == nullptr) return FE_ERR_ARG;
-    if (!aligned(d_coords, 8) || !aligned(d_bc_val, 8) || (d_face_vals && !aligned(d_face_vals, 8)))
+    if (d_bc_flag == nullptr || d_bc_val == nullptr) return FE_ERR_ARG;
+    if ((d_coords && !aligned(d_coords, 8)) || !aligned(d_bc_val, 8) || (d_face_vals && !aligned(d_face_vals, 8)))
         return FE_ERR_ARG;
     if (d_conn != nullptr && !aligned(d_conn, 16)) return FE_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;

@@ -101,6 +101,13 @@ SIGNATURES = {
                               ctypes.POINTER(fe_cg_result), _VP]),
     "fe_true_relres": (_I32, [ctypes.POINTER(fe_matrix), _VP, _VP, _VP, _SZ,
                               ctypes.POINTER(_D), _VP]),
+    "fe_stencil_spmv": (_I32, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, _VP, _VP]),
+    "fe_stencil_rhs": (_I32, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, _VP, _VP]),
+    "fe_stencil_cg_workspace": (_I32, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_SZ)]),
+    "fe_stencil_cg_solve": (_I32, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, _VP, _D, ctypes.c_int,
+                                   _D, _VP, _SZ, ctypes.POINTER(fe_cg_result), _VP]),
+    "fe_stencil_true_relres": (_I32, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, _VP, _VP, _SZ,
+                                      ctypes.POINTER(_D), _VP]),
     "fe_cg_mixed_workspace": (_I32, [ctypes.POINTER(fe_matrix), ctypes.POINTER(_SZ)]),
     "fe_cg_solve_mixed": (_I32, [ctypes.POINTER(fe_matrix), ctypes.POINTER(fe_matrix), _VP, _VP,
                                  _D, ctypes.c_int, ctypes.c_int, _D, ctypes.c_int, _D, _VP, _SZ,
@@ -328,6 +335,73 @@ def fe_true_relres(A: fe_matrix, b, x, work, stream=None) -> float:
         ctypes.byref(A), _ptr(b), _ptr(x), _ptr(work), work.numel() * work.element_size(),
         ctypes.byref(out), _stream(stream)))
     return out.value
+
+
+# ---------------------------------------------------------------- matrix-free form
+
+def fe_stencil_spmv(nx, ny, nz, x, y, stream=None):
+    return _check("fe_stencil_spmv", load().fe_stencil_spmv(nx, ny, nz, _ptr(x), _ptr(y), _stream(stream)))
+
+
+def fe_stencil_rhs(nx, ny, nz, bc_val, b, stream=None):
+    return _check("fe_stencil_rhs", load().fe_stencil_rhs(nx, ny, nz, _ptr(bc_val), _ptr(b), _stream(stream)))
+
+
+def fe_stencil_cg_workspace(nx, ny, nz) -> int:
+    n = ctypes.c_size_t(0)
+    _check("fe_stencil_cg_workspace", load().fe_stencil_cg_workspace(nx, ny, nz, ctypes.byref(n)))
+    return n.value
+
+
+def fe_stencil_cg_solve(nx, ny, nz, b, x, tol, maxit, work, timeout_s=0.0, stream=None,
+                        check=True) -> fe_cg_result:
+    res = fe_cg_result()
+    st = load().fe_stencil_cg_solve(nx, ny, nz, _ptr(b), _ptr(x), float(tol), int(maxit), float(timeout_s),
+                                    _ptr(work), work.numel() * work.element_size(), ctypes.byref(res),
+                                    _stream(stream))
+    if check and st != FE_OK:
+        raise FeError("fe_stencil_cg_solve", st)
+    return res
+
+
+def fe_stencil_true_relres(nx, ny, nz, b, x, work, stream=None) -> float:
+    out = ctypes.c_double(0.0)
+    _check("fe_stencil_true_relres", load().fe_stencil_true_relres(
+        nx, ny, nz, _ptr(b), _ptr(x), _ptr(work), work.numel() * work.element_size(), ctypes.byref(out),
+        _stream(stream)))
+    return out.value
+
+
+class StencilSystem:
+    """Matrix-free form of one nx x ny x nz problem: the mesh's boundary data,
+    the right-hand side and the CG workspace (no matrix, no coordinates)."""
+
+    def __init__(self, nx: int, ny: int | None = None, nz: int | None = None, device="cuda",
+                 face_vals: torch.Tensor | None = None):
+        ny = nx if ny is None else ny
+        nz = nx if nz is None else nz
+        self.dims = (nx, ny, nz)
+        self.device = torch.device(device)
+        self.m = (nx + 1) * (ny + 1) * (nz + 1)
+        self.bc_flag = torch.empty(self.m, dtype=torch.uint8, device=self.device)
+        self.bc_val = torch.empty(self.m, dtype=torch.float64, device=self.device)
+        self.b = torch.empty(self.m, dtype=torch.float64, device=self.device)
+        self.face_vals = face_vals
+        self.work = _alloc_bytes(fe_stencil_cg_workspace(*self.dims), self.device)
+
+    def build(self, stream=None):
+        fe_generate_mesh(*self.dims, self.face_vals, None, self.bc_flag, self.bc_val, None, stream)
+        fe_stencil_rhs(*self.dims, self.bc_val, self.b, stream)
+        return self
+
+    def spmv(self, x, y, stream=None):
+        fe_stencil_spmv(*self.dims, x, y, stream)
+
+    def solve(self, x, tol=1e-10, maxit=100000, timeout_s=0.0, stream=None, check=True) -> fe_cg_result:
+        return fe_stencil_cg_solve(*self.dims, self.b, x, tol, maxit, self.work, timeout_s, stream, check)
+
+    def true_relres(self, x, stream=None) -> float:
+        return fe_stencil_true_relres(*self.dims, self.b, x, self.work, stream)
 
 
 def fe_inject_barrier_stall(barrier_index: int):

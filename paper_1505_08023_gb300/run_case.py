@@ -7,8 +7,8 @@ Builds the N x N x N problem through the C ABI (mesh, assembly, conversion to
 CG for --cg-steps steps (tol 0, or to --tol when --cg-steps is 0), the
 single-reduction CG for --sr-steps steps, and the mixed-precision
 reliable-update solve for --mixed-steps FP32 steps; or, with --conv, one
-stride-1 convolution of the warm-start network (tensor-core and CUDA-core
-kernels); or, with --batch, the batched solver on a seeded batch of meshes.  With
+stride-1 convolution of the warm-start network (tensor-core kernels with
+TMA-staged BF16 input and with FP32 input, then the CUDA-core kernel); or, with --batch, the batched solver on a seeded batch of meshes.  With
 --drop-csr the CSR arrays are released after conversion (smaller footprint
 for profiler captures that save and restore device memory).  Prints one line
 per step taken.
@@ -101,8 +101,13 @@ def run_conv(cin: int, cout: int, n: int):
     if cout in fe.TC_COUT:
         img = fe.mma_image(cin, cout)
         fe.fe_nn_pack_weights_mma(w16, cin, cout, img)
+        x16 = fe.bf16i_buffer(cin, dims, "cuda")
+        fe.fe_nn_to_bf16i(x, cin, dims, x16)
+        fe.fe_nn_conv3d_tc_bf16i("s1", x16, cin, dims, img, b, y, cout, dims, 1)
+        print(f"tensor-core conv (TMA-staged BF16 input) {cin}->{cout} on {n}^3 done, "
+              f"wait flag {fe.fe_nn_tc_check()}")
         fe.fe_nn_conv3d_s1_tc(x, cin, dims, img, b, y, cout, 1)
-        print(f"tensor-core conv {cin}->{cout} on {n}^3 done, wait flag {fe.fe_nn_tc_check()}")
+        print(f"tensor-core conv (FP32 input) {cin}->{cout} on {n}^3 done, wait flag {fe.fe_nn_tc_check()}")
     fe.fe_nn_conv3d(fe.NN_MODES["s1"], x, cin, dims, w16, b, y, cout, dims, 1)
     torch.cuda.synchronize()
     print(f"CUDA-core conv {cin}->{cout} on {n}^3 done")
