@@ -19,16 +19,19 @@
 // Interior rows: a block of 8 warps owns a 32 x 8 (x, y) column of interior
 // nodes and marches along z through a range of planes.  Each plane is staged
 // in shared memory with a one-node halo (boundary and out-of-range nodes as
-// 0; double-buffered, one __syncthreads per plane, the next plane's loads in
-// flight while this one is used), and every thread forms the plane sums of
-// its node:  X (centre), Sx = x(-1) + x(+1), Sy = y(-1) + y(+1), D = the four
-// in-plane diagonal neighbours.  The row of plane z is
+// 0; double-buffered, the next plane's loads in flight while this one is
+// used), and every thread forms the plane sums of its node:  X (centre),
+// Sx = x(-1) + x(+1), Sy = y(-1) + y(+1), D = the four in-plane diagonal
+// neighbours, taken as Sx of the rows above and below (the staged rows' Sx go
+// through shared memory: one add per row instead of three).  The row of
+// plane z is
 //   y = c0 X + c1 Sx + c2 Sy + c3 D              (plane z)
 //     + Q(z-1) + Q(z+1),  Q = c4 X + c5 Sx + c6 Sy + c7 D   (planes z-1, z+1)
 // with Q carried in registers from plane to plane.  On a cube the face
 // classes vanish (c1 = c2 = c4 = 0) and the three edge classes agree, so
 //   y = c0 X + c3 D + P(z-1) + P(z+1),  P = c3 (Sx + Sy) + c7 D:
-// 11 FP64 operations per row where the stored matrix takes 27 FMAs.  The
+// 9.25 FP64 operations per row (Sx 1.25 with the halo rows, Sy 1, D 1, P 3,
+// the row 3) where the stored matrix takes 27 FMAs.  The
 // work (interior columns x interior planes) is cut into equal contiguous
 // ranges, one per block, so every block marches the same number of planes.
 // Boundary rows (y = x) are a separate row loop.
@@ -49,6 +52,7 @@ constexpr int kStY = kCgWarps;           // tile height along y: one row per war
 constexpr int kStPitch = kStX + 2;       // staged row with its halo
 constexpr int kStElems = kStPitch * (kStY + 2);
 static_assert(kStElems <= 2 * kCgThreads, "two staged elements per thread");
+constexpr int kStBuf = 2 * kStElems + (kStY + 2) * kStX;   // two staged planes + their row sums
 
 struct StencilGeom {
     int nx, ny, nz;          // elements per axis
@@ -99,7 +103,7 @@ __host__ __device__ inline long long bc_count(int nx, int ny, int nz) {
 // whose first owned node is (x0, y0); `ok` is false for boundary nodes (x or
 // y on a face) and nodes past the mesh, which are staged as 0.
 struct StageSlot {
-    long long off;   // node offset within a plane
+    int off;   // node offset within a plane ((nx+1)(ny+1) <= INT32_MAX, checked on the host)
     bool ok;
 };
 
@@ -108,7 +112,7 @@ __host__ __device__ inline StageSlot stage_slot(int nx, int ny, int x0, int y0, 
     const int ey = e / kStPitch, ex = e - ey * kStPitch;
     const int gx = x0 - 1 + ex, gy = y0 - 1 + ey;
     s.ok = e < kStElems && gx >= 1 && gx < nx && gy >= 1 && gy < ny;
-    s.off = s.ok ? gx + (long long)(nx + 1) * gy : 0;
+    s.off = s.ok ? gx + (nx + 1) * gy : 0;
     return s;
 }
 
@@ -122,10 +126,24 @@ struct StencilIO {
     double beta, alpha_old;
 };
 
+// Staging: every thread stages its own node (the tile's element (warp + 1,
+// lane + 1)), and threads 0 .. kStHalo-1 one halo node each: the rows above
+// and below the tile, then the two ends of each owned row.
+constexpr int kStHalo = 2 * kStPitch + 2 * kStY;
+static_assert(kStHalo <= kCgThreads, "one halo node per thread at most");
+
+__host__ __device__ inline int halo_elem(int h) {
+    if (h < kStPitch) return h;
+    if (h < 2 * kStPitch) return (kStY + 1) * kStPitch + (h - kStPitch);
+    const int k = h - 2 * kStPitch;
+    return (1 + (k >> 1)) * kStPitch + ((k & 1) ? kStPitch - 1 : 0);
+}
+
 // One column of interior rows, planes zlo .. zhi-1 (1-based interior
 // planes); returns the thread's partial of operand . (A operand).
 // FUSED: the operand is p = r + beta p_old (r alone on the first step), p is
-// stored and x takes its update for the owned rows.
+// stored and x takes its update for the owned rows; the thread's own p_old
+// and x values come with the plane loads, one plane ahead of their use.
 template <bool ISO, bool FUSED>
 __device__ __forceinline__ double stencil_column(const StencilGeom &g, const StencilIO &io, long long t,
                                                  int zlo, int zhi, double *buf) {
@@ -133,40 +151,52 @@ __device__ __forceinline__ double stencil_column(const StencilGeom &g, const Ste
     const int tx = (int)(t % g.ntx), ty = (int)(t / g.ntx);
     const int x0 = 1 + kStX * tx, y0 = 1 + kStY * ty;
     const long long sxy = (long long)(g.nx + 1) * (g.ny + 1);
-    const StageSlot s0 = stage_slot(g.nx, g.ny, x0, y0, threadIdx.x);
-    const StageSlot s1 = stage_slot(g.nx, g.ny, x0, y0, threadIdx.x + kCgThreads);
-    const bool has1 = threadIdx.x + kCgThreads < kStElems;
-    const int gx = x0 + lane, gy = y0 + warp;
-    const bool own = gx < g.nx && gy < g.ny;
-    const long long orow = gx + (long long)(g.nx + 1) * gy;
     const int c = (warp + 1) * kStPitch + lane + 1;
+    const bool has_h = threadIdx.x < kStHalo;
+    const int eh = has_h ? halo_elem(threadIdx.x) : 0;
+    const StageSlot s0 = stage_slot(g.nx, g.ny, x0, y0, c);
+    const StageSlot s1 = has_h ? stage_slot(g.nx, g.ny, x0, y0, eh) : StageSlot{0, false};
+    const bool own = s0.ok;            // the own node is interior (x0 + lane < nx, y0 + warp < ny)
     const bool upd = FUSED && io.pold != nullptr;
+    double *sxb = buf + 2 * kStElems;   // Sx of the staged rows
 
     // raw loads of one plane (operand, or r and p_old), combined when staged
     double ra0 = 0.0, ra1 = 0.0, pa0 = 0.0, pa1 = 0.0;
     auto fetch = [&](int q) {
         const bool zin = q >= 1 && q < g.nz;
         const long long b = sxy * q;
-        ra0 = (zin && s0.ok) ? io.in[s0.off + b] : 0.0;
-        ra1 = (zin && s1.ok) ? io.in[s1.off + b] : 0.0;
+        ra0 = (zin && s0.ok) ? io.in[b + s0.off] : 0.0;
+        ra1 = (zin && s1.ok) ? io.in[b + s1.off] : 0.0;
         if (upd) {
-            pa0 = (zin && s0.ok) ? io.pold[s0.off + b] : 0.0;
-            pa1 = (zin && s1.ok) ? io.pold[s1.off + b] : 0.0;
+            pa0 = (zin && s0.ok) ? io.pold[b + s0.off] : 0.0;
+            pa1 = (zin && s1.ok) ? io.pold[b + s1.off] : 0.0;
         }
     };
     fetch(zlo - 1);
     double Xm = 0.0, Sxm = 0.0, Sym = 0.0, Dm = 0.0, Qm1 = 0.0, Qm2 = 0.0, acc = 0.0;
+    double pm = 0.0, xm = 0.0;   // own p_old and x of plane q - 1 (CG pass)
     int par = 0;
     for (int q = zlo - 1; q <= zhi; ++q) {
         double *s = buf + par * kStElems;
-        s[threadIdx.x] = upd ? fma(io.beta, pa0, ra0) : ra0;
-        if (has1) s[threadIdx.x + kCgThreads] = upd ? fma(io.beta, pa1, ra1) : ra1;
+        const double X = upd ? fma(io.beta, pa0, ra0) : ra0;
+        const double pq = pa0;
+        s[c] = X;
+        if (has_h) s[eh] = upd ? fma(io.beta, pa1, ra1) : ra1;
         __syncthreads();
+        double xq = 0.0;
+        if (upd && own && q >= zlo && q < zhi) xq = io.x[sxy * q + s0.off];
         if (q < zhi) fetch(q + 1);
-        const double X = s[c];
+        // Sx of every staged row (the own row's in a register, all of them in
+        // shared memory): the diagonal sum D is Sx of the rows above and below
         const double Sx = s[c - 1] + s[c + 1];
+        sxb[(warp + 1) * kStX + lane] = Sx;
+        if (warp < 2) {
+            const int r = warp == 0 ? 0 : kStY + 1;
+            sxb[r * kStX + lane] = s[r * kStPitch + lane] + s[r * kStPitch + lane + 2];
+        }
+        __syncthreads();
         const double Sy = s[c - kStPitch] + s[c + kStPitch];
-        const double D = (s[c - kStPitch - 1] + s[c - kStPitch + 1]) + (s[c + kStPitch - 1] + s[c + kStPitch + 1]);
+        const double D = sxb[warp * kStX + lane] + sxb[(warp + 2) * kStX + lane];
         double Q;
         if constexpr (ISO) Q = fma(g.c[3], Sx + Sy, g.c[7] * D);
         else Q = fma(g.c[7], D, fma(g.c[6], Sy, fma(g.c[5], Sx, g.c[4] * X)));
@@ -175,11 +205,11 @@ __device__ __forceinline__ double stencil_column(const StencilGeom &g, const Ste
             if constexpr (ISO) yv = fma(g.c[0], Xm, fma(g.c[3], Dm, Qm2 + Q));
             else yv = fma(g.c[3], Dm, fma(g.c[2], Sym, fma(g.c[1], Sxm, fma(g.c[0], Xm, Qm2 + Q))));
             if (own) {
-                const long long i = orow + sxy * (q - 1);
+                const long long i = sxy * (q - 1) + s0.off;
                 io.out[i] = yv;
                 if constexpr (FUSED) {
                     io.pnew[i] = Xm;
-                    if (upd) io.x[i] = fma(io.alpha_old, io.pold[i], io.x[i]);
+                    if (upd) io.x[i] = fma(io.alpha_old, pm, xm);
                 }
                 acc = fma(Xm, yv, acc);
             }
@@ -188,6 +218,8 @@ __device__ __forceinline__ double stencil_column(const StencilGeom &g, const Ste
         Qm1 = Q;
         Xm = X;
         Dm = D;
+        pm = pq;
+        xm = xq;
         if constexpr (!ISO) {
             Sxm = Sx;
             Sym = Sy;
@@ -252,7 +284,7 @@ __device__ __forceinline__ double stencil_pass(const StencilGeom &g, const Stenc
 
 template <bool ISO>
 __global__ void __launch_bounds__(kCgThreads, 3) k_stencil_spmv(const StencilGeom g, const double *x, double *y) {
-    __shared__ double buf[2 * kStElems];
+    __shared__ double buf[kStBuf];
     StencilIO io{x, nullptr, nullptr, nullptr, y, 0.0, 0.0};
     (void)stencil_pass<ISO, false>(g, io, buf);
 }
@@ -302,7 +334,7 @@ struct StencilCgArgs {
 template <bool ISO>
 __global__ void __launch_bounds__(kCgThreads, 3) k_cg_stencil(const StencilCgArgs a) {
     __shared__ CgBlockState st;
-    __shared__ double buf[2 * kStElems];
+    __shared__ double buf[kStBuf];
     const long long m = a.g.m;
     const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long nth = (long long)gridDim.x * blockDim.x;
@@ -337,9 +369,12 @@ __global__ void __launch_bounds__(kCgThreads, 3) k_cg_stencil(const StencilCgArg
         }
         __syncthreads();
     }
-    double *pcur = a.p0, *pold = a.p1;   // pcur: the p this step writes
-    double alpha_old = 0.0, beta = 0.0;
-    bool pending = false;                // x still lacks alpha_old p_old (p_old = the last p written)
+    // Step k writes p into p0 (k even) or p1 (k odd) and reads the other one
+    // as p_old.  alpha_old and beta live in shared memory, so that only
+    // status flags stay in registers across the operator pass.
+    __shared__ double coef[2];           // alpha_old, beta
+    if (threadIdx.x == 0) coef[0] = coef[1] = 0.0;
+    __syncthreads();
     if (alive && st.bb == 0.0) {         // b = 0: the solution is 0
         for (long long i = tid; i < m; i += nth) a.x[i] = 0.0;
         if (threadIdx.x == 0) st.rr = 0.0;
@@ -349,24 +384,23 @@ __global__ void __launch_bounds__(kCgThreads, 3) k_cg_stencil(const StencilCgArg
             if (st.rr <= a.tol2 * st.bb) { status = FE_OK; break; }
             if (st.k >= a.maxit) { status = FE_ERR_MAXIT; break; }
             // A: p = r + beta p_old, x += alpha_old p_old, w = A p, p.w
-            StencilIO io{a.r, st.k > 0 ? pold : nullptr, pcur, a.x, a.w, beta, alpha_old};
+            const int k = st.k;
+            double *pcur = (k & 1) ? a.p1 : a.p0;
+            const double *pold = k > 0 ? ((k & 1) ? a.p0 : a.p1) : nullptr;
+            const StencilIO io{a.r, pold, pcur, a.x, a.w, coef[1], coef[0]};
             const double pw_part = stencil_pass<ISO, true>(a.g, io, buf);
             double pw, unused;
             if (!(alive = grid_sum2(a, &st, pw_part, 0.0, pw, unused))) break;
             if (!(pw > 0.0) || !(pw < INFINITY)) { status = FE_ERR_BREAKDOWN; break; }
             // B: r -= alpha w, r.r
             const double alpha = st.rr / pw;
-            const double rr_part = update_r<double>(a.r, a.w, m, alpha);
+            const double rr_part = update_r<double>(a.r, a.w, a.g.m, alpha);
             double rr_new;
             if (!(alive = grid_sum2(a, &st, rr_part, 0.0, rr_new, unused))) break;
-            beta = rr_new / st.rr;
-            alpha_old = alpha;
-            pending = true;
-            double *t = pold;
-            pold = pcur;
-            pcur = t;
-            __syncthreads();   // every thread has read st.rr
+            __syncthreads();   // every thread has read st.rr and coef
             if (threadIdx.x == 0) {
+                coef[0] = alpha;
+                coef[1] = rr_new / st.rr;
                 st.rr = rr_new;
                 st.k += 1;
             }
@@ -375,9 +409,12 @@ __global__ void __launch_bounds__(kCgThreads, 3) k_cg_stencil(const StencilCgArg
             if (st.k >= a.maxit) { status = FE_ERR_MAXIT; break; }
         }
     }
-    // the last x update, row by row
-    if (alive && pending && (status == FE_OK || status == FE_ERR_MAXIT))
-        for (long long i = tid; i < m; i += nth) a.x[i] = fma(alpha_old, pold[i], a.x[i]);
+    // the last x update (x lacks alpha_old p of the last step taken), row by row
+    if (alive && st.k > 0 && (status == FE_OK || status == FE_ERR_MAXIT)) {
+        const double *plast = (st.k & 1) ? a.p0 : a.p1;   // written by step k - 1
+        const double al = coef[0];
+        for (long long i = tid; i < m; i += nth) a.x[i] = fma(al, plast[i], a.x[i]);
+    }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         a.ctrl->status = alive ? status : FE_ERR_TIMEOUT;
         a.ctrl->iterations = st.k;
@@ -390,6 +427,7 @@ __global__ void __launch_bounds__(kCgThreads, 3) k_cg_stencil(const StencilCgArg
 
 static bool stencil_geom(int nx, int ny, int nz, StencilGeom *g) {
     if (nx < 1 || ny < 1 || nz < 1) return false;
+    if ((long long)(nx + 1) * (ny + 1) > INT32_MAX) return false;   // plane offsets are int32
     g->nx = nx;
     g->ny = ny;
     g->nz = nz;

@@ -6,7 +6,8 @@ Builds the N x N x N problem through the C ABI (mesh, assembly, conversion to
 --format), then runs, as asked: one stand-alone SpMV (--spmv), the fused FP64
 CG for --cg-steps steps (tol 0, or to --tol when --cg-steps is 0), the
 single-reduction CG for --sr-steps steps, and the mixed-precision
-reliable-update solve for --mixed-steps FP32 steps; or, with --conv, one
+reliable-update solve for --mixed-steps FP32 steps; or, with
+--stencil-steps, the matrix-free operator and CG; or, with --conv, one
 stride-1 convolution of the warm-start network (tensor-core kernels with
 TMA-staged BF16 input and with FP32 input, then the CUDA-core kernel); or, with --batch, the batched solver on a seeded batch of meshes.  With
 --drop-csr the CSR arrays are released after conversion (smaller footprint
@@ -40,7 +41,13 @@ def main():
     ap.add_argument("--conv", type=int, nargs=3, metavar=("CIN", "COUT", "N"), default=None,
                     help="instead of the solver: one stride-1 conv of the warm-start network on an "
                          "N^3 grid, tensor-core kernel then CUDA-core kernel")
+    ap.add_argument("--stencil-steps", type=int, default=None,
+                    help="instead of the stored matrix: the matrix-free operator once, then this many "
+                         "matrix-free CG steps (tol 0; 0: solve to --tol)")
     a = ap.parse_args()
+    if a.stencil_steps is not None:
+        run_stencil(a.n, a.stencil_steps, a.tol)
+        return
     if a.conv is not None:
         run_conv(*a.conv)
         return
@@ -87,6 +94,17 @@ def run_batch(count: int, lo: int, hi: int, fmt: str, steps: int):
     st, res = fe.fe_cg_batched_results(plan)
     print(f"batched: {count} meshes, {sum((n + 1) ** 3 for n in sizes):,} rows, {steps} steps, "
           f"statuses {sorted(set(r.status for r in res))}")
+
+
+def run_stencil(n: int, steps: int, tol: float):
+    st = fe.StencilSystem(n).build()
+    x = torch.zeros(st.m, dtype=torch.float64, device="cuda")
+    y = torch.empty_like(x)
+    st.spmv(st.b, y)
+    print("matrix-free spmv done")
+    tol, steps = (0.0, steps) if steps > 0 else (tol, 100000)
+    r = st.solve(x, tol, steps, check=False)
+    print(f"matrix-free cg: status {r.status} steps {r.iterations} relres {r.relres:.3e}")
 
 
 def run_conv(cin: int, cout: int, n: int):
