@@ -265,6 +265,16 @@ def run_reference(args, rank: int, world: int):
     print(json.dumps(line), flush=True)
 
 
+def max_over_ranks(values, device):
+    """Element-wise maximum of `values` over the ranks of the default process
+    group (the slowest replica sets every time in the line)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t]
+
+
 def config_dict(args):
     n = args.n
     m = (n + 1) ** 3
@@ -284,7 +294,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--n", "--elements", dest="n", type=int, default=256,
+                    help="elements per axis (--elements: the same, a name torchrun does not take for its own)")
     ap.add_argument("--format", choices=["csr", "sell", "bcrs3"], default="bcrs3")
     ap.add_argument("--cpu-iters", type=int, default=8, help="oracle CG iterations in the CPU sample")
     ap.add_argument("--cpu-parallel-iters", type=int, default=40,
@@ -374,9 +385,7 @@ def main():
     cg_ms = statistics.mean(phases["cg"])
     step_ms = statistics.mean(phases["step"])
     if world > 1:
-        t = torch.tensor([cg_ms, step_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        cg_ms, step_ms = float(t[0]), float(t[1])
+        cg_ms, step_ms = max_over_ranks([cg_ms, step_ms], dev)
 
     A = state["A"]
     it = statistics.mean(iters)
