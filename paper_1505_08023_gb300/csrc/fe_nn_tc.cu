@@ -533,12 +533,18 @@ static fe_status launch_tc(const float *d_in, const void *d_in16, int cin, const
     if (smem > (size_t)232448) smem = 232448;
     auto kern = k_conv_tc<MODE, TMA>;
     FE_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FE_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     (int)cudaSharedmemCarveoutMaxShared));
     int per_sm = 0;
     FE_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTcThreads, smem));
     if (per_sm < 1) return FE_ERR_CUDA;
     if (per_sm > g.ctas_per_sm) return FE_ERR_CUDA;       // tensor memory would be oversubscribed
     const long long ntiles = (long long)tdims[0] * ((tdims[1] + g.ty - 1) / g.ty);
-    long long grid = (long long)sm_count() * per_sm;
+    // ctas_per_sm blocks per SM (shared and tensor memory admit them; the
+    // occupancy query answers 1 for this kernel although the SM holds 2): a
+    // second CTA's staging and MMAs overlap the first's epilogue.  The tiles
+    // are independent, so blocks that do not fit simply run later.
+    long long grid = (long long)sm_count() * g.ctas_per_sm;
     if (grid > ntiles) grid = ntiles;
     TcDims dm{h_dims[0], h_dims[1], h_dims[2]};
     TcDims dout{h_dims_out[0], h_dims_out[1], h_dims_out[2]};
