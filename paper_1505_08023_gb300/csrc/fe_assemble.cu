@@ -5,7 +5,9 @@
 // the CRS arrays inside an OpenMP critical section.  Here
 //   1. k_element_matrices: one thread per element computes its 8x8 matrix by
 //      2x2x2 Gauss quadrature from the node coordinates and stores the 36
-//      entries of the upper triangle (SoA, coalesced) in the workspace;
+//      entries of the upper triangle (SoA, coalesced) in the workspace; a
+//      parallelepiped (constant Jacobian) takes the same quadrature with the
+//      sum over the points done ahead of time (216 FMAs instead of ~2,000);
 //   2. k_assemble_rows: one thread per node gathers the rows of its (up to 8)
 //      incident elements in element-id order, so each entry is summed in a
 //      fixed order with no atomics, applies the Dirichlet elimination, and
@@ -81,6 +83,53 @@ __host__ __device__ constexpr int edge_corner(int j, int k, int e) {
     return j == 0 ? corner_of(e, c1, c2) : (j == 1 ? corner_of(c1, e, c2) : corner_of(c1, c2, e));
 }
 
+// For an element whose four edges along each axis are equal (a
+// parallelepiped: the trilinear map is affine and its Jacobian constant), the
+// quadrature sum K_ab = sum_q grad N_a(q) . grad N_b(q) det J factors as
+// K_ab = sum_{j,l} C_jl S^{jl}_ab with the constant metric C = det J J^-1 J^-T
+// and S^{jl}_ab = sum_q d_j N_a(q) d_l N_b(q), the same reference-gradient
+// products summed over the eight points ahead of time.  Six symmetric pairs
+// (j,l) = (0,0) (1,1) (2,2) (0,1) (0,2) (1,2); an off-diagonal pair holds
+// both orders, since C_jl = C_lj.
+struct AffineTable {
+    double s[6][36];  // [pair][packed upper-triangle entry]
+};
+__host__ __device__ constexpr AffineTable make_affine_table() {
+    AffineTable t{};
+    constexpr int pj[6] = {0, 1, 2, 0, 0, 1}, pl[6] = {0, 1, 2, 1, 2, 2};
+    for (int p = 0; p < 6; ++p)
+        for (int a = 0; a < 8; ++a)
+            for (int b = a; b < 8; ++b) {
+                double v = 0.0;
+                for (int q = 0; q < 8; ++q) {
+                    v += ref_grad(q, a, pj[p]) * ref_grad(q, b, pl[p]);
+                    if (pj[p] != pl[p]) v += ref_grad(q, a, pl[p]) * ref_grad(q, b, pj[p]);
+                }
+                t.s[p][tri_index(a, b)] = v;
+            }
+    return t;
+}
+__constant__ AffineTable kAffine = make_affine_table();
+
+// J^-1 (as the transposed cofactor matrix over det) and det J
+__device__ __forceinline__ double jac_inverse(const double J[3][3], double Ji[3][3]) {
+    const double c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+    const double c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+    const double c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+    const double det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
+    const double rdet = 1.0 / det;
+    Ji[0][0] = c00 * rdet;
+    Ji[1][0] = c01 * rdet;
+    Ji[2][0] = c02 * rdet;
+    Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) * rdet;
+    Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) * rdet;
+    Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) * rdet;
+    Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) * rdet;
+    Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) * rdet;
+    Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) * rdet;
+    return det;
+}
+
 __global__ void __launch_bounds__(128)
 k_element_matrices(int nx, int ny, int nz, const double *__restrict__ coords,
                    double *__restrict__ work) {
@@ -115,6 +164,44 @@ k_element_matrices(int nx, int ny, int nz, const double *__restrict__ coords,
 #pragma unroll
                 for (int i = 0; i < 3; ++i) E[j][k][i] = X[edge_corner(j, k, 1)][i] - X[edge_corner(j, k, 0)][i];
         double K[36];
+        // parallelepiped: the four edges along each axis agree bit for bit
+        bool affine = true;
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int k = 1; k < 4; ++k)
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+                    affine = affine && __double_as_longlong(E[j][k][i]) == __double_as_longlong(E[j][0][i]);
+        if (affine) {
+            // constant Jacobian d x_i / d xi_j = E_j / 2 (reference cell [-1, 1]^3)
+            double J[3][3], Ji[3][3];
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int j = 0; j < 3; ++j) J[i][j] = 0.5 * E[j][0][i];
+            const double det = jac_inverse(J, Ji);
+            // C_jl = det sum_i Ji[j][i] Ji[l][i], pairs in the table's order
+            constexpr int pj[6] = {0, 1, 2, 0, 0, 1}, pl[6] = {0, 1, 2, 1, 2, 2};
+            double C[6];
+#pragma unroll
+            for (int p = 0; p < 6; ++p) {
+                double c = Ji[pj[p]][0] * Ji[pl[p]][0];
+                c = fma(Ji[pj[p]][1], Ji[pl[p]][1], c);
+                c = fma(Ji[pj[p]][2], Ji[pl[p]][2], c);
+                C[p] = det * c;
+            }
+#pragma unroll
+            for (int k = 0; k < 36; ++k) {
+                double v = C[0] * kAffine.s[0][k];
+#pragma unroll
+                for (int p = 1; p < 6; ++p) v = fma(C[p], kAffine.s[p][k], v);
+                K[k] = v;
+            }
+#pragma unroll
+            for (int k = 0; k < 36; ++k) work[k * ne + e] = K[k];
+            continue;
+        }
 #pragma unroll
         for (int k = 0; k < 36; ++k) K[k] = 0.0;
 
@@ -131,22 +218,8 @@ k_element_matrices(int nx, int ny, int nz, const double *__restrict__ coords,
                     for (int k = 0; k < 4; ++k) s = fma(E[j][k][i], kEdgeW.w[q][j][k], s);
                     J[i][j] = s;
                 }
-            const double c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
-            const double c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
-            const double c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
-            const double det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
-            const double rdet = 1.0 / det;
-            // Jinv[i][j] = cofactor(J)[j][i] / det
             double Ji[3][3];
-            Ji[0][0] = c00 * rdet;
-            Ji[1][0] = c01 * rdet;
-            Ji[2][0] = c02 * rdet;
-            Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) * rdet;
-            Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) * rdet;
-            Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) * rdet;
-            Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) * rdet;
-            Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) * rdet;
-            Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) * rdet;
+            const double det = jac_inverse(J, Ji);
             // physical gradients G[a] = J^{-T} grad_xi N_a; weight 1 at every point
             double G[8][3];
 #pragma unroll

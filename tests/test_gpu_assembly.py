@@ -2,7 +2,10 @@
 CPU oracle, through the C ABI.
 
 Bars: coordinates, boundary data, row pointer and columns bit-exact; matrix
-values and right-hand side within 1e-14 of the row's largest |a_ij| (each
+values and right-hand side within 1e-14 of the row's largest |a_ij|, on box
+meshes (parallelepipeds: the constant-Jacobian path), sheared meshes of
+exact binary coordinates (the same path with a full Jacobian) and meshes with
+moved interior nodes (the per-point quadrature path) (each
 entry sums <= 8 element contributions, each a Gauss sum of O(100) roundings,
 so about 45 ulp of the row scale; entries that are zero in exact arithmetic
 come out near 1e-18 and are covered by the row scale).
@@ -87,6 +90,48 @@ def test_face_data_assembly(fe, dims):
     ref = oracle.build_system(*dims, face)
     assert row_scaled_close(ref["row_ptr"], ref["vals"], host(s.vals)) <= VAL_TOL
     assert np.abs(host(s.b) - ref["b"]).max() <= VAL_TOL * max(np.abs(ref["b"]).max(), 1.0)
+
+
+def _assemble_with_coords(fe, dims, X):
+    """GPU assembly from the given node coordinates, and the oracle's."""
+    s = fe.System(*dims)
+    s.generate_mesh()
+    s.coords.copy_(torch.from_numpy(X))
+    s.assemble()
+    _, flag, val = oracle.mesh(*dims)
+    row_ptr, cols = oracle.pattern(*dims)
+    vals, b = oracle.assemble(*dims, X, row_ptr, cols)
+    oracle.dirichlet(flag, val, row_ptr, cols, vals, b)
+    return s, row_ptr, vals, b
+
+
+@pytest.mark.parametrize("dims", [(5, 4, 3), (12, 9, 7)])
+def test_assembly_of_distorted_elements(fe, dims):
+    """Interior nodes moved at random: trilinear elements with a varying
+    Jacobian (the per-point quadrature path of the element kernel)."""
+    coords, flag, _ = oracle.mesh(*dims)
+    rng = np.random.default_rng(7)
+    X = coords.copy()
+    inner = ~flag.astype(bool)
+    X[inner] += (0.2 / max(dims)) * rng.uniform(-1.0, 1.0, (int(inner.sum()), 3))
+    s, row_ptr, vals, b = _assemble_with_coords(fe, dims, X)
+    assert row_scaled_close(row_ptr, vals, host(s.vals)) <= VAL_TOL
+    assert np.abs(host(s.b) - b).max() <= VAL_TOL * max(np.abs(b).max(), 1.0)
+
+
+def test_assembly_of_sheared_parallelepipeds(fe):
+    """A sheared mesh whose coordinates are exact binary fractions, so every
+    element is a parallelepiped bit for bit (the constant-Jacobian path with
+    a full, non-diagonal Jacobian)."""
+    dims = (8, 8, 8)
+    coords, _, _ = oracle.mesh(*dims)
+    X = coords.copy()
+    X[:, 0] = coords[:, 0] + 0.5 * coords[:, 1] + 0.25 * coords[:, 2]
+    X[:, 1] = coords[:, 1] + 0.5 * coords[:, 2]
+    X[:, 2] = 0.75 * coords[:, 2]
+    s, row_ptr, vals, b = _assemble_with_coords(fe, dims, X)
+    assert row_scaled_close(row_ptr, vals, host(s.vals)) <= VAL_TOL
+    assert np.abs(host(s.b) - b).max() <= VAL_TOL * max(np.abs(b).max(), 1.0)
 
 
 def test_rerun_is_bitwise_identical(fe):
