@@ -16,22 +16,23 @@
 // 4|dz|.  Boundary rows are identity rows and boundary columns are
 // eliminated (their values read as 0), as in the assembled system.
 //
-// Interior rows: a block of 8 warps owns a 32 x 8 (x, y) column of interior
-// nodes and marches along z through a range of planes.  Each plane is staged
-// in shared memory with a one-node halo (boundary and out-of-range nodes as
-// 0; double-buffered, the next plane's loads in flight while this one is
-// used), and every thread forms the plane sums of its node:  X (centre),
-// Sx = x(-1) + x(+1), Sy = y(-1) + y(+1), D = the four in-plane diagonal
-// neighbours, taken as Sx of the rows above and below (the staged rows' Sx go
-// through shared memory: one add per row instead of three).  The row of
-// plane z is
+// Interior rows: a block of 8 warps owns a 32 x 16 (x, y) column of interior
+// nodes (two rows per warp) and marches along z through a range of planes.
+// Each plane is staged in shared memory with a one-node halo (boundary and
+// out-of-range nodes as 0; double-buffered, the next plane's loads in flight
+// while this one is used), and every thread forms the plane sums of its two
+// nodes:  X (centre), Sx = x(-1) + x(+1), Sy = y(-1) + y(+1), D = the four
+// in-plane diagonal neighbours, taken as Sx of the rows above and below (the
+// staged rows' Sx go through shared memory: one add per row instead of
+// three; a thread's two rows take each other's X and Sx from registers).
+// The row of plane z is
 //   y = c0 X + c1 Sx + c2 Sy + c3 D              (plane z)
 //     + Q(z-1) + Q(z+1),  Q = c4 X + c5 Sx + c6 Sy + c7 D   (planes z-1, z+1)
 // with Q carried in registers from plane to plane.  On a cube the face
 // classes vanish (c1 = c2 = c4 = 0) and the three edge classes agree, so
 //   y = c0 X + c3 D + P(z-1) + P(z+1),  P = c3 (Sx + Sy) + c7 D:
-// 9.25 FP64 operations per row (Sx 1.25 with the halo rows, Sy 1, D 1, P 3,
-// the row 3) where the stored matrix takes 27 FMAs.  The
+// 9.125 FP64 operations per row (Sx 1.125 with the halo rows, Sy 1, D 1,
+// P 3, the row 3) where the stored matrix takes 27 FMAs.  The
 // work (interior columns x interior planes) is cut into equal contiguous
 // ranges, one per block, so every block marches the same number of planes.
 // Boundary rows (y = x) are a separate row loop.
@@ -48,10 +49,10 @@
 namespace fe {
 
 constexpr int kStX = 32;                 // tile width along x: one warp
-constexpr int kStY = kCgWarps;           // tile height along y: one row per warp
+constexpr int kStR = 2;                  // rows per warp
+constexpr int kStY = kCgWarps * kStR;    // tile height along y
 constexpr int kStPitch = kStX + 2;       // staged row with its halo
 constexpr int kStElems = kStPitch * (kStY + 2);
-static_assert(kStElems <= 2 * kCgThreads, "two staged elements per thread");
 constexpr int kStBuf = 2 * kStElems + (kStY + 2) * kStX;   // two staged planes + their row sums
 
 struct StencilGeom {
@@ -126,9 +127,9 @@ struct StencilIO {
     double beta, alpha_old;
 };
 
-// Staging: every thread stages its own node (the tile's element (warp + 1,
-// lane + 1)), and threads 0 .. kStHalo-1 one halo node each: the rows above
-// and below the tile, then the two ends of each owned row.
+// Staging: every thread stages its own kStR nodes (the tile's elements
+// (kStR warp + r + 1, lane + 1)), and threads 0 .. kStHalo-1 one halo node
+// each: the rows above and below the tile, then the two ends of each owned row.
 constexpr int kStHalo = 2 * kStPitch + 2 * kStY;
 static_assert(kStHalo <= kCgThreads, "one halo node per thread at most");
 
@@ -144,6 +145,8 @@ __host__ __device__ inline int halo_elem(int h) {
 // FUSED: the operand is p = r + beta p_old (r alone on the first step), p is
 // stored and x takes its update for the owned rows; the thread's own p_old
 // and x values come with the plane loads, one plane ahead of their use.
+// A thread owns kStR = 2 vertically adjacent rows: each one's row sum Sx and
+// centre value serve the other's D and Sy from registers.
 template <bool ISO, bool FUSED>
 __device__ __forceinline__ double stencil_column(const StencilGeom &g, const StencilIO &io, long long t,
                                                  int zlo, int zhi, double *buf) {
@@ -151,78 +154,97 @@ __device__ __forceinline__ double stencil_column(const StencilGeom &g, const Ste
     const int tx = (int)(t % g.ntx), ty = (int)(t / g.ntx);
     const int x0 = 1 + kStX * tx, y0 = 1 + kStY * ty;
     const long long sxy = (long long)(g.nx + 1) * (g.ny + 1);
-    const int c = (warp + 1) * kStPitch + lane + 1;
+    const int sr0 = kStR * warp + 1;                  // staged row of the first own node
+    const int c0 = sr0 * kStPitch + lane + 1, c1 = c0 + kStPitch;
     const bool has_h = threadIdx.x < kStHalo;
     const int eh = has_h ? halo_elem(threadIdx.x) : 0;
-    const StageSlot s0 = stage_slot(g.nx, g.ny, x0, y0, c);
-    const StageSlot s1 = has_h ? stage_slot(g.nx, g.ny, x0, y0, eh) : StageSlot{0, false};
-    const bool own = s0.ok;            // the own node is interior (x0 + lane < nx, y0 + warp < ny)
+    const StageSlot s0 = stage_slot(g.nx, g.ny, x0, y0, c0);
+    const StageSlot s1 = stage_slot(g.nx, g.ny, x0, y0, c1);
+    const StageSlot sh = has_h ? stage_slot(g.nx, g.ny, x0, y0, eh) : StageSlot{0, false};
     const bool upd = FUSED && io.pold != nullptr;
     double *sxb = buf + 2 * kStElems;   // Sx of the staged rows
 
     // raw loads of one plane (operand, or r and p_old), combined when staged
-    double ra0 = 0.0, ra1 = 0.0, pa0 = 0.0, pa1 = 0.0;
+    double ra0 = 0.0, ra1 = 0.0, rh = 0.0, pa0 = 0.0, pa1 = 0.0, ph = 0.0;
     auto fetch = [&](int q) {
         const bool zin = q >= 1 && q < g.nz;
         const long long b = sxy * q;
         ra0 = (zin && s0.ok) ? io.in[b + s0.off] : 0.0;
         ra1 = (zin && s1.ok) ? io.in[b + s1.off] : 0.0;
+        rh = (zin && sh.ok) ? io.in[b + sh.off] : 0.0;
         if (upd) {
             pa0 = (zin && s0.ok) ? io.pold[b + s0.off] : 0.0;
             pa1 = (zin && s1.ok) ? io.pold[b + s1.off] : 0.0;
+            ph = (zin && sh.ok) ? io.pold[b + sh.off] : 0.0;
         }
     };
+    // the row of plane q - 1 from the plane sums of q - 1 and the carried Q's
+    auto row_out = [&](const StageSlot &so, int q, double Xm, double Sxm, double Sym, double Dm, double Qm2,
+                       double Q, double pm, double xm, double &acc) {
+        double yv;
+        if constexpr (ISO) yv = fma(g.c[0], Xm, fma(g.c[3], Dm, Qm2 + Q));
+        else yv = fma(g.c[3], Dm, fma(g.c[2], Sym, fma(g.c[1], Sxm, fma(g.c[0], Xm, Qm2 + Q))));
+        if (so.ok) {
+            const long long i = sxy * (q - 1) + so.off;
+            io.out[i] = yv;
+            if constexpr (FUSED) {
+                io.pnew[i] = Xm;
+                if (upd) io.x[i] = fma(io.alpha_old, pm, xm);
+            }
+            acc = fma(Xm, yv, acc);
+        }
+    };
+    auto plane_q = [&](double X, double Sx, double Sy, double D) -> double {
+        if constexpr (ISO) return fma(g.c[3], Sx + Sy, g.c[7] * D);
+        else return fma(g.c[7], D, fma(g.c[6], Sy, fma(g.c[5], Sx, g.c[4] * X)));
+    };
     fetch(zlo - 1);
-    double Xm = 0.0, Sxm = 0.0, Sym = 0.0, Dm = 0.0, Qm1 = 0.0, Qm2 = 0.0, acc = 0.0;
-    double pm = 0.0, xm = 0.0;   // own p_old and x of plane q - 1 (CG pass)
+    // per own row: centre, row sums and carried Q of plane q - 1 (and q - 2)
+    double Xm0 = 0.0, Sxm0 = 0.0, Sym0 = 0.0, Dm0 = 0.0, Qa0 = 0.0, Qb0 = 0.0, pm0 = 0.0, xm0 = 0.0;
+    double Xm1 = 0.0, Sxm1 = 0.0, Sym1 = 0.0, Dm1 = 0.0, Qa1 = 0.0, Qb1 = 0.0, pm1 = 0.0, xm1 = 0.0;
+    double acc = 0.0;
     int par = 0;
     for (int q = zlo - 1; q <= zhi; ++q) {
         double *s = buf + par * kStElems;
-        const double X = upd ? fma(io.beta, pa0, ra0) : ra0;
-        const double pq = pa0;
-        s[c] = X;
-        if (has_h) s[eh] = upd ? fma(io.beta, pa1, ra1) : ra1;
+        const double X0 = upd ? fma(io.beta, pa0, ra0) : ra0;
+        const double X1 = upd ? fma(io.beta, pa1, ra1) : ra1;
+        const double pq0 = pa0, pq1 = pa1;
+        s[c0] = X0;
+        s[c1] = X1;
+        if (has_h) s[eh] = upd ? fma(io.beta, ph, rh) : rh;
         __syncthreads();
-        double xq = 0.0;
-        if (upd && own && q >= zlo && q < zhi) xq = io.x[sxy * q + s0.off];
+        double xq0 = 0.0, xq1 = 0.0;
+        if (upd && q >= zlo && q < zhi) {
+            if (s0.ok) xq0 = io.x[sxy * q + s0.off];
+            if (s1.ok) xq1 = io.x[sxy * q + s1.off];
+        }
         if (q < zhi) fetch(q + 1);
-        // Sx of every staged row (the own row's in a register, all of them in
-        // shared memory): the diagonal sum D is Sx of the rows above and below
-        const double Sx = s[c - 1] + s[c + 1];
-        sxb[(warp + 1) * kStX + lane] = Sx;
+        // Sx of every staged row (the own rows' in registers, all of them in
+        // shared memory): D is Sx of the rows above and below
+        const double Sx0 = s[c0 - 1] + s[c0 + 1];
+        const double Sx1 = s[c1 - 1] + s[c1 + 1];
+        sxb[sr0 * kStX + lane] = Sx0;
+        sxb[(sr0 + 1) * kStX + lane] = Sx1;
         if (warp < 2) {
             const int r = warp == 0 ? 0 : kStY + 1;
             sxb[r * kStX + lane] = s[r * kStPitch + lane] + s[r * kStPitch + lane + 2];
         }
         __syncthreads();
-        const double Sy = s[c - kStPitch] + s[c + kStPitch];
-        const double D = sxb[warp * kStX + lane] + sxb[(warp + 2) * kStX + lane];
-        double Q;
-        if constexpr (ISO) Q = fma(g.c[3], Sx + Sy, g.c[7] * D);
-        else Q = fma(g.c[7], D, fma(g.c[6], Sy, fma(g.c[5], Sx, g.c[4] * X)));
-        if (q > zlo) {  // the row of plane q - 1
-            double yv;
-            if constexpr (ISO) yv = fma(g.c[0], Xm, fma(g.c[3], Dm, Qm2 + Q));
-            else yv = fma(g.c[3], Dm, fma(g.c[2], Sym, fma(g.c[1], Sxm, fma(g.c[0], Xm, Qm2 + Q))));
-            if (own) {
-                const long long i = sxy * (q - 1) + s0.off;
-                io.out[i] = yv;
-                if constexpr (FUSED) {
-                    io.pnew[i] = Xm;
-                    if (upd) io.x[i] = fma(io.alpha_old, pm, xm);
-                }
-                acc = fma(Xm, yv, acc);
-            }
+        const double D0 = sxb[(sr0 - 1) * kStX + lane] + Sx1;
+        const double D1 = Sx0 + sxb[(sr0 + 2) * kStX + lane];
+        const double Sy0 = s[c0 - kStPitch] + X1;
+        const double Sy1 = X0 + s[c1 + kStPitch];
+        const double Q0 = plane_q(X0, Sx0, Sy0, D0);
+        const double Q1 = plane_q(X1, Sx1, Sy1, D1);
+        if (q > zlo) {
+            row_out(s0, q, Xm0, Sxm0, Sym0, Dm0, Qb0, Q0, pm0, xm0, acc);
+            row_out(s1, q, Xm1, Sxm1, Sym1, Dm1, Qb1, Q1, pm1, xm1, acc);
         }
-        Qm2 = Qm1;
-        Qm1 = Q;
-        Xm = X;
-        Dm = D;
-        pm = pq;
-        xm = xq;
+        Qb0 = Qa0; Qa0 = Q0; Xm0 = X0; Dm0 = D0; pm0 = pq0; xm0 = xq0;
+        Qb1 = Qa1; Qa1 = Q1; Xm1 = X1; Dm1 = D1; pm1 = pq1; xm1 = xq1;
         if constexpr (!ISO) {
-            Sxm = Sx;
-            Sym = Sy;
+            Sxm0 = Sx0; Sym0 = Sy0;
+            Sxm1 = Sx1; Sym1 = Sy1;
         }
         par ^= 1;
     }
@@ -332,7 +354,7 @@ struct StencilCgArgs {
 };
 
 template <bool ISO>
-__global__ void __launch_bounds__(kCgThreads, 3) k_cg_stencil(const StencilCgArgs a) {
+__global__ void __launch_bounds__(kCgThreads, 2) k_cg_stencil(const StencilCgArgs a) {
     __shared__ CgBlockState st;
     __shared__ double buf[kStBuf];
     const long long m = a.g.m;
