@@ -191,11 +191,19 @@ k_element_matrices(int nx, int ny, int nz, const double *__restrict__ coords,
                 c = fma(Ji[pj[p]][2], Ji[pl[p]][2], c);
                 C[p] = det * c;
             }
+            // an axis-aligned brick has a diagonal metric: the three cross
+            // pairs would add exact zeros, so they are skipped
+            const int np = (C[3] == 0.0 && C[4] == 0.0 && C[5] == 0.0) ? 3 : 6;
 #pragma unroll
             for (int k = 0; k < 36; ++k) {
                 double v = C[0] * kAffine.s[0][k];
-#pragma unroll
-                for (int p = 1; p < 6; ++p) v = fma(C[p], kAffine.s[p][k], v);
+                v = fma(C[1], kAffine.s[1][k], v);
+                v = fma(C[2], kAffine.s[2][k], v);
+                if (np == 6) {
+                    v = fma(C[3], kAffine.s[3][k], v);
+                    v = fma(C[4], kAffine.s[4][k], v);
+                    v = fma(C[5], kAffine.s[5][k], v);
+                }
                 K[k] = v;
             }
 #pragma unroll
