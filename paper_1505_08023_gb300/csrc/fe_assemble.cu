@@ -130,7 +130,12 @@ __device__ __forceinline__ double jac_inverse(const double J[3][3], double Ji[3]
     return det;
 }
 
-__global__ void __launch_bounds__(128)
+// PARALLELEPIPEDS = true: the elements whose edges along each axis agree
+// (constant Jacobian); false: all others, by per-point quadrature.  Two
+// launches, so that the common constant-Jacobian case does not carry the
+// quadrature's registers (224) and runs at full occupancy.
+template <bool PARALLELEPIPEDS>
+__global__ void __launch_bounds__(128, PARALLELEPIPEDS ? 4 : 1)
 k_element_matrices(int nx, int ny, int nz, const double *__restrict__ coords,
                    double *__restrict__ work) {
     const int64_t ne = (int64_t)nx * ny * nz;
@@ -155,31 +160,24 @@ k_element_matrices(int nx, int ny, int nz, const double *__restrict__ coords,
         for (int a = 7; a >= 0; --a)
 #pragma unroll
             for (int i = 0; i < 3; ++i) X[a][i] -= X[0][i];
-        // the twelve edge vectors (once per element)
-        double E[3][4][3];
-#pragma unroll
-        for (int j = 0; j < 3; ++j)
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-#pragma unroll
-                for (int i = 0; i < 3; ++i) E[j][k][i] = X[edge_corner(j, k, 1)][i] - X[edge_corner(j, k, 0)][i];
-        double K[36];
-        // parallelepiped: the four edges along each axis agree bit for bit
-        bool affine = true;
-#pragma unroll
-        for (int j = 0; j < 3; ++j)
-#pragma unroll
-            for (int k = 1; k < 4; ++k)
-#pragma unroll
-                for (int i = 0; i < 3; ++i)
-                    affine = affine && __double_as_longlong(E[j][k][i]) == __double_as_longlong(E[j][0][i]);
-        if (affine) {
-            // constant Jacobian d x_i / d xi_j = E_j / 2 (reference cell [-1, 1]^3)
+        if constexpr (PARALLELEPIPEDS) {
+            // parallelepiped: the four edges along each axis agree bit for bit;
+            // then d x_i / d xi_j = E_j / 2 is constant (reference cell [-1, 1]^3)
+            bool affine = true;
             double J[3][3], Ji[3][3];
 #pragma unroll
-            for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
 #pragma unroll
-                for (int j = 0; j < 3; ++j) J[i][j] = 0.5 * E[j][0][i];
+                for (int i = 0; i < 3; ++i) {
+                    const double e0 = X[edge_corner(j, 0, 1)][i] - X[edge_corner(j, 0, 0)][i];
+#pragma unroll
+                    for (int k = 1; k < 4; ++k) {
+                        const double ek = X[edge_corner(j, k, 1)][i] - X[edge_corner(j, k, 0)][i];
+                        affine = affine && __double_as_longlong(ek) == __double_as_longlong(e0);
+                    }
+                    J[i][j] = 0.5 * e0;
+                }
+            if (!affine) continue;   // the quadrature launch's element
             const double det = jac_inverse(J, Ji);
             // C_jl = det sum_i Ji[j][i] Ji[l][i], pairs in the table's order
             constexpr int pj[6] = {0, 1, 2, 0, 0, 1}, pl[6] = {0, 1, 2, 1, 2, 2};
@@ -193,69 +191,90 @@ k_element_matrices(int nx, int ny, int nz, const double *__restrict__ coords,
             }
             // an axis-aligned brick has a diagonal metric: the three cross
             // pairs would add exact zeros, so they are skipped
-            const int np = (C[3] == 0.0 && C[4] == 0.0 && C[5] == 0.0) ? 3 : 6;
-#pragma unroll
-            for (int k = 0; k < 36; ++k) {
-                double v = C[0] * kAffine.s[0][k];
-                v = fma(C[1], kAffine.s[1][k], v);
-                v = fma(C[2], kAffine.s[2][k], v);
-                if (np == 6) {
-                    v = fma(C[3], kAffine.s[3][k], v);
-                    v = fma(C[4], kAffine.s[4][k], v);
-                    v = fma(C[5], kAffine.s[5][k], v);
+            double *w = work + e;   // entry k at w[k ne]
+            if (C[3] == 0.0 && C[4] == 0.0 && C[5] == 0.0) {
+#pragma unroll 4
+                for (int k = 0; k < 36; ++k, w += ne) {
+                    double v = C[0] * kAffine.s[0][k];
+                    v = fma(C[1], kAffine.s[1][k], v);
+                    *w = fma(C[2], kAffine.s[2][k], v);
                 }
-                K[k] = v;
+            } else {
+#pragma unroll 4
+                for (int k = 0; k < 36; ++k, w += ne) {
+                    double v = C[0] * kAffine.s[0][k];
+#pragma unroll
+                    for (int p = 1; p < 6; ++p) v = fma(C[p], kAffine.s[p][k], v);
+                    *w = v;
+                }
+            }
+            continue;
+        } else {
+            // the twelve edge vectors (once per element)
+            double E[3][4][3];
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+#pragma unroll
+                    for (int i = 0; i < 3; ++i) E[j][k][i] = X[edge_corner(j, k, 1)][i] - X[edge_corner(j, k, 0)][i];
+            bool affine = true;
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+#pragma unroll
+                for (int k = 1; k < 4; ++k)
+#pragma unroll
+                    for (int i = 0; i < 3; ++i)
+                        affine = affine && __double_as_longlong(E[j][k][i]) == __double_as_longlong(E[j][0][i]);
+            if (affine) continue;   // the parallelepiped launch's element
+            double K[36];
+#pragma unroll
+            for (int k = 0; k < 36; ++k) K[k] = 0.0;
+
+#pragma unroll 1
+            for (int q = 0; q < 8; ++q) {
+                // J[i][j] = d x_i / d xi_j = sum over the four edges along j
+                double J[3][3];
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) {
+                        double s = 0.0;
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) s = fma(E[j][k][i], kEdgeW.w[q][j][k], s);
+                        J[i][j] = s;
+                    }
+                double Ji[3][3];
+                const double det = jac_inverse(J, Ji);
+                // physical gradients G[a] = J^{-T} grad_xi N_a; weight 1 at every point
+                double G[8][3];
+#pragma unroll
+                for (int a = 0; a < 8; ++a)
+#pragma unroll
+                    for (int i = 0; i < 3; ++i) {
+                        double s = 0.0;
+#pragma unroll
+                        for (int j = 0; j < 3; ++j) s = fma(Ji[j][i], kRefGrad.v[q][a][j], s);
+                        G[a][i] = s;
+                    }
+                double H[8][3];
+#pragma unroll
+                for (int a = 0; a < 8; ++a)
+#pragma unroll
+                    for (int i = 0; i < 3; ++i) H[a][i] = det * G[a][i];
+#pragma unroll
+                for (int a = 0; a < 8; ++a)
+#pragma unroll
+                    for (int b = a; b < 8; ++b) {
+                        double d = H[a][0] * G[b][0];
+                        d = fma(H[a][1], G[b][1], d);
+                        d = fma(H[a][2], G[b][2], d);
+                        K[tri_index(a, b)] += d;
+                    }
             }
 #pragma unroll
             for (int k = 0; k < 36; ++k) work[k * ne + e] = K[k];
-            continue;
         }
-#pragma unroll
-        for (int k = 0; k < 36; ++k) K[k] = 0.0;
-
-#pragma unroll 1
-        for (int q = 0; q < 8; ++q) {
-            // J[i][j] = d x_i / d xi_j = sum over the four edges along j
-            double J[3][3];
-#pragma unroll
-            for (int i = 0; i < 3; ++i)
-#pragma unroll
-                for (int j = 0; j < 3; ++j) {
-                    double s = 0.0;
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) s = fma(E[j][k][i], kEdgeW.w[q][j][k], s);
-                    J[i][j] = s;
-                }
-            double Ji[3][3];
-            const double det = jac_inverse(J, Ji);
-            // physical gradients G[a] = J^{-T} grad_xi N_a; weight 1 at every point
-            double G[8][3];
-#pragma unroll
-            for (int a = 0; a < 8; ++a)
-#pragma unroll
-                for (int i = 0; i < 3; ++i) {
-                    double s = 0.0;
-#pragma unroll
-                    for (int j = 0; j < 3; ++j) s = fma(Ji[j][i], kRefGrad.v[q][a][j], s);
-                    G[a][i] = s;
-                }
-            double H[8][3];
-#pragma unroll
-            for (int a = 0; a < 8; ++a)
-#pragma unroll
-                for (int i = 0; i < 3; ++i) H[a][i] = det * G[a][i];
-#pragma unroll
-            for (int a = 0; a < 8; ++a)
-#pragma unroll
-                for (int b = a; b < 8; ++b) {
-                    double d = H[a][0] * G[b][0];
-                    d = fma(H[a][1], G[b][1], d);
-                    d = fma(H[a][2], G[b][2], d);
-                    K[tri_index(a, b)] += d;
-                }
-        }
-#pragma unroll
-        for (int k = 0; k < 36; ++k) work[k * ne + e] = K[k];
     }
 }
 
@@ -374,8 +393,11 @@ fe_status fe_assemble_csr(int nx, int ny, int nz, const double *d_coords,
         return FE_ERR_ARG;
     if (work_bytes < (size_t)sz.n_elems * 36 * sizeof(double)) return FE_ERR_WORKSPACE;
     cudaStream_t s = (cudaStream_t)stream;
-    k_element_matrices<<<grid_cap(sz.n_elems, 128, 32), 128, 0, s>>>(nx, ny, nz, d_coords,
-                                                                     (double *)d_work);
+    k_element_matrices<true><<<grid_cap(sz.n_elems, 128, 32), 128, 0, s>>>(nx, ny, nz, d_coords,
+                                                                           (double *)d_work);
+    FE_TRY_LAUNCH();
+    k_element_matrices<false><<<grid_cap(sz.n_elems, 128, 32), 128, 0, s>>>(nx, ny, nz, d_coords,
+                                                                            (double *)d_work);
     FE_TRY_LAUNCH();
     k_assemble_rows<<<grid_cap(sz.n_rows, 128, 32), 128, 0, s>>>(
         nx, ny, nz, (const double *)d_work, d_bc_flag, d_bc_val, d_row_ptr, d_cols, d_vals, d_b);
