@@ -156,6 +156,36 @@ k_element_matrices(int nx, int ny, int nz, const double *__restrict__ coords,
 #pragma unroll
             for (int i = 0; i < 3; ++i) X[a][i] = coords[3 * node + i];
         }
+        // axis-aligned brick: a corner's x depends only on its x bit, y on its
+        // y bit, z on its z bit, bit for bit (integer compares, no FP64 work)
+        bool brick = true;
+#pragma unroll
+        for (int a = 1; a < 8; ++a) {
+            brick = brick && __double_as_longlong(X[a][0]) == __double_as_longlong(X[corner_of(corner_x(a), 0, 0)][0]);
+            brick = brick && __double_as_longlong(X[a][1]) == __double_as_longlong(X[corner_of(0, corner_y(a), 0)][1]);
+            brick = brick && __double_as_longlong(X[a][2]) == __double_as_longlong(X[corner_of(0, 0, corner_z(a))][2]);
+        }
+        if (brick) {
+            if constexpr (!PARALLELEPIPEDS) continue;   // the parallelepiped launch's element
+            // the parallelepiped path below with J = diag(hx, hy, hz) / 2: the
+            // same operations less the ones on exact zeros (bit-identical)
+            const double J0 = 0.5 * (X[1][0] - X[0][0]);
+            const double J1 = 0.5 * (X[3][1] - X[0][1]);
+            const double J2 = 0.5 * (X[4][2] - X[0][2]);
+            const double c00 = J1 * J2;
+            const double det = J0 * c00;
+            const double rdet = 1.0 / det;
+            const double i0 = c00 * rdet, i1 = (J0 * J2) * rdet, i2 = (J0 * J1) * rdet;
+            const double C0 = det * (i0 * i0), C1 = det * (i1 * i1), C2 = det * (i2 * i2);
+            double *w = work + e;   // entry k at w[k ne]
+#pragma unroll 4
+            for (int k = 0; k < 36; ++k, w += ne) {
+                double v = C0 * kAffine.s[0][k];
+                v = fma(C1, kAffine.s[1][k], v);
+                *w = fma(C2, kAffine.s[2][k], v);
+            }
+            continue;
+        }
 #pragma unroll
         for (int a = 7; a >= 0; --a)
 #pragma unroll
@@ -189,24 +219,13 @@ k_element_matrices(int nx, int ny, int nz, const double *__restrict__ coords,
                 c = fma(Ji[pj[p]][2], Ji[pl[p]][2], c);
                 C[p] = det * c;
             }
-            // an axis-aligned brick has a diagonal metric: the three cross
-            // pairs would add exact zeros, so they are skipped
             double *w = work + e;   // entry k at w[k ne]
-            if (C[3] == 0.0 && C[4] == 0.0 && C[5] == 0.0) {
 #pragma unroll 4
-                for (int k = 0; k < 36; ++k, w += ne) {
-                    double v = C[0] * kAffine.s[0][k];
-                    v = fma(C[1], kAffine.s[1][k], v);
-                    *w = fma(C[2], kAffine.s[2][k], v);
-                }
-            } else {
-#pragma unroll 4
-                for (int k = 0; k < 36; ++k, w += ne) {
-                    double v = C[0] * kAffine.s[0][k];
+            for (int k = 0; k < 36; ++k, w += ne) {
+                double v = C[0] * kAffine.s[0][k];
 #pragma unroll
-                    for (int p = 1; p < 6; ++p) v = fma(C[p], kAffine.s[p][k], v);
-                    *w = v;
-                }
+                for (int p = 1; p < 6; ++p) v = fma(C[p], kAffine.s[p][k], v);
+                *w = v;
             }
             continue;
         } else {
