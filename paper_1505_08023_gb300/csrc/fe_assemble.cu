@@ -306,19 +306,34 @@ __device__ __forceinline__ int64_t axis_prefix(int i) {  // sum of counts of ind
     return i == 0 ? 0 : 3 * (int64_t)i - 1;
 }
 
-__global__ void __launch_bounds__(128)
+// One warp per 32 consecutive rows (contiguous in CSR): each lane gathers its
+// row from the element workspace (the up to 64 loads issued without branches,
+// zeros for missing elements), writes the row into the warp's shared-memory
+// slice at its exclusive-scan offset, and the warp stores the slice with
+// coalesced writes.
+constexpr int kAsmWarps = 4;
+constexpr int kAsmSlice = 32 * 27;   // entries of 32 full rows
+
+__global__ void __launch_bounds__(32 * kAsmWarps)
 k_assemble_rows(int nx, int ny, int nz, const double *__restrict__ work,
                 const uint8_t *__restrict__ bc_flag, const double *__restrict__ bc_val,
                 int32_t *__restrict__ row_ptr, int32_t *__restrict__ cols,
                 double *__restrict__ vals, double *__restrict__ b) {
+    __shared__ int32_t s_cols[kAsmWarps][kAsmSlice];
+    __shared__ double s_vals[kAsmWarps][kAsmSlice];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int64_t nxn = nx + 1, nyn = ny + 1;
     const int64_t m = nxn * nyn * (nz + 1);
     const int64_t ne = (int64_t)nx * ny * nz;
     const int64_t Cx = 3 * (int64_t)nx + 1, Cy = 3 * (int64_t)ny + 1;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int ix = (int)(i % nxn);
-        const int64_t q = i / nxn;
+    const int64_t ngroups = (m + 31) / 32;
+    for (int64_t grp = (int64_t)blockIdx.x * kAsmWarps + wib; grp < ngroups;
+         grp += (int64_t)gridDim.x * kAsmWarps) {
+        const int64_t i = grp * 32 + lane;
+        const bool live = i < m;
+        const int64_t ii = live ? i : m - 1;
+        const int ix = (int)(ii % nxn);
+        const int64_t q = ii / nxn;
         const int iy = (int)(q % nyn);
         const int iz = (int)(q / nyn);
 
@@ -333,46 +348,65 @@ k_assemble_rows(int nx, int ny, int nz, const double *__restrict__ work,
 #pragma unroll
                 for (int dx = -1; dx <= 0; ++dx) {
                     const int ex = ix + dx, ey = iy + dy, ez = iz + dz;
-                    if (ex < 0 || ex >= nx || ey < 0 || ey >= ny || ez < 0 || ez >= nz) continue;
-                    const int64_t e = ex + (int64_t)nx * (ey + (int64_t)ny * ez);
+                    const bool has = ex >= 0 && ex < nx && ey >= 0 && ey < ny && ez >= 0 && ez < nz;
+                    const int64_t e = has ? ex + (int64_t)nx * (ey + (int64_t)ny * ez) : 0;
                     const int a = corner_of(-dx, -dy, -dz);
 #pragma unroll
                     for (int bb = 0; bb < 8; ++bb) {
                         const int sx = dx + corner_x(bb), sy = dy + corner_y(bb), sz = dz + corner_z(bb);
                         const int slot = (sz + 1) * 9 + (sy + 1) * 3 + (sx + 1);
-                        acc[slot] += work[(int64_t)tri_index(a, bb) * ne + e];
+                        acc[slot] += has ? work[(int64_t)tri_index(a, bb) * ne + e] : 0.0;
                     }
                 }
 
         const int64_t start = Cx * Cy * axis_prefix(iz) + Cx * axis_count(iz, nz) * axis_prefix(iy) +
                               axis_count(iy, ny) * axis_count(iz, nz) * axis_prefix(ix);
-        row_ptr[i] = (int32_t)start;
-        if (i == m - 1) row_ptr[m] = (int32_t)(start + axis_count(ix, nx) * axis_count(iy, ny) *
-                                                           axis_count(iz, nz));
-        const bool brow = bc_flag[i] != 0;
+        const int cnt = live ? (int)(axis_count(ix, nx) * axis_count(iy, ny) * axis_count(iz, nz)) : 0;
+        if (live) row_ptr[i] = (int32_t)start;
+        if (i == m - 1) row_ptr[m] = (int32_t)(start + cnt);
+        // exclusive scan of the row lengths: the row's place in the warp's slice
+        int off = cnt;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, off, d);
+            if (lane >= d) off += t;
+        }
+        const int total = __shfl_sync(0xffffffffu, off, 31);
+        off -= cnt;
+        const int64_t start0 = __shfl_sync(0xffffffffu, start, 0);
+
+        const bool brow = live && bc_flag[ii] != 0;
         double bi = 0.0;
-        int64_t pos = start;
+        int pos = off;
+        if (live) {
 #pragma unroll
-        for (int sz = -1; sz <= 1; ++sz)
+            for (int sz = -1; sz <= 1; ++sz)
 #pragma unroll
-            for (int sy = -1; sy <= 1; ++sy)
+                for (int sy = -1; sy <= 1; ++sy)
 #pragma unroll
-                for (int sx = -1; sx <= 1; ++sx) {
-                    const int jx = ix + sx, jy = iy + sy, jz = iz + sz;
-                    if (jx < 0 || jx > nx || jy < 0 || jy > ny || jz < 0 || jz > nz) continue;
-                    const int64_t j = i + sx + nxn * (sy + nyn * sz);
-                    double v = acc[(sz + 1) * 9 + (sy + 1) * 3 + (sx + 1)];
-                    if (brow) {
-                        v = (j == i) ? 1.0 : 0.0;
-                    } else if (bc_flag[j]) {
-                        bi = fma(-v, bc_val[j], bi);
-                        v = 0.0;
+                    for (int sx = -1; sx <= 1; ++sx) {
+                        const int jx = ix + sx, jy = iy + sy, jz = iz + sz;
+                        if (jx < 0 || jx > nx || jy < 0 || jy > ny || jz < 0 || jz > nz) continue;
+                        const int64_t j = i + sx + nxn * (sy + nyn * sz);
+                        double v = acc[(sz + 1) * 9 + (sy + 1) * 3 + (sx + 1)];
+                        if (brow) {
+                            v = (j == i) ? 1.0 : 0.0;
+                        } else if (bc_flag[j]) {
+                            bi = fma(-v, bc_val[j], bi);
+                            v = 0.0;
+                        }
+                        s_cols[wib][pos] = (int32_t)j;
+                        s_vals[wib][pos] = v;
+                        ++pos;
                     }
-                    cols[pos] = (int32_t)j;
-                    vals[pos] = v;
-                    ++pos;
-                }
-        b[i] = brow ? bc_val[i] : bi;
+            b[i] = brow ? bc_val[i] : bi;
+        }
+        __syncwarp();
+        for (int t = lane; t < total; t += 32) {
+            cols[start0 + t] = s_cols[wib][t];
+            vals[start0 + t] = s_vals[wib][t];
+        }
+        __syncwarp();
     }
 }
 
@@ -418,7 +452,7 @@ fe_status fe_assemble_csr(int nx, int ny, int nz, const double *d_coords,
     k_element_matrices<false><<<grid_cap(sz.n_elems, 128, 32), 128, 0, s>>>(nx, ny, nz, d_coords,
                                                                             (double *)d_work);
     FE_TRY_LAUNCH();
-    k_assemble_rows<<<grid_cap(sz.n_rows, 128, 32), 128, 0, s>>>(
+    k_assemble_rows<<<grid_cap((sz.n_rows + 31) / 32, kAsmWarps, 32), 32 * kAsmWarps, 0, s>>>(
         nx, ny, nz, (const double *)d_work, d_bc_flag, d_bc_val, d_row_ptr, d_cols, d_vals, d_b);
     FE_TRY_LAUNCH();
     return FE_OK;
