@@ -110,35 +110,57 @@ __global__ void k_fill_sell(int64_t n_rows, int64_t n_slices, const int32_t *__r
     }
 }
 
+// One warp per slice.  The slice's CSR entries are contiguous; when they fit
+// (kFillCap: 32 rows of 27) the warp first copies them to shared memory with
+// coalesced loads, so that each lane's walk along its own row (a 27-entry
+// stride between lanes) reads shared memory instead of scattered global
+// sectors; longer slices read global memory directly.
+constexpr int kFillWarps = 4;
+constexpr int kFillCap = 32 * 27;
+
 template <class VT>
-__global__ void k_fill_bcrs3(int64_t n_rows, int64_t n_cols, int64_t n_slices,
-                             const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ cols,
-                             const double *__restrict__ vals, const int64_t *__restrict__ slice_ptr,
-                             int32_t *__restrict__ out_cols, VT *__restrict__ out_vals) {
-    const int lane = threadIdx.x & 31;
-    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+__global__ void __launch_bounds__(32 * kFillWarps)
+k_fill_bcrs3(int64_t n_rows, int64_t n_cols, int64_t n_slices,
+             const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ cols,
+             const double *__restrict__ vals, const int64_t *__restrict__ slice_ptr,
+             int32_t *__restrict__ out_cols, VT *__restrict__ out_vals) {
+    __shared__ int32_t s_cols[kFillWarps][kFillCap];
+    __shared__ double s_vals[kFillWarps][kFillCap];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int64_t warps = (int64_t)gridDim.x * kFillWarps;
     const int32_t cmax = (int32_t)(n_cols - 3);  // last legal segment start
-    for (int64_t s = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); s < n_slices;
-         s += warps) {
+    for (int64_t s = blockIdx.x * (int64_t)kFillWarps + wib; s < n_slices; s += warps) {
         const int64_t row = s * kSlice + lane;
         const int64_t base = slice_ptr[s];
         const int w = (int)((slice_ptr[s + 1] - base) >> 5);
+        const int64_t last = (s * kSlice + kSlice < n_rows) ? s * kSlice + kSlice : n_rows;
+        const int32_t lo0 = row_ptr[s * kSlice], hi0 = row_ptr[last];
+        const bool staged = hi0 - lo0 <= kFillCap;
+        if (staged) {
+            for (int32_t t = lane; t < hi0 - lo0; t += 32) {
+                s_cols[wib][t] = cols[lo0 + t];
+                s_vals[wib][t] = vals[lo0 + t];
+            }
+        }
+        __syncwarp();
         int32_t j = 0, hi = 0, last_start = 0;
         if (row < n_rows) {
             j = row_ptr[row];
             hi = row_ptr[row + 1];
         }
+        auto col_at = [&](int32_t jj) { return staged ? s_cols[wib][jj - lo0] : cols[jj]; };
+        auto val_at = [&](int32_t jj) { return staged ? s_vals[wib][jj - lo0] : vals[jj]; };
         for (int k = 0; k < w; ++k) {
             const int64_t slot = base + (int64_t)k * kSlice + lane;
             VT *v = out_vals + 3 * base + (int64_t)k * 96 + lane;
             double seg[3] = {0.0, 0.0, 0.0};
             int32_t start = last_start;
             if (j < hi) {
-                const int32_t c = cols[j];
+                const int32_t c = col_at(j);
                 // shift the block left when it would run past the last column
                 start = c < cmax ? c : cmax;
-                while (j < hi && cols[j] <= c + 2) {
-                    seg[cols[j] - start] = vals[j];
+                while (j < hi && col_at(j) <= c + 2) {
+                    seg[col_at(j) - start] = val_at(j);
                     ++j;
                 }
                 last_start = start;
@@ -147,6 +169,7 @@ __global__ void k_fill_bcrs3(int64_t n_rows, int64_t n_cols, int64_t n_slices,
 #pragma unroll
             for (int t = 0; t < 3; ++t) v[32 * t] = round_to<VT>(seg[t]);
         }
+        __syncwarp();   // the slice buffer is reused by the warp's next slice
     }
 }
 
@@ -157,8 +180,8 @@ __global__ void k_round(int64_t n, const double *__restrict__ src, VT *__restric
         dst[i] = round_to<VT>(src[i]);
 }
 
-static int warp_grid(int64_t n_slices) {
-    int64_t blocks = (n_slices + 7) / 8;
+static int warp_grid(int64_t n_slices, int warps_per_block = 8) {
+    int64_t blocks = (n_slices + warps_per_block - 1) / warps_per_block;
     int64_t cap = (int64_t)sm_count() * 16;
     if (cap < 1) cap = 1024;
     return (int)(blocks < 1 ? 1 : (blocks > cap ? cap : blocks));
@@ -171,7 +194,7 @@ static fe_status launch_fill(const fe_matrix *src, const fe_matrix *dst, cudaStr
             src->n_rows, dst->n_slices, src->d_row_ptr, src->d_cols, (const double *)src->d_vals,
             dst->d_slice_ptr, const_cast<int32_t *>(dst->d_cols), (VT *)const_cast<void *>(dst->d_vals));
     else
-        k_fill_bcrs3<VT><<<warp_grid(dst->n_slices), 256, 0, s>>>(
+        k_fill_bcrs3<VT><<<warp_grid(dst->n_slices, kFillWarps), 32 * kFillWarps, 0, s>>>(
             src->n_rows, src->n_cols, dst->n_slices, src->d_row_ptr, src->d_cols,
             (const double *)src->d_vals, dst->d_slice_ptr, const_cast<int32_t *>(dst->d_cols),
             (VT *)const_cast<void *>(dst->d_vals));
