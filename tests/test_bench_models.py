@@ -1,0 +1,42 @@
+"""The benchmark's byte, FLOP and operation models and its clock-sample
+parsing, checked on the CPU against hand counts (the roofline fractions in
+the bench line are only as good as these)."""
+import bench
+
+
+def test_csr_spmv_bytes_match_the_closed_form():
+    # (sv + 4) nnz + 4 (m + 1) + 2 sv m with sv = 8: 5.797 GB at N = 256
+    n = 256
+    m, nnz = (n + 1) ** 3, (3 * n + 1) ** 3
+    b = bench.spmv_bytes("csr", m, (m + 31) // 32, nnz, nnz)
+    assert b == 12 * nnz + 4 * (m + 1) + 16 * m
+    assert abs(b / 1e9 - 5.7966) < 1e-4
+
+
+def test_bcrs3_step_model_counts_indices_values_and_vectors():
+    m, ns, slots = 1000, 32, 400
+    byts, fma, mat = bench.cg_iteration_model("bcrs3", m, ns, slots, 0)
+    assert mat == slots * (4 + 3 * 8) + 8 * (ns + 1)
+    assert byts == mat + 80 * m          # w=Ap 16 B, r update 24 B, x and p update 40 B per row
+    assert fma == 3 * slots + 5 * m      # one FMA per stored value + p.w, r, r.r, x, p
+
+
+def test_matrix_free_operation_model_on_a_tiny_cube():
+    # N = 2: 27 nodes, one interior node, 26 boundary nodes
+    ops = bench.matrix_free_ops(2)
+    assert ops["spmv"] == 9
+    assert ops["step"] == 12 * 1 + 3 * 26 + 2 * 27
+    assert ops["init"] == 10 * 1 + 2 * 27
+
+
+def test_clock_samples_are_parsed_into_median_and_reasons():
+    c = bench.ClockSampler("0")
+    c.proc = type("P", (), {"terminate": lambda self: None, "wait": lambda self, timeout=None: 0,
+                            "kill": lambda self: None})()
+    c.lines = ["2070, 2070, 800.5, 0x0, Not Active, Not Active, Not Active, Not Active",
+               "2055, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active",
+               "2070, 2070, 900.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+               "garbage line"]
+    out = c.stop()
+    assert out["sm_mhz"] == 2070.0 and out["sm_max_mhz"] == 2070.0
+    assert out["reasons"] == ["sw_power_cap"] and out["power_w_max"] == 1390.0
