@@ -423,9 +423,9 @@ fe_status fe_nn_conv3d_s2_tc(const float *d_in, int cin, const int *h_dims_in, c
  * that fe_nn_to_bf16i writes (fe_nn_bf16i_bytes bytes, 16-byte aligned).  The
  * input box of each 16-channel chunk is staged by tensor-map (TMA) loads with
  * zero fill outside the grid; otherwise as fe_nn_conv3d_{s1,s2,t2}_tc (same
- * result bits: the FP32 kernels round the same values to BF16).  The fine
- * box of a stride-2 layer must be at most 256 points per row after the
- * stride (output width <= 127). */
+ * result bits: the FP32 kernels round the same values to BF16).  A TMA box
+ * spans at most 256 points per axis: input width <= 254 (stride 1), <= 255
+ * (transposed), output width <= 127 (stride 2); wider grids get FE_ERR_ARG. */
 fe_status fe_nn_bf16i_bytes(int c, const int *h_dims, size_t *h_bytes);
 fe_status fe_nn_to_bf16i(const float *d_in, int c, const int *h_dims, void *d_out, fe_stream_t stream);
 fe_status fe_nn_conv3d_tc_bf16i(int mode, const void *d_in16, int cin, const int *h_dims_in, const void *d_img,
