@@ -296,8 +296,9 @@ fe_status fe_cg_solve_mixed(const fe_matrix *A64, const fe_matrix *A_lo, const d
  *   exits), so A may have at most FE_NOALLOC_MAX_ROWS rows (32 * n_slices <=
  *   FE_NOALLOC_MAX_ROWS, e.g. meshes up to 63 x 63 x 63 elements); larger A
  *   returns FE_ERR_WORKSPACE before anything is enqueued.
- *   The first call on a device looks up that array's device address (with the
- *   device current); make that first call before any stream capture.
+ *   Every call looks up that array's device address on the current device
+ *   (a host-side query that allocates nothing), so the address stays valid
+ *   after a cudaDeviceReset.
  *   All calls share the one array: calls whose work overlaps on the GPU (two
  *   streams, two host threads) race and give undefined results; serialise
  *   them.  Each call re-initialises the part that must start at zero.

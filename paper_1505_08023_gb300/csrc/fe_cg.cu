@@ -21,8 +21,6 @@
 // poll).  Every wait is bounded: past `timeout_ns` (or a poll cap) the block
 // raises the abort flag and leaves; the others see the flag at their next
 // wait and leave too, and the host reports FE_ERR_TIMEOUT.  Nothing traps.
-#include <mutex>
-
 #include "fe_cg_common.cuh"
 
 namespace fe {
@@ -283,9 +281,11 @@ fe_status fe_true_relres(const fe_matrix *A, const double *d_b, const double *d_
 // still pass A, b and x; the solver's own scratch (barrier/result block,
 // reduction partials and the r, p, w vectors) lives in the file-scope array
 // below, which every GPU that loads this library holds until the process
-// exits.  Host code cannot use the array's name as a device address, so the
-// first call on each device looks the address up with cudaGetSymbolAddress
-// (with that device current) and caches it.
+// exits.  Host code cannot use the array's name as a device address, so every
+// call looks the address up with cudaGetSymbolAddress on the current device.
+// The lookup is a host-side query (no allocation, nothing enqueued); doing it
+// per call instead of caching it keeps the address valid after a
+// cudaDeviceReset, which reloads the module and moves the array.
 
 namespace fe {
 
@@ -295,21 +295,11 @@ constexpr size_t kNoallocBytes =
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
 
-static std::mutex g_noalloc_mu;
-static void *g_noalloc_addr[64];
-
-// Device address of g_noalloc_scratch on the current device (looked up once).
+// Device address of g_noalloc_scratch on the current device.
 static fe_status noalloc_scratch(void **out) {
-    int dev = 0;
-    FE_TRY_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 64) return FE_ERR_ARG;
-    std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (g_noalloc_addr[dev] == nullptr) {
-        void *p = nullptr;
-        FE_TRY_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
-        g_noalloc_addr[dev] = p;
-    }
-    *out = g_noalloc_addr[dev];
+    void *p = nullptr;
+    FE_TRY_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    *out = p;
     return FE_OK;
 }
 
