@@ -313,17 +313,26 @@ void orc_dirichlet(int64_t m, const uint8_t *bc_flag, const double *bc_val,
 }
 
 /* ------------------------------------------------------------------------ */
-/* CRS SpMV, y = A x (paper Fig 3.1; y is cleared first because the listing  */
-/* accumulates into it).                                                     */
+/* CRS SpMV, y = A x (paper Fig 3.1).  By the definition of the CRS format, */
+/* row i stores the pairs (cols[k], vals[k]) for row_ptr[i] <= k <           */
+/* row_ptr[i+1], so y_i is the inner product of those values with the x      */
+/* entries they name, summed in stored (ascending column) order.             */
 /* ------------------------------------------------------------------------ */
+static double crs_row_product(const int32_t *row_ptr, const int32_t *cols, const double *vals,
+                              const double *x, int64_t i)
+{
+    const int64_t first = row_ptr[i], count = (int64_t)row_ptr[i + 1] - first;
+    double s = 0.0;
+    for (int64_t t = 0; t < count; ++t)
+        s += vals[first + t] * x[cols[first + t]];
+    return s;
+}
+
 void orc_spmv_csr(int64_t m, const int32_t *row_ptr, const int32_t *cols,
                   const double *vals, const double *x, double *y)
 {
-    for (int64_t i = 0; i < m; ++i) {
-        y[i] = 0.0;
-        for (int64_t j = row_ptr[i]; j < row_ptr[i + 1]; ++j)
-            y[i] += vals[j] * x[cols[j]];
-    }
+    for (int64_t i = 0; i < m; ++i)
+        y[i] = crs_row_product(row_ptr, cols, vals, x, i);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -358,18 +367,24 @@ int64_t orc_csr_to_bcrs(int64_t m, const int32_t *row_ptr, const int32_t *cols,
     return nns;
 }
 
-/* BCRS SpMV (paper Fig 3.2): per segment, walk its values against x from jas. */
+/* BCRS SpMV (paper Sec. 3.1, Fig 3.2).  By the format's definition segment */
+/* j of row i (ptr[i] <= j < ptr[i+1]) is the run of L_j = offsets[j+1] -    */
+/* offsets[j] adjacent columns jas[j], jas[j]+1, ..., whose values are       */
+/* val[offsets[j] + t], t < L_j; y_i sums value times x over the segments in */
+/* order, which is the CRS order of the same entries.                        */
 void orc_spmv_bcrs(int64_t m, const int32_t *ptr, const int32_t *jas,
                    const int32_t *offsets, const double *val, const double *x, double *y)
 {
     for (int64_t i = 0; i < m; ++i) {
-        double sum = 0.0;
+        double s = 0.0;
         for (int64_t j = ptr[i]; j < ptr[i + 1]; ++j) {
-            int64_t col = jas[j];
-            for (int64_t k = offsets[j]; k < offsets[j + 1]; ++k)
-                sum += val[k] * x[col++];
+            const double *seg_val = val + offsets[j];
+            const double *seg_x = x + jas[j];
+            const int64_t len = (int64_t)offsets[j + 1] - offsets[j];
+            for (int64_t t = 0; t < len; ++t)
+                s += seg_val[t] * seg_x[t];
         }
-        y[i] = sum;
+        y[i] = s;
     }
 }
 
