@@ -390,14 +390,55 @@ void orc_spmv_bcrs(int64_t m, const int32_t *ptr, const int32_t *jas,
 
 /* ------------------------------------------------------------------------ */
 /* Vector kernels named in the paper's CG module (Sec. 1): DOT and WAXPY.    */
-/* DOT sums sequentially in index order.                                     */
+/* Reading of DOT: the inner product of the two vectors, rounded once.  A    */
+/* plain running sum in index order carries a rounding error that grows      */
+/* with n (up to n u relative) and, through CG's sensitivity to its          */
+/* inner products, moves the stop step of a 10^6-row solve by several steps  */
+/* away from every accurately summed order.  So DOT is the compensated dot   */
+/* product Dot2 of Ogita, Rump and Oishi ("Accurate sum and dot product",    */
+/* SIAM J. Sci. Comput. 26, 2005): each product split exactly into p + e     */
+/* (Dekker's product with Veltkamp's splitting), the running sum kept with   */
+/* its exact rounding error (Knuth's TwoSum), the errors summed on the side  */
+/* and added once at the end.  The result is as accurate as the inner        */
+/* product computed in twice the working precision and then rounded:         */
+/* |DOT - a.b| <= u |a.b| + gamma_n^2 |a|.|b|.  Plain operations only, in    */
+/* index order, so x86 and Arm give the same bits.                           */
 /* ------------------------------------------------------------------------ */
+static void two_sum(double a, double b, double *s, double *err)
+{
+    const double x = a + b, z = x - a;
+    *s = x;
+    *err = (a - (x - z)) + (b - z);
+}
+
+static void veltkamp_split(double a, double *hi, double *lo)
+{
+    const double c = 134217729.0 * a;         /* (2^27 + 1) a */
+    const double h = c - (c - a);
+    *hi = h;
+    *lo = a - h;
+}
+
+static void two_product(double a, double b, double *p, double *err)
+{
+    double ah, al, bh, bl;
+    const double x = a * b;
+    veltkamp_split(a, &ah, &al);
+    veltkamp_split(b, &bh, &bl);
+    *p = x;
+    *err = al * bl - (((x - ah * bh) - al * bh) - ah * bl);
+}
+
 double orc_dot(int64_t n, const double *a, const double *b)
 {
-    double s = 0.0;
-    for (int64_t i = 0; i < n; ++i)
-        s += a[i] * b[i];
-    return s;
+    double s = 0.0, c = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        double p, ep, q;
+        two_product(a[i], b[i], &p, &ep);
+        two_sum(s, p, &s, &q);
+        c += q + ep;
+    }
+    return s + c;
 }
 
 /* w = alpha x + beta y */

@@ -1,12 +1,14 @@
 """GPU parity of the fused persistent CG (paper Sec. 1: MATVEC, DOT, WAXPY,
 no preconditioner) against the oracle's CG, through the C ABI.
 
-The GPU sums dot products in a different (blocked) order than the oracle's
-sequential sums.  CG amplifies that rounding in its iterates: a CPU CG that
-differs from the oracle only by pairwise dot products already stops one step
-earlier and sits 1.7e-9 (relative) from the oracle's iterate at 1e-10
-(tests/test_oracle_solve.py::test_summation_order_changes_iterates).  So an
-iterate-for-iterate 1e-10 match is not a property of CG; the criteria are
+The GPU sums dot products in a blocked order, the oracle with a compensated
+(accurately rounded) running sum.  CG amplifies rounding in its iterates: in
+the middle of a solve the iterates of two summation orders wander apart, and
+at relative residual 1e-10 only the error left in the solution bounds their
+distance; on a 97^3-node mesh a CPU CG that differs from the oracle only by
+pairwise dot products stops within a step of it, 5e-9 (relative) from the
+oracle's iterate (tests/test_oracle_solve.py::test_summation_order_changes_iterates).
+So an iterate-for-iterate 1e-10 match is not a property of CG; the criteria are
   (i)   stop iteration k_gpu within +-1 of the oracle's;
   (ii)  at tol 1e-10 the GPU solution is as accurate as the oracle's:
         ||x_gpu - x*|| <= 2 ||x_oracle - x*|| + 1e-12 ||x*||, x* the oracle's
@@ -192,3 +194,130 @@ def test_full_size_n256_solve(fe):
     assert tr <= 1.5e-10
     centre = 128 + 257 * (128 + 257 * 128)
     assert abs(float(x[centre]) - 1.0 / 6.0) < 2e-5
+
+
+# ---------------------------------------------------------------- kernel forms
+
+def solve_form(fe, s, fmt, form, tol=1e-10, maxit=1000, x0=None, b=None, timeout=0.0, check=True):
+    A = s.matrix(fmt, "f64")
+    x = torch.zeros(s.m, dtype=torch.float64, device="cuda") if x0 is None else x0.clone()
+    res = fe.fe_cg_solve_form(A.desc, s.b if b is None else b, x, tol, maxit, form,
+                              fe.cg_workspace(A), timeout, check=check)
+    return x, res
+
+
+@pytest.mark.parametrize("fmt", ["csr", "sell", "bcrs3"])
+@pytest.mark.parametrize("dims", [(30, 30, 30), (17, 9, 23), (4, 4, 4), (64, 64, 64)])
+def test_two_phase_form_is_bitwise_the_three_phase_form(fe, fmt, dims):
+    """The two-phase kernel (x and p update folded into the next SpMV's operand
+    gather) performs the three-phase kernel's operations in the same order:
+    same stop step, same residual, identical bits -- also on a mesh with
+    several slices per warp."""
+    s = fe.System(*dims).build()
+    x3, r3 = solve_form(fe, s, fmt, fe.FE_CG_THREE_PHASE)
+    x2, r2 = solve_form(fe, s, fmt, fe.FE_CG_TWO_PHASE)
+    assert r3.status == r2.status == fe.FE_OK
+    assert r3.iterations == r2.iterations and r3.relres == r2.relres
+    assert torch.equal(x3, x2)
+
+
+def test_two_phase_form_matches_oracle_and_edge_cases(fe):
+    dims = (30, 30, 30)
+    ref = reference(dims)
+    s = fe.System(*dims).build()
+    x, res = solve_form(fe, s, "bcrs3", fe.FE_CG_TWO_PHASE)
+    assert res.status == fe.FE_OK
+    check_parity(ref, x.cpu().numpy(), res.iterations)
+    t = fe.System(6, 5, 4).build()
+    F2 = fe.FE_CG_TWO_PHASE
+    zero = torch.zeros(t.m, dtype=torch.float64, device="cuda")
+    x, res = solve_form(fe, t, "bcrs3", F2, b=zero, x0=torch.ones_like(zero))
+    assert res.status == fe.FE_OK and res.iterations == 0 and torch.count_nonzero(x) == 0
+    # maxit: the iterate after exactly maxit steps (the pending x update applied)
+    x, res = solve_form(fe, t, "csr", F2, maxit=3, check=False)
+    assert res.status == fe.FE_ERR_MAXIT and res.iterations == 3
+    sysm = oracle.build_system(6, 5, 4)
+    x3, _, _, _ = oracle.cg(sysm["row_ptr"], sysm["cols"], sysm["vals"], sysm["b"], tol=0, maxit=3)
+    assert np.allclose(x.cpu().numpy(), x3, rtol=0, atol=1e-12)
+    x, res = solve_form(fe, t, "sell", F2, maxit=0, check=False)
+    assert res.status == fe.FE_ERR_MAXIT and res.iterations == 0
+    xs, _ = solve_form(fe, t, "bcrs3", F2, tol=1e-13)
+    x, res = solve_form(fe, t, "bcrs3", F2, x0=xs, tol=1e-10)
+    assert res.status == fe.FE_OK and res.iterations == 0 and torch.equal(x, xs)
+    bn = t.b.clone()
+    bn[t.m // 2] = float("nan")
+    x, res = solve_form(fe, t, "csr", F2, b=bn, check=False)
+    assert res.status == fe.FE_ERR_BREAKDOWN
+    with pytest.raises(fe.FeError) as e:
+        solve_form(fe, t, "csr", 7)
+    assert e.value.status == fe.FE_ERR_ARG
+    u = fe.System(16).build()
+    fe.fe_inject_barrier_stall(3)
+    x, res = solve_form(fe, u, "bcrs3", F2, timeout=0.2, check=False)
+    assert res.status == fe.FE_ERR_TIMEOUT
+    x, res = solve_form(fe, u, "bcrs3", F2)
+    assert res.status == fe.FE_OK
+
+
+@pytest.mark.parametrize("fmt", ["sell", "bcrs3"])
+@pytest.mark.parametrize("dims", [(30, 30, 30), (4, 4, 4), (17, 9, 23), (32, 32, 32), (1, 1, 1)])
+def test_resident_form_matches_oracle(fe, fmt, dims):
+    """The matrix-resident kernel (each warp's slice and rows in registers)
+    against the oracle with the FP64 criteria, and against the three-phase
+    kernel: same stop step (+-1), solutions within the 1e-10 bar."""
+    s = fe.System(*dims).build()
+    x, res = solve_form(fe, s, fmt, fe.FE_CG_RESIDENT)
+    assert res.status == fe.FE_OK and res.relres <= 1e-10
+    if dims != (1, 1, 1):
+        check_parity(reference(dims), x.cpu().numpy(), res.iterations)
+    else:
+        assert torch.equal(x, s.bc_val)
+    x3, r3 = solve_form(fe, s, fmt, fe.FE_CG_THREE_PHASE)
+    assert abs(res.iterations - r3.iterations) <= 1
+    assert torch.linalg.norm(x - x3) <= 1e-10 * torch.linalg.norm(x3)
+    xa, ra = solve_form(fe, s, fmt, fe.FE_CG_AUTO)          # AUTO picks this form here
+    assert torch.equal(xa, x) and ra.iterations == res.iterations
+
+
+def test_resident_form_face_data_and_edge_cases(fe):
+    dims = (24, 24, 24)
+    face = fe_inputs.face_data(0, 5, *dims)
+    ref = reference(dims, face)
+    s = fe.System(*dims, face_vals=torch.from_numpy(face).cuda()).build()
+    R = fe.FE_CG_RESIDENT
+    x, res = solve_form(fe, s, "bcrs3", R)
+    assert res.status == fe.FE_OK
+    check_parity(ref, x.cpu().numpy(), res.iterations)
+    t = fe.System(6, 5, 4).build()
+    zero = torch.zeros(t.m, dtype=torch.float64, device="cuda")
+    x, res = solve_form(fe, t, "bcrs3", R, b=zero, x0=torch.ones_like(zero))
+    assert res.status == fe.FE_OK and res.iterations == 0 and torch.count_nonzero(x) == 0
+    x, res = solve_form(fe, t, "sell", R, maxit=3, check=False)
+    assert res.status == fe.FE_ERR_MAXIT and res.iterations == 3
+    sysm = oracle.build_system(6, 5, 4)
+    x3, _, _, _ = oracle.cg(sysm["row_ptr"], sysm["cols"], sysm["vals"], sysm["b"], tol=0, maxit=3)
+    assert np.allclose(x.cpu().numpy(), x3, rtol=0, atol=1e-12)
+    x, res = solve_form(fe, t, "bcrs3", R, maxit=0, check=False)
+    assert res.status == fe.FE_ERR_MAXIT and res.iterations == 0
+    xs, _ = solve_form(fe, t, "bcrs3", R, tol=1e-13)
+    x, res = solve_form(fe, t, "bcrs3", R, x0=xs, tol=1e-10)
+    assert res.status == fe.FE_OK and res.iterations == 0 and torch.equal(x, xs)
+    bn = t.b.clone()
+    bn[t.m // 2] = float("nan")
+    x, res = solve_form(fe, t, "sell", R, b=bn, check=False)
+    assert res.status == fe.FE_ERR_BREAKDOWN
+    # only FP64 BCRS3 / sliced-ELL matrices of at most one slice per warp qualify
+    for fmt, value, dims_ in (("csr", "f64", (6, 5, 4)), ("bcrs3", "f32", (6, 5, 4)),
+                              ("bcrs3", "f64", (40, 40, 40))):
+        u = fe.System(*dims_).build()
+        A = u.matrix(fmt, value)
+        xx = torch.zeros(u.m, dtype=torch.float64, device="cuda")
+        with pytest.raises(fe.FeError) as e:
+            fe.fe_cg_solve_form(A.desc, u.b, xx, 1e-10, 100, R, fe.cg_workspace(A))
+        assert e.value.status == fe.FE_ERR_ARG
+    u = fe.System(16).build()
+    fe.fe_inject_barrier_stall(3)
+    x, res = solve_form(fe, u, "bcrs3", R, timeout=0.2, check=False)
+    assert res.status == fe.FE_ERR_TIMEOUT
+    x, res = solve_form(fe, u, "bcrs3", R)
+    assert res.status == fe.FE_OK
