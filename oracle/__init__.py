@@ -312,6 +312,41 @@ def stencil_rhs(nx: int, ny: int, nz: int, bc_val) -> np.ndarray:
     return b
 
 
+def dirichlet_extreme_eigenvalues(nx: int, ny: int, nz: int):
+    """(lambda_min, lambda_max) of the Dirichlet system A of the box mesh.
+
+    Symmetric elimination (Sec. 1, boundary rows recorded by the mesh module)
+    splits A into the identity on the boundary nodes and the interior block
+    K_II.  On the brick mesh the trilinear element's stiffness is the Kronecker
+    sum of 1D linear-element stiffness L = (1/h) tridiag(-1, 2, -1) and mass
+    M = (h/6) tridiag(1, 4, 1), so K_II = Lx (x) My (x) Mz + Mx (x) Ly (x) Mz +
+    Mx (x) My (x) Lz restricted to the interior nodes.  With Dirichlet ends the
+    1D matrices share the eigenvectors sin(k pi j h), k = 1..N-1, with
+    eigenvalues l(k) = (2/h)(1 - cos k pi h) and m(k) = (h/3)(2 + cos k pi h),
+    and K_II's eigenvalues are lx(i) my(j) mz(k) + mx(i) ly(j) mz(k) +
+    mx(i) my(j) lz(k).  The spectrum of A is that set together with 1.
+    """
+    def one_d(n):
+        h = 1.0 / n
+        k = np.arange(1, n, dtype=np.float64)
+        c = np.cos(k * np.pi * h)
+        return (2.0 / h) * (1.0 - c), (h / 3.0) * (2.0 + c)
+
+    lo, hi = 1.0, 1.0                      # the boundary nodes' identity rows
+    if min(nx, ny, nz) >= 2:
+        lx, mx = one_d(nx)
+        ly, my = one_d(ny)
+        lz, mz = one_d(nz)
+        lymz = np.multiply.outer(ly, mz)
+        mylz = np.multiply.outer(my, lz)
+        mymz = np.multiply.outer(my, mz)
+        for i in range(lx.size):
+            lam = lx[i] * mymz + mx[i] * (lymz + mylz)
+            lo = min(lo, float(lam.min()))
+            hi = max(hi, float(lam.max()))
+    return lo, hi
+
+
 def dense(row_ptr, cols, vals) -> np.ndarray:
     """Dense copy of a CRS matrix (small meshes only)."""
     m = row_ptr.shape[0] - 1
