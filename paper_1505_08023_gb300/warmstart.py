@@ -386,6 +386,47 @@ def predict_x0(net: WarmStartNet, prob: Problem, x0: torch.Tensor):
                           net._infer_work, net.tensor_cores)
 
 
+BLOB_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights")
+DEFAULT_BLOB = os.path.join(BLOB_DIR, "warmstart_n128.blob")
+
+
+def save_blob(net: WarmStartNet, path: str, meta: dict):
+    """Write the inference blob (the fe_warmstart_infer weight layout) and a
+    JSON description of how it was trained beside it."""
+    os.makedirs(os.path.dirname(os.path.abspath(path)), exist_ok=True)
+    with open(path, "wb") as f:
+        f.write(net.blob().cpu().numpy().tobytes())
+    info = dict(meta)
+    info.update({"channels": list(net.ch), "n_nodes": net.n_nodes,
+                 "layout": "fe_warmstart_blob_layout (bias FP32, weights BF16 per layer)"})
+    with open(path + ".json", "w") as f:
+        json.dump(info, f, indent=1)
+
+
+class TrainedWarmStart:
+    """Inference from a saved blob: x0 = network(boundary data), boundary
+    nodes set to g exactly (one fe_warmstart_infer call)."""
+
+    def __init__(self, path: str = DEFAULT_BLOB, device="cuda"):
+        with open(path + ".json") as f:
+            self.meta = json.load(f)
+        self.ch = tuple(self.meta["channels"])
+        self.n_nodes = int(self.meta["n_nodes"])
+        raw = np.fromfile(path, dtype=np.uint8)
+        _, nbytes = fe.fe_warmstart_blob_layout(self.ch)
+        if raw.size != nbytes:
+            raise ValueError(f"{path}: {raw.size} bytes, the layout of channels {self.ch} has {nbytes}")
+        self.dev = torch.device(device)
+        self.blob = torch.from_numpy(raw).to(self.dev)
+        self.work = fe._alloc_bytes(fe.fe_warmstart_workspace(self.n_nodes, self.ch), self.dev)
+
+    def predict(self, sys, x0: torch.Tensor, stream=None):
+        if any(d + 1 != self.n_nodes for d in sys.dims):
+            raise ValueError("the blob was trained for a different mesh")
+        fe.fe_warmstart_infer(self.n_nodes, self.ch, self.blob, sys.bc_flag, sys.bc_val, x0, self.work,
+                              True, stream)
+
+
 def evaluate(net: WarmStartNet, prob: Problem, faces, tol=1e-10):
     """CG from x0 = 0 and from the network's x0 on each boundary data set."""
     EV = lambda: torch.cuda.Event(enable_timing=True)
@@ -444,7 +485,7 @@ def summarize(rows):
 
 
 def run(N=128, n_train=2000, n_test=200, epochs=1, lr=1e-3, device="cuda", seed_train=1000,
-        seed_test=2000, lr_final=None, res_weight=0.0):
+        seed_test=2000, lr_final=None, res_weight=0.0, save=None):
     t0 = time.time()
     prob = Problem(N, device)
     faces_tr = face_set(seed_train, 0, n_train, N)
@@ -459,6 +500,11 @@ def run(N=128, n_train=2000, n_test=200, epochs=1, lr=1e-3, device="cuda", seed_
     torch.cuda.synchronize()
     t3 = time.time()
     del targets
+    if save:
+        save_blob(net, save, {"N": N, "n_train": n_train, "epochs": epochs, "lr": lr,
+                              "lr_final": lr_final, "res_weight": res_weight,
+                              "train_seeds": f"PCG64({seed_train}, 0..{n_train - 1})",
+                              "final_losses": losses[-3:] if losses else []})
     rows = evaluate(net, prob, faces_te)
     t4 = time.time()
     rep = summarize(rows)
@@ -482,8 +528,10 @@ def main():
     ap.add_argument("--lr-final", type=float, default=None)
     ap.add_argument("--res-weight", type=float, default=0.0)
     ap.add_argument("--out", default=None)
+    ap.add_argument("--save-blob", default=None, help="write the trained inference blob here")
     a = ap.parse_args()
-    rep = run(a.n, a.train, a.test, a.epochs, a.lr, lr_final=a.lr_final, res_weight=a.res_weight)
+    rep = run(a.n, a.train, a.test, a.epochs, a.lr, lr_final=a.lr_final, res_weight=a.res_weight,
+              save=a.save_blob)
     s = json.dumps(rep)
     print(s)
     if a.out:
