@@ -49,8 +49,10 @@ typedef enum fe_status {
 typedef enum fe_format {
     FE_FMT_CSR = 0,   /* compressed rows (paper Sec. 3.1, "CRS"): row_ptr, cols, vals */
     FE_FMT_SELL = 1,  /* sliced ELL, 32-row slices, column-major inside a slice */
-    FE_FMT_BCRS3 = 2  /* 1x3 blocked rows (the paper's BCRS, Sec. 3.1, with every
+    FE_FMT_BCRS3 = 2, /* 1x3 blocked rows (the paper's BCRS, Sec. 3.1, with every
                          segment padded to length 3), 32-row slices */
+    FE_FMT_VBCRS = 3  /* the paper's BCRS as printed (Sec. 3.1, Fig 3.2/3.3): maximal
+                         runs of adjacent columns of variable length, no padding */
 } fe_format;
 
 /* Storage type of matrix values. */
@@ -72,7 +74,16 @@ typedef enum fe_value_type { FE_VAL_F64 = 0, FE_VAL_F32 = 1, FE_VAL_BF16 = 2 } f
  *                three values multiply x[c], x[c+1], x[c+2].  Values of slot
  *                group g = slice_ptr[s]/32 + k sit at vals[96g + 32t + r],
  *                t = 0, 1, 2 (component), r = row in slice.
+ *   FE_FMT_VBCRS the paper's BCRS: a segment is a maximal run of adjacent
+ *                columns of a row.  row_ptr[n_rows+1] (int32) holds each
+ *                row's first segment ("ptr"), cols[n_stored] each segment's
+ *                first column ("jas"), seg_offsets[n_stored+1] (int32) each
+ *                segment's first value ("offsets", seg_offsets[n_stored] =
+ *                nnz); vals[nnz] is the CSR value array unchanged (values of
+ *                segment j at vals[seg_offsets[j] + t], t < its length,
+ *                multiplying x[cols[j] + t]).  n_stored = segments (nns).
  * vals has the element type value_type.  n_slices = ceil(n_rows / 32).
+ * seg_offsets is used by FE_FMT_VBCRS only (NULL otherwise).
  */
 typedef struct fe_matrix {
     int32_t format;           /* fe_format */
@@ -85,6 +96,7 @@ typedef struct fe_matrix {
     const int64_t *d_slice_ptr; /* SELL, BCRS3 */
     const int32_t *d_cols;
     const void *d_vals;
+    const int32_t *d_seg_offsets; /* VBCRS only */
 } fe_matrix;
 
 /* Sizes of the problem nx x ny x nz (all >= 1). */
@@ -165,6 +177,23 @@ fe_status fe_sliced_plan(int32_t format, int64_t n_rows, int64_t n_cols,
  * to value_type (round to nearest even). */
 fe_status fe_convert(const fe_matrix *src_csr, const fe_matrix *dst, fe_stream_t stream);
 
+/*
+ * The paper's BCRS (Sec. 3.1) from a CSR matrix with sorted columns: a new
+ * segment starts at the first entry of a row and wherever a column is not the
+ * previous column + 1.  fe_vbcrs_plan writes the segment row pointer
+ * d_seg_ptr[n_rows+1] and the segment count to *h_nns (synchronises
+ * `stream`; d_work: fe_vbcrs_workspace() bytes of scratch, 8-byte aligned);
+ * fe_vbcrs_fill then writes d_jas[nns] and d_seg_offsets[nns+1].  The value
+ * array is the CSR one (or a rounded copy of it, fe_round_values): the VBCRS
+ * descriptor points at it.  Errors: FE_ERR_ARG (not CSR, null or misaligned
+ * pointers), FE_ERR_WORKSPACE, FE_ERR_OVERFLOW (nns above int32).
+ */
+fe_status fe_vbcrs_workspace(int64_t n_rows, size_t *h_bytes);
+fe_status fe_vbcrs_plan(const fe_matrix *csr, int32_t *d_seg_ptr, void *d_work, size_t work_bytes,
+                        int64_t *h_nns, fe_stream_t stream);
+fe_status fe_vbcrs_fill(const fe_matrix *csr, const int32_t *d_seg_ptr, int32_t *d_jas,
+                        int32_t *d_seg_offsets, fe_stream_t stream);
+
 /* Round an FP64 array to value_type (FE_VAL_F32 or FE_VAL_BF16), nearest even:
  * a CSR copy of the matrix with lower-precision values. */
 fe_status fe_round_values(int64_t n, const double *d_src, int32_t value_type, void *d_dst,
@@ -186,8 +215,9 @@ typedef struct fe_cg_result {
     double bnorm;        /* ||b|| */
 } fe_cg_result;
 
-/* Workspace of fe_cg_solve for matrix A: three vectors (r, p, w) of
- * 32 * n_slices doubles plus the reduction and barrier block (about 64 KiB). */
+/* Workspace of fe_cg_solve and fe_cg_solve_form for matrix A: four vectors
+ * (r, w and two p buffers) of 32 * n_slices doubles plus the reduction and
+ * barrier block (about 128 KiB). */
 fe_status fe_cg_workspace(const fe_matrix *A, size_t *h_bytes);
 
 /*
@@ -207,6 +237,41 @@ fe_status fe_cg_workspace(const fe_matrix *A, size_t *h_bytes);
 fe_status fe_cg_solve(const fe_matrix *A, const double *d_b, double *d_x, double tol, int maxit,
                       double timeout_s, void *d_work, size_t work_bytes,
                       fe_cg_result *h_result, fe_stream_t stream);
+
+/*
+ * fe_cg_solve with the kernel form chosen by the caller (paper Sec. 1, the
+ * same CG iteration; the forms differ only in how a step is cut into grid
+ * phases).  fe_cg_solve is this call with FE_CG_AUTO.
+ *   FE_CG_THREE_PHASE: SpMV with p.w; r update with r.r; x and p update --
+ *     three grid barriers per step, no work repeated.
+ *   FE_CG_TWO_PHASE: the x and p update of a step is folded into the next
+ *     step's SpMV (p = r + beta p_old formed at every gathered column, p
+ *     double-buffered) -- two barriers per step, one more FMA and two vector
+ *     loads per stored entry; for meshes whose step time is set by barrier
+ *     latency.
+ *   FE_CG_RESIDENT: the two-phase step with the matrix held in registers:
+ *     for FP64 BCRS3 or sliced-ELL matrices of at most SMs * 8 slices (one
+ *     slice per warp, one block of 8 warps per SM; 38,912 rows on 152 SMs),
+ *     each warp loads its slice's entries once and keeps its rows' x, r, p
+ *     and w in registers for the whole solve (x is stored once, at the end);
+ *     for matrices that do not qualify: FE_ERR_ARG.
+ *   FE_CG_AUTO: the resident form when A qualifies, else the two-phase form
+ *     while the grid holds at most one 32-row slice per warp
+ *     (n_slices <= SMs * 4 * 8), else the three-phase form.
+ *   The three- and two-phase forms perform the same floating-point operations
+ *   in the same order and return identical bits; the resident form sums the
+ *   dot products' per-thread partials per row instead of per 16-byte pack,
+ *   so its bits can differ in the last place.  Other form values:
+ *   FE_ERR_ARG.  Arguments, workspace, result and errors otherwise as
+ *   fe_cg_solve.
+ */
+#define FE_CG_AUTO 0
+#define FE_CG_THREE_PHASE 1
+#define FE_CG_TWO_PHASE 2
+#define FE_CG_RESIDENT 3
+fe_status fe_cg_solve_form(const fe_matrix *A, const double *d_b, double *d_x, double tol, int maxit,
+                           double timeout_s, int form, void *d_work, size_t work_bytes,
+                           fe_cg_result *h_result, fe_stream_t stream);
 
 /* Workspace of fe_cg_solve_sr: four vectors (r, p, w, s) of 32 * n_slices
  * doubles plus the reduction and barrier block. */
@@ -292,7 +357,7 @@ fe_status fe_cg_solve_mixed(const fe_matrix *A64, const fe_matrix *A_lo, const d
  * framework owns all device memory).  The paper has no counterpart: this is
  * a packaging variant of the same solve.
  *   The solver's scratch comes from a fixed array inside the library (about
- *   6.4 MB, held on every GPU that loads the library until the process
+ *   8.5 MB, held on every GPU that loads the library until the process
  *   exits), so A may have at most FE_NOALLOC_MAX_ROWS rows (32 * n_slices <=
  *   FE_NOALLOC_MAX_ROWS, e.g. meshes up to 63 x 63 x 63 elements); larger A
  *   returns FE_ERR_WORKSPACE before anything is enqueued.
@@ -446,6 +511,17 @@ fe_status fe_nn_corr_workspace(int stride, int ca, const int *h_dims_a, int cb, 
 fe_status fe_nn_conv3d_weight_grad(int mode, const float *d_x, int cin, const int *h_dims_in,
                                    const float *d_dy, int cout, const int *h_dims_out, float *d_dw,
                                    float *d_work, size_t work_bytes, fe_stream_t stream);
+/* The same weight gradient on the tensor cores (tcgen05): per tap a GEMM over
+ * the voxels, operands rounded to BF16 (nearest even), FP32 accumulation in
+ * tensor memory, per-block partials (d_work: fe_nn_wgrad_tc_workspace()
+ * bytes) summed in a fixed order.  The channels of the layer's input (S1,
+ * S2) or output (T2) must be 16, 32 or 64, the others at most 128; other
+ * shapes: FE_ERR_ARG (the CUDA-core fe_nn_conv3d_weight_grad takes them). */
+fe_status fe_nn_wgrad_tc_workspace(int mode, int cin, const int *h_dims_in, int cout, const int *h_dims_out,
+                                   size_t *h_bytes);
+fe_status fe_nn_conv3d_weight_grad_tc(int mode, const float *d_x, int cin, const int *h_dims_in,
+                                      const float *d_dy, int cout, const int *h_dims_out, float *d_dw,
+                                      float *d_work, size_t work_bytes, fe_stream_t stream);
 /* db[c] = sum over the volume of dY[c] (bias gradient), fixed order. */
 fe_status fe_nn_channel_sum(const float *d_dy, int c, const int *h_dims, float *d_db,
                             fe_stream_t stream);

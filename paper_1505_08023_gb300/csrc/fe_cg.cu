@@ -138,9 +138,147 @@ __global__ void __launch_bounds__(kCgThreads, cg_min_blocks<FMT>()) k_cg(const C
     }
 }
 
+// Two-phase form of the same iteration, for meshes small enough that the
+// grid barriers, not the matrix stream, set the step time.  Phase C of k_cg
+// (x += alpha p, p = r + beta p) moves into the next step's SpMV: every
+// gathered operand value is formed where it is read, p_k[j] = beta p_{k-1}[j]
+// + r[j] (one FMA, the same rounding for every reader), the warp owning row i
+// also stores p_k[i] and applies x_i += alpha_{k-1} p_{k-1}[i].  p is double-
+// buffered (p_k goes to pbuf[k & 1] while other warps still gather p_{k-1}
+// from the other buffer), so a step is
+//   A  w = A p_k (operand formed on the fly), p_k.w; x and p for own rows
+//   B  r -= alpha w, r.r
+// with two grid reductions and no third barrier.  Every value is computed by
+// the same operations in the same order as in k_cg, so both forms give
+// identical bits; this one reads r and p_{k-1} at each gathered column and
+// does one more FMA there, which costs more than a barrier once the FP64
+// pipe, not latency, bounds the step.
+template <int FMT, class VT>
+__global__ void __launch_bounds__(kCgThreads, cg_min_blocks<FMT>()) k_cg2(const CgArgs<double> a) {
+    __shared__ CgBlockState st;
+    __shared__ double coef[2];           // alpha of the last step, beta
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int m = (int)a.A.n_rows, ns = (int)a.A.n_slices;
+    const int tw = gridDim.x * kCgWarps;
+    if (threadIdx.x == 0) {
+        st.target = 0;
+        st.round = 0;
+        st.k = 0;
+        st.ok = 1;
+        coef[0] = coef[1] = 0.0;
+    }
+    __syncthreads();
+    int status = FE_ERR_MAXIT;
+    bool alive = true;
+    // r = b - A x; pbuf[1] = r stands for p_{-1}, so that step 0 forms
+    // p_0 = 0 * r + r = r and applies x += 0 * r
+    {
+        double s0 = 0.0, s1 = 0.0;
+        for (int s = blockIdx.x * kCgWarps + warp; s < ns; s += tw) {
+            double ax = 0.0;
+            if (!a.x0_zero) ax = slice_spmv<FMT, VT, double, double, false>(a.A, s, lane, a.x);
+            const int row = s * kSlice + lane;
+            if (row < m) {
+                const double bi = a.b[row];
+                const double ri = bi - ax;
+                if (a.x0_zero) a.x[row] = 0.0;
+                a.r[row] = ri;
+                a.p2[row] = ri;
+                s0 = fma(ri, ri, s0);
+                s1 = fma(bi, bi, s1);
+            }
+        }
+        double rr0, bb0;
+        alive = grid_sum2(a, &st, s0, s1, rr0, bb0);
+        if (threadIdx.x == 0) {
+            st.rr = rr0;
+            st.bb = bb0;
+        }
+        __syncthreads();
+    }
+    if (alive && st.bb == 0.0) {  // b = 0: the solution is 0
+        for (int s = blockIdx.x * kCgWarps + warp; s < ns; s += tw) {
+            const int row = s * kSlice + lane;
+            if (row < m) a.x[row] = 0.0;
+        }
+        if (threadIdx.x == 0) st.rr = 0.0;
+        status = FE_OK;
+    } else {
+        while (alive) {
+            if (st.rr <= a.tol2 * st.bb) { status = FE_OK; break; }
+            if (st.k >= a.maxit) { status = FE_ERR_MAXIT; break; }
+            const int k = st.k;
+            double *pnew = (k & 1) ? a.p2 : a.p;
+            const double *pold = (k & 1) ? a.p : a.p2;
+            const double beta = coef[1], alpha_old = coef[0];
+            // A: p_k = r + beta p_{k-1} formed at every gathered column, w = A p_k, p_k.w;
+            //    own rows: store p_k, x += alpha_{k-1} p_{k-1}
+            const AxpyGather<double> gat{a.r, pold, beta};
+            double pw_part = 0.0;
+            for (int s = blockIdx.x * kCgWarps + warp; s < ns; s += tw) {
+                const double y = slice_spmv_g<FMT, VT, double, double>(a.A, s, lane, gat);
+                const int row = s * kSlice + lane;
+                if (row < m) {
+                    const double po = pold[row];
+                    const double pk = fma(beta, po, a.r[row]);
+                    a.x[row] = fma(alpha_old, po, a.x[row]);
+                    pnew[row] = pk;
+                    a.w[row] = y;
+                    pw_part = fma(pk, y, pw_part);
+                }
+            }
+            double pw, unused;
+            if (!(alive = grid_sum2(a, &st, pw_part, 0.0, pw, unused))) break;
+            if (!(pw > 0.0) || !(pw < INFINITY)) { status = FE_ERR_BREAKDOWN; break; }
+            // B: r -= alpha w, r.r
+            const double alpha = st.rr / pw;
+            const double rr_part = update_r<double>(a.r, a.w, m, alpha);
+            double rr_new;
+            if (!(alive = grid_sum2(a, &st, rr_part, 0.0, rr_new, unused))) break;
+            __syncthreads();                 // every thread has read st.rr and coef
+            if (threadIdx.x == 0) {
+                coef[0] = alpha;
+                coef[1] = rr_new / st.rr;
+                st.rr = rr_new;
+                st.k += 1;
+            }
+            __syncthreads();
+            if (rr_new <= a.tol2 * st.bb) { status = FE_OK; break; }
+            if (st.k >= a.maxit) { status = FE_ERR_MAXIT; break; }
+        }
+    }
+    // the last step's x update: x += alpha_{k-1} p_{k-1}, p_{k-1} in pbuf[(k-1) & 1]
+    if (alive && st.k > 0 && (status == FE_OK || status == FE_ERR_MAXIT)) {
+        const double *plast = ((st.k - 1) & 1) ? a.p2 : a.p;
+        const double al = coef[0];
+        const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+        for (int row = tid; row < m; row += nth) a.x[row] = fma(al, plast[row], a.x[row]);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.ctrl->status = alive ? status : FE_ERR_TIMEOUT;
+        a.ctrl->iterations = st.k;
+        a.ctrl->rr = st.rr;
+        a.ctrl->bb = st.bb;
+    }
+}
+
+// Workspace: control block, reduction partials, then r, p, w and the second
+// p buffer of the two-phase form.
 static size_t cg_workspace_bytes(const fe_matrix &A) {
     const size_t vec = align256((size_t)A.n_slices * kSlice * sizeof(double));
-    return 256 + align256(2 * 2 * (size_t)kCgMaxBlocks * sizeof(double)) + 3 * vec;
+    return 256 + align256(2 * 2 * (size_t)kCgMaxBlocks * sizeof(double)) + 4 * vec;
+}
+
+// FE_CG_AUTO: the matrix-resident kernel when A qualifies (FP64 BCRS3 or
+// sliced-ELL values, at most one slice per warp of one block per SM), else the
+// two-phase form while the whole grid holds at most one slice per warp (every
+// warp's SpMV is one pass of its slice, so the step time is the barriers' and
+// reductions' latency, not the FP64 pipe's), else the three-phase form.
+static int cg_pick_form(const fe_matrix &A, int form) {
+    if (form != FE_CG_AUTO) return form;
+    if (resident_cg_fits(A)) return FE_CG_RESIDENT;
+    const int64_t warps = (int64_t)sm_count() * kCgBlocksPerSm * kCgWarps;
+    return A.n_slices <= warps ? FE_CG_TWO_PHASE : FE_CG_THREE_PHASE;
 }
 
 template <int FMT, class VT, class XT>
@@ -162,6 +300,24 @@ static fe_status launch_cg(const CgArgs<XT> &args, cudaStream_t s) {
 
 template <int FMT, class VT> static fe_status launch_cg64(const CgArgs<double> &a, cudaStream_t s) {
     return launch_cg<FMT, VT, double>(a, s);
+}
+template <int FMT, class VT> static fe_status launch_cg2(const CgArgs<double> &args, cudaStream_t s) {
+    auto kern = k_cg2<FMT, VT>;
+    int per_sm = 0;
+    FE_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kCgThreads, 0));
+    if (per_sm < 1) return FE_ERR_CUDA;
+    int64_t blocks = (int64_t)sm_count() * per_sm;
+    const int64_t need = (args.A.n_slices + kCgWarps - 1) / kCgWarps;
+    if (blocks > need) blocks = need;
+    if (blocks > kCgMaxBlocks) blocks = kCgMaxBlocks;
+    if (blocks < 1) blocks = 1;
+    void *params[] = {(void *)&args};
+    FE_TRY_CUDA(cudaLaunchCooperativeKernel((const void *)kern, dim3((unsigned)blocks), dim3(kCgThreads),
+                                            params, 0, s));
+    return FE_OK;
+}
+static fe_status dispatch_cg2(const CgArgs<double> &args, cudaStream_t s) {
+    FE_DISPATCH_FMT_VT(args.A, launch_cg2, args, s)
 }
 template <int FMT, class VT> static fe_status launch_cg32(const CgArgs<float> &a, cudaStream_t s) {
     return launch_cg<FMT, VT, float>(a, s);
@@ -205,12 +361,16 @@ fe_status fe_cg_workspace(const fe_matrix *A, size_t *h_bytes) {
     return FE_OK;
 }
 
-fe_status fe_cg_solve(const fe_matrix *A, const double *d_b, double *d_x, double tol, int maxit,
-                      double timeout_s, void *d_work, size_t work_bytes, fe_cg_result *h_result,
-                      fe_stream_t stream) {
+fe_status fe_cg_solve_form(const fe_matrix *A, const double *d_b, double *d_x, double tol, int maxit,
+                           double timeout_s, int form, void *d_work, size_t work_bytes,
+                           fe_cg_result *h_result, fe_stream_t stream) {
     fe_status st = check_matrix(A);
     if (st != FE_OK) return st;
     if (!d_b || !d_x || !d_work || !h_result || maxit < 0 || !(tol >= 0.0)) return FE_ERR_ARG;
+    if (form != FE_CG_AUTO && form != FE_CG_THREE_PHASE && form != FE_CG_TWO_PHASE &&
+        form != FE_CG_RESIDENT)
+        return FE_ERR_ARG;
+    if (form == FE_CG_RESIDENT && !resident_cg_fits(*A)) return FE_ERR_ARG;
     if (A->n_rows != A->n_cols) return FE_ERR_ARG;
     if (!aligned(d_b, 16) || !aligned(d_x, 16) || !aligned(d_work, 256)) return FE_ERR_ARG;
     if (work_bytes < cg_workspace_bytes(*A)) return FE_ERR_WORKSPACE;
@@ -228,6 +388,7 @@ fe_status fe_cg_solve(const fe_matrix *A, const double *d_b, double *d_x, double
     args.r = (double *)v0;
     args.p = (double *)(v0 + vec);
     args.w = (double *)(v0 + 2 * vec);
+    args.p2 = (double *)(v0 + 3 * vec);
     args.tol2 = tol * tol;
     args.maxit = maxit;
     const double tmo = timeout_s > 0.0 ? timeout_s : 2.0;
@@ -237,7 +398,14 @@ fe_status fe_cg_solve(const fe_matrix *A, const double *d_b, double *d_x, double
     args.x64 = nullptr;
 
     FE_TRY_CUDA(cudaMemsetAsync(args.ctrl, 0, sizeof(CgCtrl), s));
-    st = dispatch_cg(args, s);
+    const int pick = cg_pick_form(*A, form);
+    bool taken = false;
+    if (pick == FE_CG_RESIDENT) {
+        st = launch_cg_resident(args, s, &taken);
+        if (st != FE_OK) return st;
+        if (!taken && form == FE_CG_RESIDENT) return FE_ERR_ARG;
+    }
+    if (!taken) st = (pick == FE_CG_THREE_PHASE) ? dispatch_cg(args, s) : dispatch_cg2(args, s);
     if (st != FE_OK) return st;
     CgCtrl ctrl;
     FE_TRY_CUDA(cudaMemcpyAsync(&ctrl, args.ctrl, sizeof(CgCtrl), cudaMemcpyDeviceToHost, s));
@@ -247,6 +415,13 @@ fe_status fe_cg_solve(const fe_matrix *A, const double *d_b, double *d_x, double
     h_result->bnorm = sqrt(ctrl.bb);
     h_result->relres = ctrl.bb > 0.0 ? sqrt(ctrl.rr / ctrl.bb) : 0.0;
     return (fe_status)ctrl.status;
+}
+
+fe_status fe_cg_solve(const fe_matrix *A, const double *d_b, double *d_x, double tol, int maxit,
+                      double timeout_s, void *d_work, size_t work_bytes, fe_cg_result *h_result,
+                      fe_stream_t stream) {
+    return fe_cg_solve_form(A, d_b, d_x, tol, maxit, timeout_s, FE_CG_AUTO, d_work, work_bytes,
+                            h_result, stream);
 }
 
 fe_status fe_true_relres(const fe_matrix *A, const double *d_b, const double *d_x, void *d_work,
@@ -291,7 +466,7 @@ namespace fe {
 
 constexpr size_t kNoallocVecBytes = ((size_t)FE_NOALLOC_MAX_ROWS * sizeof(double) + 255) & ~(size_t)255;
 constexpr size_t kNoallocBytes =
-    256 + ((2 * 2 * (size_t)kCgMaxBlocks * sizeof(double) + 255) & ~(size_t)255) + 3 * kNoallocVecBytes;
+    256 + ((2 * 2 * (size_t)kCgMaxBlocks * sizeof(double) + 255) & ~(size_t)255) + 4 * kNoallocVecBytes;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
 

@@ -16,7 +16,9 @@ constexpr int kCgBlocksPerSm = 4;
 // Resident blocks the persistent kernels are compiled for: the CSR slice
 // kernel keeps seven entries per lane in flight, which needs more than the
 // 64 registers of four blocks per SM.
-template <int FMT> constexpr int cg_min_blocks() { return FMT == FE_FMT_CSR ? 3 : kCgBlocksPerSm; }
+template <int FMT> constexpr int cg_min_blocks() {
+    return (FMT == FE_FMT_CSR || FMT == FE_FMT_VBCRS) ? 3 : kCgBlocksPerSm;
+}
 constexpr unsigned kMaxPolls = 1u << 28;
 
 struct CgCtrl {
@@ -41,6 +43,7 @@ template <class XT> struct CgArgs {
     long long timeout_ns;
     long long stall_barrier;  // fault injection: block 0 skips this arrival (-1: none)
     double *x64;             // if set: x64 += x on exit (mixed-precision refinement step)
+    XT *p2;                  // second p buffer of the two-phase form (k_cg2)
 };
 
 __device__ __forceinline__ long long global_ns() {
@@ -131,11 +134,23 @@ __device__ __forceinline__ bool grid_sum2(const Args &a, CgBlockState *st, doubl
     // from the previous reduction before warp 0 overwrites it below
     if (!grid_barrier(a.ctrl, st, a.timeout_ns, a.stall_barrier)) return false;
     if (warp == 0) {
+        // lane-strided partials, four loads in flight per lane (a loop of one
+        // dependent load per trip costs an L2 round trip per 32 blocks); the
+        // additions keep the order i, i + 32, i + 64, ...
         double t0 = 0.0, t1 = 0.0;
-        for (unsigned i = lane; i < gridDim.x; i += 32) {
-            const double2 v = __ldcg(part + i);
-            t0 += v.x;
-            t1 += v.y;
+        const unsigned G = gridDim.x;
+        for (unsigned i = lane; i < G; i += 128) {
+            double2 v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                v[u] = (i + 32 * u < G) ? __ldcg(part + i + 32 * u) : make_double2(0.0, 0.0);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (i + 32 * u < G) {
+                    t0 += v[u].x;
+                    t1 += v[u].y;
+                }
+            }
         }
         t0 = warp_sum(t0);
         t1 = warp_sum(t1);
@@ -394,6 +409,9 @@ static fe_status launch_resid(const fe_matrix &A, const double *b, const double 
         case FE_FMT_BCRS3 * 3 + FE_VAL_F64: return FN<FE_FMT_BCRS3, double>(__VA_ARGS__);   \
         case FE_FMT_BCRS3 * 3 + FE_VAL_F32: return FN<FE_FMT_BCRS3, float>(__VA_ARGS__);    \
         case FE_FMT_BCRS3 * 3 + FE_VAL_BF16: return FN<FE_FMT_BCRS3, __nv_bfloat16>(__VA_ARGS__); \
+        case FE_FMT_VBCRS * 3 + FE_VAL_F64: return FN<FE_FMT_VBCRS, double>(__VA_ARGS__);   \
+        case FE_FMT_VBCRS * 3 + FE_VAL_F32: return FN<FE_FMT_VBCRS, float>(__VA_ARGS__);    \
+        case FE_FMT_VBCRS * 3 + FE_VAL_BF16: return FN<FE_FMT_VBCRS, __nv_bfloat16>(__VA_ARGS__); \
         default: return FE_ERR_ARG;                                                        \
     }
 
@@ -406,6 +424,12 @@ static inline fe_status dispatch_resid(const fe_matrix &A, const double *b, cons
 // Launch of the FP32-vector CG kernel (defined in fe_cg.cu): the inner solver
 // of the restarted mixed-precision mode.
 fe_status launch_cg_f32(const CgArgs<float> &args, cudaStream_t s);
+
+// The matrix-resident CG kernel (fe_cg_resident.cu): whether A qualifies (FP64
+// BCRS3 or sliced-ELL values, at most one slice per warp of one block per SM),
+// and its launch; *taken is false when the grid would not be co-resident.
+bool resident_cg_fits(const fe_matrix &A);
+fe_status launch_cg_resident(const CgArgs<double> &args, cudaStream_t s, bool *taken);
 
 // Barrier index armed by fe_inject_barrier_stall (test hook), consumed by the
 // next solve that takes it (-1: none).  Defined in fe_cg.cu.

@@ -34,6 +34,11 @@ fe_status check_matrix(const fe_matrix *A);
 // Number of SMs of the current device (cached per device).
 int sm_count();
 
+// Weight-gradient partials part[split][a][b][t] summed in split order into
+// dW[ci][t][co] (a = co and b = ci when a_is_co, else the reverse); fe_nn.cu.
+fe_status launch_corr_reduce(const float *part, int n_split, int ca, int cb, int a_is_co, float *dw,
+                             cudaStream_t s);
+
 // ---------------------------------------------------------------- device loads
 
 // Matrix streams are read once per pass and are far larger than L2: load them
@@ -75,11 +80,23 @@ __device__ __forceinline__ int warp_max(int v) {
 
 // ---------------------------------------------------------------- slice SpMV
 
+// Operand gathers of the slice SpMV: x[j] from a stored vector, or an operand
+// formed on the fly from two vectors (the fused CG step's p = r + beta p_old,
+// computed where it is gathered, so that no pass stores p before the SpMV).
+template <bool kReadOnly, class XT> struct PtrGather {
+    const XT *x;
+    __device__ __forceinline__ XT operator()(int64_t j) const { return ld_vec<kReadOnly>(x + j); }
+};
+template <class XT> struct AxpyGather {   // beta * pold[j] + r[j], one rounding (FMA)
+    const XT *r, *pold;
+    XT beta;
+    __device__ __forceinline__ XT operator()(int64_t j) const { return fma(beta, pold[j], r[j]); }
+};
+
 // One warp computes the 32 rows of slice s; returns lane's row sum (0 for
 // rows past the end).  XT: vector type, AT: accumulation type.
-template <class VT, class XT, class AT, bool kReadOnlyX>
-__device__ __forceinline__ AT slice_spmv_sell(const fe_matrix &A, int64_t s, int lane,
-                                              const XT *x) {
+template <class VT, class XT, class AT, class G>
+__device__ __forceinline__ AT slice_spmv_sell(const fe_matrix &A, int64_t s, int lane, const G &x) {
     const int64_t b = A.d_slice_ptr[s];
     const int w = (int)((A.d_slice_ptr[s + 1] - b) >> 5);
     const int32_t *c = A.d_cols + b + lane;
@@ -97,21 +114,20 @@ __device__ __forceinline__ AT slice_spmv_sell(const fe_matrix &A, int64_t s, int
         }
         XT xx[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) xx[u] = ld_vec<kReadOnlyX>(x + cc[u]);
+        for (int u = 0; u < U; ++u) xx[u] = x(cc[u]);
 #pragma unroll
         for (int u = 0; u < U; ++u) acc = fma(to_acc<AT>(vv[u]), (AT)xx[u], acc);
     }
     for (; k < w; ++k) {
         int32_t cc = ld_stream(c + 32 * k);
         VT vv = ld_stream(v + 32 * k);
-        acc = fma(to_acc<AT>(vv), (AT)ld_vec<kReadOnlyX>(x + cc), acc);
+        acc = fma(to_acc<AT>(vv), (AT)x(cc), acc);
     }
     return acc;
 }
 
-template <class VT, class XT, class AT, bool kReadOnlyX>
-__device__ __forceinline__ AT slice_spmv_bcrs3(const fe_matrix &A, int64_t s, int lane,
-                                               const XT *x) {
+template <class VT, class XT, class AT, class G>
+__device__ __forceinline__ AT slice_spmv_bcrs3(const fe_matrix &A, int64_t s, int lane, const G &x) {
     const int64_t b = A.d_slice_ptr[s];
     const int w = (int)((A.d_slice_ptr[s + 1] - b) >> 5);
     const int32_t *c = A.d_cols + b + lane;
@@ -132,7 +148,7 @@ __device__ __forceinline__ AT slice_spmv_bcrs3(const fe_matrix &A, int64_t s, in
 #pragma unroll
         for (int u = 0; u < U; ++u)
 #pragma unroll
-            for (int t = 0; t < 3; ++t) xx[u][t] = ld_vec<kReadOnlyX>(x + jj[u] + t);
+            for (int t = 0; t < 3; ++t) xx[u][t] = x((int64_t)jj[u] + t);
 #pragma unroll
         for (int u = 0; u < U; ++u)
 #pragma unroll
@@ -143,7 +159,7 @@ __device__ __forceinline__ AT slice_spmv_bcrs3(const fe_matrix &A, int64_t s, in
 #pragma unroll
         for (int t = 0; t < 3; ++t)
             acc = fma(to_acc<AT>(ld_stream(v + 96 * k + 32 * t)),
-                      (AT)ld_vec<kReadOnlyX>(x + j + t), acc);
+                      (AT)x((int64_t)j + t), acc);
     }
     return acc;
 }
@@ -156,9 +172,8 @@ __device__ __forceinline__ AT slice_spmv_bcrs3(const fe_matrix &A, int64_t s, in
 // a fixed transpose-reduce (xor 1 then xor 2: three adds per lane) and one
 // shuffle hands each row's sum to the lane of that row.  The order of every
 // addition is fixed, so results are bitwise repeatable.
-template <class VT, class XT, class AT, bool kReadOnlyX>
-__device__ __forceinline__ AT slice_spmv_csr(const fe_matrix &A, int64_t s, int lane,
-                                             const XT *x) {
+template <class VT, class XT, class AT, class G>
+__device__ __forceinline__ AT slice_spmv_csr(const fe_matrix &A, int64_t s, int lane, const G &x) {
     const int g = lane >> 2, j = lane & 3;
     const int64_t r0 = s * kSlice;
     const int64_t nrows = A.n_rows;
@@ -183,7 +198,7 @@ __device__ __forceinline__ AT slice_spmv_csr(const fe_matrix &A, int64_t s, int 
                 }
                 XT xx[7];
 #pragma unroll
-                for (int u = 0; u < 7; ++u) xx[u] = (k + 4 * u < hi) ? ld_vec<kReadOnlyX>(x + c[u]) : XT(0);
+                for (int u = 0; u < 7; ++u) xx[u] = (k + 4 * u < hi) ? x(c[u]) : XT(0);
 #pragma unroll
                 for (int u = 0; u < 7; ++u) acc = fma(to_acc<AT>(v[u]), (AT)xx[u], acc);
             }
@@ -205,11 +220,83 @@ __device__ __forceinline__ AT slice_spmv_csr(const fe_matrix &A, int64_t s, int 
     return __shfl_sync(0xffffffffu, row_sum, src);
 }
 
+// The paper's BCRS (FE_FMT_VBCRS): the CSR kernel's layout -- four lanes per
+// row, eight rows per pass, four passes per 32-row slice -- with a lane
+// taking whole segments: lane j of a row's group runs segments lo + j,
+// lo + j + 4, lo + j + 8 (a 27-point row has at most nine), reading each
+// segment's first column and value offset and its (up to three, then a loop)
+// values, which are contiguous in the CSR value array.  Every load of a trip
+// is issued before the first FMA; the four lane partials of a row are then
+// combined by the same fixed transpose-reduce as the CSR kernel.
+template <class VT, class XT, class AT, class G>
+__device__ __forceinline__ AT slice_spmv_vbcrs(const fe_matrix &A, int64_t s, int lane, const G &x) {
+    constexpr int S = 2, L = 3;       // segments per lane per trip, values unrolled per segment
+    const int g = lane >> 2, j = lane & 3;
+    const int64_t r0 = s * kSlice;
+    const int64_t nrows = A.n_rows;
+    const VT *vals = reinterpret_cast<const VT *>(A.d_vals);
+    const int32_t *seg_ptr = A.d_row_ptr, *jas = A.d_cols, *off = A.d_seg_offsets;
+    AT part[4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        const int64_t row = r0 + 8 * p + g;
+        AT acc = AT(0);
+        if (row < nrows) {
+            const int32_t lo = seg_ptr[row], hi = seg_ptr[row + 1];
+            for (int32_t q = lo + j; q < hi; q += 4 * S) {
+                int32_t c[S], o[S], len[S];
+#pragma unroll
+                for (int u = 0; u < S; ++u) {
+                    const bool ok = q + 4 * u < hi;
+                    c[u] = ok ? ld_stream(jas + q + 4 * u) : 0;
+                    o[u] = ok ? ld_stream(off + q + 4 * u) : 0;
+                    len[u] = ok ? ld_stream(off + q + 4 * u + 1) - o[u] : 0;
+                }
+                VT v[S][L];
+                XT xx[S][L];
+#pragma unroll
+                for (int u = 0; u < S; ++u)
+#pragma unroll
+                    for (int t = 0; t < L; ++t) {
+                        const bool ok = t < len[u];
+                        v[u][t] = ok ? ld_stream(vals + o[u] + t) : VT(0);
+                        xx[u][t] = ok ? x((int64_t)c[u] + t) : XT(0);
+                    }
+#pragma unroll
+                for (int u = 0; u < S; ++u) {
+#pragma unroll
+                    for (int t = 0; t < L; ++t)
+                        if (t < len[u]) acc = fma(to_acc<AT>(v[u][t]), (AT)xx[u][t], acc);
+                    for (int t = L; t < len[u]; ++t)       // runs longer than three
+                        acc = fma(to_acc<AT>(ld_stream(vals + o[u] + t)), (AT)x((int64_t)c[u] + t), acc);
+                }
+            }
+        }
+        part[p] = acc;
+    }
+    const int b = j & 1, h = (j >> 1) & 1;
+    const AT s0 = __shfl_xor_sync(0xffffffffu, b ? part[0] : part[2], 1);
+    const AT s1 = __shfl_xor_sync(0xffffffffu, b ? part[1] : part[3], 1);
+    const AT k0 = (b ? part[2] : part[0]) + s0;
+    const AT k1 = (b ? part[3] : part[1]) + s1;
+    const AT t = __shfl_xor_sync(0xffffffffu, h ? k0 : k1, 2);
+    const AT row_sum = (h ? k1 : k0) + t;
+    const int qq = lane >> 3;
+    const int src = 4 * (lane & 7) + ((qq & 1) << 1) + (qq >> 1);
+    return __shfl_sync(0xffffffffu, row_sum, src);
+}
+
+template <int FMT, class VT, class XT, class AT, class G>
+__device__ __forceinline__ AT slice_spmv_g(const fe_matrix &A, int64_t s, int lane, const G &x) {
+    if constexpr (FMT == FE_FMT_CSR) return slice_spmv_csr<VT, XT, AT>(A, s, lane, x);
+    else if constexpr (FMT == FE_FMT_VBCRS) return slice_spmv_vbcrs<VT, XT, AT>(A, s, lane, x);
+    else if constexpr (FMT == FE_FMT_SELL) return slice_spmv_sell<VT, XT, AT>(A, s, lane, x);
+    else return slice_spmv_bcrs3<VT, XT, AT>(A, s, lane, x);
+}
+
 template <int FMT, class VT, class XT, class AT, bool kReadOnlyX>
 __device__ __forceinline__ AT slice_spmv(const fe_matrix &A, int64_t s, int lane, const XT *x) {
-    if constexpr (FMT == FE_FMT_CSR) return slice_spmv_csr<VT, XT, AT, kReadOnlyX>(A, s, lane, x);
-    else if constexpr (FMT == FE_FMT_SELL) return slice_spmv_sell<VT, XT, AT, kReadOnlyX>(A, s, lane, x);
-    else return slice_spmv_bcrs3<VT, XT, AT, kReadOnlyX>(A, s, lane, x);
+    return slice_spmv_g<FMT, VT, XT, AT>(A, s, lane, PtrGather<kReadOnlyX, XT>{x});
 }
 
 }  // namespace fe

@@ -42,6 +42,10 @@ fe_status check_matrix(const fe_matrix *A) {
         case FE_FMT_BCRS3:
             if (A->d_slice_ptr == nullptr || A->n_cols < 3) return FE_ERR_ARG;
             break;
+        case FE_FMT_VBCRS:
+            if (A->d_row_ptr == nullptr || A->d_seg_offsets == nullptr || A->n_stored > INT32_MAX)
+                return FE_ERR_ARG;
+            break;
         default:
             return FE_ERR_ARG;
     }

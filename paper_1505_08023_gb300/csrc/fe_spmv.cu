@@ -50,6 +50,9 @@ static fe_status dispatch(const fe_matrix *A, const XT *x, XT *y, fe_stream_t st
         case FE_FMT_BCRS3 * 3 + FE_VAL_F64: return launch<FE_FMT_BCRS3, double, XT, AT>(*A, x, y, s);
         case FE_FMT_BCRS3 * 3 + FE_VAL_F32: return launch<FE_FMT_BCRS3, float, XT, AT>(*A, x, y, s);
         case FE_FMT_BCRS3 * 3 + FE_VAL_BF16: return launch<FE_FMT_BCRS3, __nv_bfloat16, XT, AT>(*A, x, y, s);
+        case FE_FMT_VBCRS * 3 + FE_VAL_F64: return launch<FE_FMT_VBCRS, double, XT, AT>(*A, x, y, s);
+        case FE_FMT_VBCRS * 3 + FE_VAL_F32: return launch<FE_FMT_VBCRS, float, XT, AT>(*A, x, y, s);
+        case FE_FMT_VBCRS * 3 + FE_VAL_BF16: return launch<FE_FMT_VBCRS, __nv_bfloat16, XT, AT>(*A, x, y, s);
         default: return FE_ERR_ARG;
     }
 }

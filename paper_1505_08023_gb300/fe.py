@@ -25,8 +25,8 @@ STATUS_NAMES = {0: "FE_OK", -1: "FE_ERR_ARG", -2: "FE_ERR_OVERFLOW", -3: "FE_ERR
                 -4: "FE_ERR_BREAKDOWN", -5: "FE_ERR_MAXIT", -6: "FE_ERR_TIMEOUT",
                 -7: "FE_ERR_WORKSPACE"}
 
-FE_FMT_CSR, FE_FMT_SELL, FE_FMT_BCRS3 = 0, 1, 2
-FORMATS = {"csr": FE_FMT_CSR, "sell": FE_FMT_SELL, "bcrs3": FE_FMT_BCRS3}
+FE_FMT_CSR, FE_FMT_SELL, FE_FMT_BCRS3, FE_FMT_VBCRS = 0, 1, 2, 3
+FORMATS = {"csr": FE_FMT_CSR, "sell": FE_FMT_SELL, "bcrs3": FE_FMT_BCRS3, "vbcrs": FE_FMT_VBCRS}
 FE_VAL_F64, FE_VAL_F32, FE_VAL_BF16 = 0, 1, 2
 VALUE_TYPES = {"f64": FE_VAL_F64, "f32": FE_VAL_F32, "bf16": FE_VAL_BF16}
 TORCH_VALUE = {FE_VAL_F64: torch.float64, FE_VAL_F32: torch.float32, FE_VAL_BF16: torch.bfloat16}
@@ -53,7 +53,8 @@ class fe_matrix(ctypes.Structure):
                 ("n_rows", ctypes.c_int64), ("n_cols", ctypes.c_int64),
                 ("n_slices", ctypes.c_int64), ("n_stored", ctypes.c_int64),
                 ("d_row_ptr", ctypes.c_void_p), ("d_slice_ptr", ctypes.c_void_p),
-                ("d_cols", ctypes.c_void_p), ("d_vals", ctypes.c_void_p)]
+                ("d_cols", ctypes.c_void_p), ("d_vals", ctypes.c_void_p),
+                ("d_seg_offsets", ctypes.c_void_p)]
 
 
 class fe_cg_result(ctypes.Structure):
@@ -90,12 +91,17 @@ SIGNATURES = {
                                _VP, _VP, _VP, _SZ, _VP]),
     "fe_sliced_plan": (_I32, [_I32, _I64, _I64, _VP, _VP, _VP, ctypes.POINTER(_I64), _VP]),
     "fe_convert": (_I32, [ctypes.POINTER(fe_matrix), ctypes.POINTER(fe_matrix), _VP]),
+    "fe_vbcrs_workspace": (_I32, [_I64, ctypes.POINTER(_SZ)]),
+    "fe_vbcrs_plan": (_I32, [ctypes.POINTER(fe_matrix), _VP, _VP, _SZ, ctypes.POINTER(_I64), _VP]),
+    "fe_vbcrs_fill": (_I32, [ctypes.POINTER(fe_matrix), _VP, _VP, _VP, _VP]),
     "fe_round_values": (_I32, [_I64, _VP, _I32, _VP, _VP]),
     "fe_spmv": (_I32, [ctypes.POINTER(fe_matrix), _VP, _VP, _VP]),
     "fe_spmv_f32": (_I32, [ctypes.POINTER(fe_matrix), _VP, _VP, _VP]),
     "fe_cg_workspace": (_I32, [ctypes.POINTER(fe_matrix), ctypes.POINTER(_SZ)]),
     "fe_cg_solve": (_I32, [ctypes.POINTER(fe_matrix), _VP, _VP, _D, ctypes.c_int, _D, _VP, _SZ,
                            ctypes.POINTER(fe_cg_result), _VP]),
+    "fe_cg_solve_form": (_I32, [ctypes.POINTER(fe_matrix), _VP, _VP, _D, ctypes.c_int, _D,
+                                ctypes.c_int, _VP, _SZ, ctypes.POINTER(fe_cg_result), _VP]),
     "fe_cg_sr_workspace": (_I32, [ctypes.POINTER(fe_matrix), ctypes.POINTER(_SZ)]),
     "fe_cg_solve_sr": (_I32, [ctypes.POINTER(fe_matrix), _VP, _VP, _D, ctypes.c_int, _D, _VP, _SZ,
                               ctypes.POINTER(fe_cg_result), _VP]),
@@ -147,6 +153,10 @@ SIGNATURES = {
                                     ctypes.POINTER(_SZ), ctypes.POINTER(ctypes.c_int)]),
     "fe_nn_conv3d_weight_grad": (_I32, [ctypes.c_int, _VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _VP,
                                         ctypes.c_int, ctypes.POINTER(ctypes.c_int), _VP, _VP, _SZ, _VP]),
+    "fe_nn_wgrad_tc_workspace": (_I32, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
+                                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_SZ)]),
+    "fe_nn_conv3d_weight_grad_tc": (_I32, [ctypes.c_int, _VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _VP,
+                                           ctypes.c_int, ctypes.POINTER(ctypes.c_int), _VP, _VP, _SZ, _VP]),
     "fe_nn_channel_sum": (_I32, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _VP, _VP]),
     "fe_nn_relu_bwd": (_I32, [_VP, _VP, _SZ, _VP]),
     "fe_nn_axpy": (_I32, [ctypes.c_float, _VP, _VP, _SZ, _VP]),
@@ -240,6 +250,25 @@ def fe_sliced_plan(fmt, n_rows, n_cols, row_ptr, cols, slice_ptr, stream=None) -
     return n.value
 
 
+def fe_vbcrs_workspace(n_rows: int) -> int:
+    n = ctypes.c_size_t(0)
+    _check("fe_vbcrs_workspace", load().fe_vbcrs_workspace(int(n_rows), ctypes.byref(n)))
+    return n.value
+
+
+def fe_vbcrs_plan(csr: fe_matrix, seg_ptr, work, stream=None) -> int:
+    n = ctypes.c_int64(0)
+    _check("fe_vbcrs_plan", load().fe_vbcrs_plan(ctypes.byref(csr), _ptr(seg_ptr), _ptr(work),
+                                                 work.numel() * work.element_size(), ctypes.byref(n),
+                                                 _stream(stream)))
+    return n.value
+
+
+def fe_vbcrs_fill(csr: fe_matrix, seg_ptr, jas, seg_offsets, stream=None):
+    return _check("fe_vbcrs_fill", load().fe_vbcrs_fill(ctypes.byref(csr), _ptr(seg_ptr), _ptr(jas),
+                                                        _ptr(seg_offsets), _stream(stream)))
+
+
 def fe_convert(src: fe_matrix, dst: fe_matrix, stream=None):
     return _check("fe_convert", load().fe_convert(ctypes.byref(src), ctypes.byref(dst),
                                                   _stream(stream)))
@@ -273,6 +302,21 @@ def fe_cg_solve(A: fe_matrix, b, x, tol, maxit, work, timeout_s=0.0, stream=None
                             ctypes.byref(res), _stream(stream))
     if check and st not in (FE_OK,):
         raise FeError("fe_cg_solve", st)
+    return res
+
+
+FE_CG_AUTO, FE_CG_THREE_PHASE, FE_CG_TWO_PHASE, FE_CG_RESIDENT = 0, 1, 2, 3
+
+
+def fe_cg_solve_form(A: fe_matrix, b, x, tol, maxit, form, work, timeout_s=0.0, stream=None,
+                     check=True) -> fe_cg_result:
+    res = fe_cg_result()
+    st = load().fe_cg_solve_form(ctypes.byref(A), _ptr(b), _ptr(x), float(tol), int(maxit),
+                                 float(timeout_s), int(form), _ptr(work),
+                                 work.numel() * work.element_size(), ctypes.byref(res),
+                                 _stream(stream))
+    if check and st not in (FE_OK,):
+        raise FeError("fe_cg_solve_form", st)
     return res
 
 
@@ -594,6 +638,19 @@ def fe_nn_conv3d_weight_grad(mode, x, cin, dims_in, dy, cout, dims_out, dw, work
         _ptr(work), work.numel() * work.element_size(), _stream(stream)))
 
 
+def fe_nn_wgrad_tc_workspace(mode, cin, dims_in, cout, dims_out) -> int:
+    n = ctypes.c_size_t(0)
+    _check("fe_nn_wgrad_tc_workspace", load().fe_nn_wgrad_tc_workspace(
+        int(mode), int(cin), _dims(dims_in), int(cout), _dims(dims_out), ctypes.byref(n)))
+    return n.value
+
+
+def fe_nn_conv3d_weight_grad_tc(mode, x, cin, dims_in, dy, cout, dims_out, dw, work, stream=None):
+    return _check("fe_nn_conv3d_weight_grad_tc", load().fe_nn_conv3d_weight_grad_tc(
+        int(mode), _ptr(x), int(cin), _dims(dims_in), _ptr(dy), int(cout), _dims(dims_out), _ptr(dw),
+        _ptr(work), work.numel() * work.element_size(), _stream(stream)))
+
+
 def fe_nn_channel_sum(dy, c, dims, db, stream=None):
     return _check("fe_nn_channel_sum", load().fe_nn_channel_sum(_ptr(dy), int(c), _dims(dims), _ptr(db),
                                                                 _stream(stream)))
@@ -737,6 +794,21 @@ class System:
             d = fe_matrix(f, vt, self.m, self.m, self.sizes.n_slices, self.sizes.nnz,
                           self.row_ptr.data_ptr(), None, self.cols.data_ptr(), v.data_ptr())
             dm = DeviceMatrix(d, {"row_ptr": self.row_ptr, "cols": self.cols, "vals": v})
+        elif f == FE_FMT_VBCRS:
+            # the paper's BCRS: segment arrays over the CSR values (or a rounded copy)
+            v = self.vals
+            if vt != FE_VAL_F64:
+                v = torch.empty(self.sizes.nnz, dtype=TORCH_VALUE[vt], device=self.device)
+                fe_round_values(self.sizes.nnz, self.vals, vt, v, stream)
+            seg_ptr = torch.empty(self.m + 1, dtype=torch.int32, device=self.device)
+            work = _alloc_bytes(fe_vbcrs_workspace(self.m), self.device)
+            nns = fe_vbcrs_plan(src.desc, seg_ptr, work, stream)
+            jas = torch.empty(nns, dtype=torch.int32, device=self.device)
+            offs = torch.empty(nns + 1, dtype=torch.int32, device=self.device)
+            fe_vbcrs_fill(src.desc, seg_ptr, jas, offs, stream)
+            d = fe_matrix(f, vt, self.m, self.m, self.sizes.n_slices, nns, seg_ptr.data_ptr(), None,
+                          jas.data_ptr(), v.data_ptr(), offs.data_ptr())
+            dm = DeviceMatrix(d, {"seg_ptr": seg_ptr, "jas": jas, "seg_offsets": offs, "vals": v})
         else:
             ns = self.sizes.n_slices
             sp = torch.empty(ns + 1, dtype=torch.int64, device=self.device)
@@ -758,7 +830,7 @@ class System:
         key = (fmt, value)
         dm = self._formats.get(key)
         f, vt = FORMATS[fmt], VALUE_TYPES[value]
-        if dm is None or f == FE_FMT_CSR:
+        if dm is None or f in (FE_FMT_CSR, FE_FMT_VBCRS):
             self._formats.pop(key, None)
             return self.matrix(fmt, value, stream)
         sp = dm.tensors["slice_ptr"]
