@@ -650,6 +650,19 @@ static bool mode_dims_ok(int mode, const int *din, const int *dout) {
 
 }  // namespace fe
 
+namespace fe {
+
+// dW[ci][t][co] from per-split partials part[split][a][b][t] (fixed order),
+// for the tensor-core weight gradient (fe_nn_tc.cu).
+fe_status launch_corr_reduce(const float *part, int n_split, int ca, int cb, int a_is_co, float *dw,
+                             cudaStream_t s) {
+    k_corr_reduce<<<(ca * cb * 27 + 31) / 32, kNnThreads, 0, s>>>(part, n_split, ca, cb, a_is_co, dw);
+    FE_TRY_LAUNCH();
+    return FE_OK;
+}
+
+}  // namespace fe
+
 using namespace fe;
 
 extern "C" {

@@ -573,6 +573,274 @@ __global__ void k_to_bf16i(const float *__restrict__ in, int c, size_t v, __nv_b
     }
 }
 
+// ---------------------------------------------------------------- weight gradient
+//
+// R[a][b][t] = sum_z A[a][z] B[b][S z + d_t - 1] over the positions z of A's
+// grid (S = 1: the stride-1 layer, A = dY, B = X; S = 2: the stride-2 layer,
+// A = dY, B = X, and the transposed layer, A = X, B = dY), on the tensor
+// cores.  Per tap t it is a GEMM with the positions as the contraction:
+// D_t[a][b] = sum_k A[a][k] B_t[k][b], M = a (padded to 128 rows), N = b,
+// K = the tile's positions.  B_t is staged exactly like the forward layer's
+// input box (halo box, or eight parity sub-boxes for S = 2) as 16-byte rows of
+// one position x 8 channels, so that B_t is the same operand shifted by a
+// whole number of rows; read with K along the rows and N along the channels,
+// both operands are MN-major (no swizzle: core matrices of 8 positions x 8
+// channels, 128 contiguous bytes; the leading offset steps along K, 128
+// bytes, the stride offset between 8-channel groups).  A block takes a range
+// of tiles (TY lines of one plane) and one group of taps whose accumulators
+// fit tensor memory (27 x b columns do not for b > 16), accumulates over its
+// tiles and writes its partial R; k_corr_reduce sums the partials in a fixed
+// order.  BF16 operands (nearest even), FP32 accumulation.
+struct WgGeom {
+    int ty, w2, ly, pz, rsub, rows, rows_pad, base, nk;
+    int taps_per_group, n_groups, tmem_cols;
+    size_t smem;
+};
+
+template <int S>
+__global__ void __launch_bounds__(kTcThreads, 1)
+k_wgrad_tc(const float *__restrict__ A, int ca, TcDims da, const float *__restrict__ B, int cb, TcDims db,
+           float *__restrict__ part, WgGeom g) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_base;
+    __shared__ int s_ok;
+    __shared__ int s_shift[27];
+    unsigned char *sA = smem;                                   // [16][nk] rows of 16 bytes
+    unsigned char *sB = smem + (size_t)16 * g.nk * 16;          // [cb/8][rows_pad] rows of 16 bytes
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int W2 = g.w2, TY = g.ty, LY = g.ly;
+    const size_t plane_a = (size_t)da.d * da.h * da.w, plane_b = (size_t)db.d * db.h * db.w;
+    const int nty = (da.h + TY - 1) / TY, ntiles = da.d * nty;
+    const int t0 = blockIdx.y * g.taps_per_group;
+    const int t1 = t0 + g.taps_per_group < 27 ? t0 + g.taps_per_group : 27;
+    const int ga = (ca + 7) / 8, gb = cb / 8;
+    const uint32_t mbar_a = smem_u32(&mbar);
+    if (tid < 27) {
+        const int iz = tid / 9, iy = (tid / 3) % 3, ix = tid % 3;
+        int shift;
+        if (S == 2) {
+            const int sub = ((iz != 1) << 2) | ((iy != 1) << 1) | (ix != 1);
+            shift = sub * g.rsub + (iz == 0 ? -1 : 0) * LY * W2 + (iy == 0 ? -1 : 0) * W2 + (ix == 0 ? -1 : 0);
+        } else {
+            shift = (iz - 1) * LY * W2 + (iy - 1) * W2 + (ix - 1);
+        }
+        s_shift[tid] = shift;
+    }
+    if (tid == 0) {
+        s_ok = 1;
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar_a), "r"(1));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    // A's channel groups past ca and every row stay zero unless staged
+    for (size_t i = tid; i < (size_t)16 * g.nk; i += kTcThreads)
+        reinterpret_cast<uint4 *>(sA)[i] = make_uint4(0u, 0u, 0u, 0u);
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                     "r"(g.tmem_cols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;
+    // both operands MN-major (transpose bits of the instruction descriptor)
+    const uint32_t idesc = umma_idesc_bf16(128, cb) | (1u << 15) | (1u << 16);
+    uint32_t phase = 0;
+    bool ok = true, first = true;
+
+    for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        const int z = tile / nty, y0 = (tile % nty) * TY;
+        // A over the tile's positions: row j = (line j / W2, point j % W2);
+        // the points past the line's end (the box's halo columns) are zero
+        for (int j = tid; j < g.nk; j += kTcThreads) {
+            const int yi = j / W2, x = j % W2, y = y0 + yi;
+            const bool inb = j < TY * W2 && x < da.w && y < da.h;
+            const size_t gidx = inb ? ((size_t)z * da.h + y) * da.w + x : 0;
+            for (int q = 0; q < ga; ++q) {
+                __nv_bfloat162 h[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const int c0 = 8 * q + 2 * c;
+                    const float v0 = (inb && c0 < ca) ? A[(size_t)c0 * plane_a + gidx] : 0.0f;
+                    const float v1 = (inb && c0 + 1 < ca) ? A[(size_t)(c0 + 1) * plane_a + gidx] : 0.0f;
+                    h[c] = __floats2bfloat162_rn(v0, v1);
+                }
+                *reinterpret_cast<uint4 *>(sA + ((size_t)q * g.nk + j) * 16) = *reinterpret_cast<const uint4 *>(h);
+            }
+        }
+        // B's box (zero outside the grid and in the padding rows)
+        for (int r = tid; r < g.rows_pad; r += kTcThreads) {
+            bool inb = false;
+            size_t gidx = 0;
+            if (r < g.rows) {
+                int gz, gy, gx;
+                if (S == 2) {
+                    const int sb = r / g.rsub, rr = r % g.rsub;
+                    const int a_ = rr / (LY * W2), rem = rr % (LY * W2);
+                    const int b_ = rem / W2, xx = rem % W2;
+                    gz = 2 * (z - 1 + a_) + ((sb >> 2) & 1);
+                    gy = 2 * (y0 - 1 + b_) + ((sb >> 1) & 1);
+                    gx = 2 * (xx - 1) + (sb & 1);
+                    inb = rr < g.pz * LY * W2;
+                } else {
+                    const int pz = r / (LY * W2), rem = r % (LY * W2);
+                    gz = z - 1 + pz;
+                    gy = y0 - 1 + rem / W2;
+                    gx = rem % W2 - 1;
+                    inb = true;
+                }
+                inb = inb && gz >= 0 && gz < db.d && gy >= 0 && gy < db.h && gx >= 0 && gx < db.w;
+                gidx = inb ? ((size_t)gz * db.h + gy) * db.w + gx : 0;
+            }
+            for (int q = 0; q < gb; ++q) {
+                __nv_bfloat162 h[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const int c0 = 8 * q + 2 * c;
+                    const float v0 = inb ? B[(size_t)c0 * plane_b + gidx] : 0.0f;
+                    const float v1 = inb ? B[(size_t)(c0 + 1) * plane_b + gidx] : 0.0f;
+                    h[c] = __floats2bfloat162_rn(v0, v1);
+                }
+                *reinterpret_cast<uint4 *>(sB + ((size_t)q * g.rows_pad + r) * 16) = *reinterpret_cast<const uint4 *>(h);
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+            for (int t = t0; t < t1; ++t) {
+                const uint32_t d_tmem = tmem + (uint32_t)((t - t0) * cb);
+                const uint32_t brow = (uint32_t)(g.base + s_shift[t]);
+                for (int kk = 0; kk < g.nk / 16; ++kk) {
+                    const uint64_t da_ = umma_smem_desc(a0 + (uint32_t)(kk * 16 * 16), 128u, (uint32_t)g.nk * 16);
+                    const uint64_t db_ = umma_smem_desc(b0 + (brow + (uint32_t)(16 * kk)) * 16, 128u,
+                                                        (uint32_t)g.rows_pad * 16);
+                    const uint32_t acc = (first && kk == 0) ? 0u : 1u;
+                    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+                                 "l"(da_), "l"(db_), "r"(idesc), "r"(acc));
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar_a)
+                         : "memory");
+        }
+        if (!mbar_wait(mbar_a, phase & 1u)) {
+            atomicExch(&g_tc_err, 1);
+            s_ok = 0;
+        }
+        phase += 1;
+        first = false;
+        __syncthreads();
+        ok = s_ok != 0;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // partial R of this block's taps: warp q (mod 4) reads lanes 32q..32q+31
+    // (a = 32q + lane); the two warpgroups take alternate 8-column chunks
+    if (ok) {
+        const int q = warp & 3, half = warp >> 2;
+        const int a = 32 * q + lane;
+        const int ncol = (t1 - t0) * cb;
+        for (int c0 = 8 * half; c0 < ncol; c0 += 16) {
+            float v[8];
+            if (!first) tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, v);
+            else
+#pragma unroll
+                for (int j = 0; j < 8; ++j) v[j] = 0.0f;
+            if (a < ca) {
+                const int t = t0 + c0 / cb, b = c0 % cb;
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    part[(((size_t)blockIdx.x * ca + a) * cb + b + j) * 27 + t] = v[j];
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(g.tmem_cols));
+}
+
+// Tile geometry of the weight gradient over A's grid (wa x ha lines): the
+// tallest tile whose A rows (16 groups of 8 channels, nk positions) and B box
+// fit the shared-memory cap; B rows cover the largest tap shift past the
+// last K step.
+static bool choose_wgrad_geom(int S, int wa, int ha, int cb, WgGeom *out) {
+    bool found = false;
+    for (int ty = 1; ty <= kTcMaxTY && ty <= ha; ++ty) {
+        WgGeom g;
+        g.ty = ty;
+        int shift_max;
+        if (S == 2) {
+            g.ly = ty + 1;
+            g.pz = 2;
+            g.w2 = wa + 1;
+            g.rsub = (g.pz * g.ly * g.w2 + 7) & ~7;
+            g.rows = 8 * g.rsub;
+            shift_max = 7 * g.rsub;
+        } else {
+            g.ly = ty + 2;
+            g.pz = 3;
+            g.w2 = wa + 2;
+            g.rsub = g.pz * g.ly * g.w2;
+            g.rows = g.rsub;
+            shift_max = g.ly * g.w2 + g.w2 + 1;
+        }
+        g.base = g.ly * g.w2 + g.w2 + 1;
+        g.nk = (ty * g.w2 + 15) & ~15;
+        const int need = g.base + shift_max + g.nk;
+        g.rows_pad = ((need > g.rows ? need : g.rows) + 7) & ~7;
+        g.smem = (size_t)16 * g.nk * 16 + (size_t)(cb / 8) * g.rows_pad * 16;
+        g.taps_per_group = 512 / cb < 27 ? 512 / cb : 27;
+        g.n_groups = (27 + g.taps_per_group - 1) / g.taps_per_group;
+        g.tmem_cols = pow2_at_least(g.taps_per_group * cb);
+        if (g.smem > kTcSmemCap || g.tmem_cols > 512 || g.rows_pad >= 16384 || g.nk >= 16384) continue;
+        *out = g;                        // taller tiles stage fewer halo rows per position
+        found = true;
+    }
+    return found;
+}
+
+struct WgradPlan {
+    int S, ca, cb, a_is_co, nx;
+    const float *A, *B;
+    TcDims da, db;
+    WgGeom g;
+};
+
+static fe_status wgrad_plan(int mode, const float *d_x, int cin, const int *dims_in, const float *d_dy, int cout,
+                            const int *dims_out, WgradPlan *p) {
+    if (mode != FE_NN_S1 && mode != FE_NN_S2 && mode != FE_NN_T2) return FE_ERR_ARG;
+    if (cin < 1 || cout < 1 || !dims_in || !dims_out) return FE_ERR_ARG;
+    for (int i = 0; i < 3; ++i) {
+        if (dims_in[i] < 1) return FE_ERR_ARG;
+        const int want = mode == FE_NN_S1 ? dims_in[i]
+                                          : (mode == FE_NN_S2 ? (dims_in[i] - 1) / 2 + 1 : 2 * (dims_in[i] - 1) + 1);
+        if (dims_out[i] != want) return FE_ERR_ARG;
+    }
+    // S1, S2: R[co][ci][t] = sum_z dY[co][z] X[ci][s z + d - 1]; T2: R[ci][co][t] = sum_z X[ci][z] dY[co][2 z + d - 1]
+    const bool t2 = mode == FE_NN_T2;
+    p->S = mode == FE_NN_S1 ? 1 : 2;
+    p->A = t2 ? d_x : d_dy;
+    p->B = t2 ? d_dy : d_x;
+    p->ca = t2 ? cin : cout;
+    p->cb = t2 ? cout : cin;
+    p->a_is_co = t2 ? 0 : 1;
+    const int *da = t2 ? dims_in : dims_out, *db = t2 ? dims_out : dims_in;
+    p->da = TcDims{da[0], da[1], da[2]};
+    p->db = TcDims{db[0], db[1], db[2]};
+    if (p->ca > 128 || (p->cb != 16 && p->cb != 32 && p->cb != 64)) return FE_ERR_ARG;
+    if (!choose_wgrad_geom(p->S, da[2], da[1], p->cb, &p->g)) return FE_ERR_ARG;
+    const int ntiles = da[0] * ((da[1] + p->g.ty - 1) / p->g.ty);
+    int nx = sm_count() / p->g.n_groups;
+    if (nx < 1) nx = 1;
+    if (nx > ntiles) nx = ntiles;
+    p->nx = nx;
+    return FE_OK;
+}
+
 }  // namespace fe
 
 using namespace fe;
@@ -659,6 +927,42 @@ fe_status fe_nn_conv3d_tc_bf16i(int mode, const void *d_in16, int cin, const int
     if (mode == FE_NN_T2)
         return launch_tc<FE_NN_T2, true>(nullptr, d_in16, cin, h_dims_in, d_img, d_bias, d_out, cout, h_dims_out, relu, s);
     return FE_ERR_ARG;
+}
+
+fe_status fe_nn_wgrad_tc_workspace(int mode, int cin, const int *h_dims_in, int cout, const int *h_dims_out,
+                                   size_t *h_bytes) {
+    if (!h_bytes) return FE_ERR_ARG;
+    WgradPlan p;
+    const float dummy = 0.0f;
+    fe_status st = wgrad_plan(mode, &dummy, cin, h_dims_in, &dummy, cout, h_dims_out, &p);
+    if (st != FE_OK) return st;
+    *h_bytes = (size_t)p.nx * p.ca * p.cb * 27 * sizeof(float);
+    return FE_OK;
+}
+
+fe_status fe_nn_conv3d_weight_grad_tc(int mode, const float *d_x, int cin, const int *h_dims_in,
+                                      const float *d_dy, int cout, const int *h_dims_out, float *d_dw,
+                                      float *d_work, size_t work_bytes, fe_stream_t stream) {
+    if (!d_x || !d_dy || !d_dw || !d_work) return FE_ERR_ARG;
+    WgradPlan p;
+    fe_status st = wgrad_plan(mode, d_x, cin, h_dims_in, d_dy, cout, h_dims_out, &p);
+    if (st != FE_OK) return st;
+    if (work_bytes < (size_t)p.nx * p.ca * p.cb * 27 * sizeof(float)) return FE_ERR_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    // one block per SM: request enough shared memory that no second block
+    // (and no second 512-column tensor-memory allocation) shares it
+    size_t smem = p.g.smem;
+    if (smem < (size_t)120 * 1024) smem = (size_t)120 * 1024;
+    const dim3 grid((unsigned)p.nx, (unsigned)p.g.n_groups);
+    if (p.S == 1) {
+        FE_TRY_CUDA(cudaFuncSetAttribute(k_wgrad_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_wgrad_tc<1><<<grid, kTcThreads, smem, s>>>(p.A, p.ca, p.da, p.B, p.cb, p.db, d_work, p.g);
+    } else {
+        FE_TRY_CUDA(cudaFuncSetAttribute(k_wgrad_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_wgrad_tc<2><<<grid, kTcThreads, smem, s>>>(p.A, p.ca, p.da, p.B, p.cb, p.db, d_work, p.g);
+    }
+    FE_TRY_LAUNCH();
+    return launch_corr_reduce(d_work, p.nx, p.ca, p.cb, p.a_is_co, d_dw, s);
 }
 
 fe_status fe_nn_tc_check(int *h_flag) {

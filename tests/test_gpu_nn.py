@@ -441,3 +441,44 @@ def test_conv_tensor_cores_tma_staging(fe, mode, cin, cout, dims):
     fe.conv3d_tc(mode, cuda32(x), cin, dims, img, cuda32(b), y2, cout, dout, 1)
     assert torch.equal(y, y2)
     assert fe.fe_nn_tc_check() == 0
+
+
+WG_TC_CASES = [("s1", 16, 20, (9, 7, 11)), ("s1", 32, 16, (17, 17, 17)), ("s1", 64, 64, (5, 6, 7)),
+               ("s1", 16, 16, (1, 1, 1)), ("s1", 16, 16, (3, 5, 129)), ("s1", 16, 16, (33, 33, 33)),
+               ("s2", 16, 32, (17, 17, 17)), ("s2", 64, 64, (9, 9, 9)), ("s2", 32, 8, (6, 10, 7)),
+               ("t2", 32, 16, (5, 4, 6)), ("t2", 64, 32, (9, 9, 9)), ("t2", 16, 64, (3, 3, 3))]
+
+
+@pytest.mark.parametrize("mode,cin,cout,dims", WG_TC_CASES)
+def test_conv_weight_gradient_tensor_cores(fe, mode, cin, cout, dims):
+    """Weight gradient on tcgen05 (per tap a GEMM over the voxels, both operands
+    rounded to BF16, FP32 accumulation, per-block partials summed in a fixed
+    order) against the FP64 oracle: each product's relative error is at most
+    (1 + 2^-9)^2 - 1 < 2^-8 + 2^-16, the FP32 sums add 2 (K + splits) 2^-24,
+    all times sum |x||dy|.  Covers one, two and four groups of taps (input
+    channels of the correlation 16, 32, 64) and the three layer kinds."""
+    x, W, b = layer_setup(mode, cin, cout, dims, 6)
+    dout = onn.out_dims(mode, dims)
+    dy = np.random.default_rng(7).standard_normal((cout,) + dout).astype(np.float32)
+    M = fe.NN_MODES[mode]
+    need = fe.fe_nn_wgrad_tc_workspace(M, cin, dims, cout, dout)
+    work = torch.empty(need // 4 + 1, dtype=torch.float32, device="cuda")
+    dw = torch.empty((cin, 27, cout), dtype=torch.float32, device="cuda")
+    fe.fe_nn_conv3d_weight_grad_tc(M, cuda32(x), cin, dims, cuda32(dy), cout, dout, dw, work)
+    assert fe.fe_nn_tc_check() == 0
+    ref = onn.conv_grad_w(mode, x.astype(np.float64), dy.astype(np.float64))
+    bound = onn.conv_grad_w(mode, np.abs(x).astype(np.float64), np.abs(dy).astype(np.float64))
+    K = int(np.prod(dout)) if mode != "t2" else int(np.prod(dims))
+    splits = need // (4 * cin * cout * 27)
+    tol = (2.0 ** -8 + 2.0 ** -16 + 2 * (K + splits) * U32) * bound
+    assert np.all(np.abs(dw.cpu().numpy() - ref) <= tol + 1e-30)
+
+
+def test_weight_gradient_tensor_cores_rejects_other_shapes(fe):
+    # the correlation's N dimension (input channels for S1/S2, output for T2) must be 16, 32 or 64
+    dims = (5, 5, 5)
+    for mode, cin, cout in (("s1", 2, 16), ("s1", 24, 16), ("t2", 16, 8)):
+        dout = onn.out_dims(mode, dims)
+        with pytest.raises(fe.FeError) as e:
+            fe.fe_nn_wgrad_tc_workspace(fe.NN_MODES[mode], cin, dims, cout, dout)
+        assert e.value.status == fe.FE_ERR_ARG
