@@ -40,3 +40,31 @@ def test_clock_samples_are_parsed_into_median_and_reasons():
     out = c.stop()
     assert out["sm_mhz"] == 2070.0 and out["sm_max_mhz"] == 2070.0
     assert out["reasons"] == ["sw_power_cap"] and out["power_w_max"] == 1390.0
+
+
+def test_bench_lambda_min_is_the_oracle_spectrum():
+    """The bench's forward-error bars use the smallest eigenvalue of the cube's
+    Dirichlet system in closed form; it is the oracle's (pinned against dense
+    eigenvalues in test_oracle_spectrum.py) for every size."""
+    import bench
+    import oracle
+    for n in list(range(1, 41)) + [96, 128, 256, 400]:
+        lo, _ = oracle.dirichlet_extreme_eigenvalues(n, n, n)
+        assert abs(bench.lambda_min_cube(n) - lo) <= 1e-12 * lo, n
+
+
+def test_vbcrs_byte_model_counts_the_paper_arrays():
+    """The bench's byte model of the paper's BCRS SpMV: the CRS values, jas and
+    offsets per segment (nns = n (3n - 2)^2 on a cube: one segment per row and
+    y/z neighbour line, lengths 2 or 3), the segment row pointer, x and y --
+    here checked against the oracle's own arrays on a small mesh."""
+    import bench
+    import oracle
+    n = 6
+    s = oracle.build_system(n, n, n)
+    ptr, jas, off = oracle.csr_to_bcrs(s["row_ptr"], s["cols"])
+    nn = n + 1
+    assert jas.size == nn * (3 * nn - 2) ** 2
+    m, nnz = ptr.size - 1, s["cols"].size
+    want = s["vals"].nbytes + jas.nbytes + off.nbytes + ptr.nbytes + 2 * 8 * m
+    assert bench.spmv_bytes("vbcrs", m, (m + 31) // 32, jas.size, nnz) == want

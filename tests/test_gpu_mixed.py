@@ -2,13 +2,17 @@
 accumulation, FP64 residual, refinement and global dot products) checked
 against the FP64 oracle, through the C ABI.
 
-Per-form tolerances:
-  * the oracle's true relative residual of the result <= 1.5e-10 (tol 1e-10);
-  * error: ||x - x*|| <= 10 ||x_oracle - x*|| + 1e-12 ||x*||, x* the oracle
-    solved to 1e-14.  The mixed solve stops on the true FP64 residual like the
-    FP64 solve, but what is left of the error sits in other (low) modes, so at
-    the same residual its error is a few times the FP64 solve's (measured
-    4.8x for BF16 at N=30); both stay far inside kappa(A) ||r||/||b|| ~ 1e-7;
+Per-form tolerances (the mixed-precision reading of the design notes):
+  * the oracle's true relative residual of the result <= 1.5e-10 (tol 1e-10):
+    the mixed form stops on the same FP64 residual test as the FP64 form;
+  * the forward-error bound that test implies for any solution,
+    ||x - x*|| <= ||b - A x|| / lambda_min(A), lambda_min from the closed-form
+    Dirichlet spectrum (tests/test_oracle_spectrum.py) -- the guarantee;
+  * a regression guard, ||x - x*|| <= 20 ||x_oracle - x*|| + 1e-12 ||x*||
+    (x* the oracle solved to 1e-14): at the same residual the mixed form
+    leaves more of its error in low modes than FP64 CG, measured 1.8-8.8x the
+    FP64 form's error on the 97^3 and 257^3 meshes, so the guard sits at about
+    twice the largest measured ratio; it is not a property of the method;
   * solved to 1e-13, the result matches the oracle's 1e-13 solution to 1e-10
     (the FP64 path's criterion (iv), one decade tighter for the same reason).
 """
@@ -48,6 +52,14 @@ def rel(a, b):
     return np.linalg.norm(a - b) / np.linalg.norm(b)
 
 
+def assert_forward_error(sysm, x, x_star, dims):
+    """||x - x*|| <= (||b - A x|| + ||b - A x*||) / lambda_min(A)."""
+    lam_min, _ = oracle.dirichlet_extreme_eigenvalues(*dims)
+    res = lambda v: np.linalg.norm(sysm["b"] - oracle.spmv_csr(sysm["row_ptr"], sysm["cols"],
+                                                              sysm["vals"], v))
+    assert np.linalg.norm(x - x_star) <= (res(x) + res(x_star)) / lam_min
+
+
 MODES = {"reliable": 0, "restart": 1}
 INNER_TOL = {("restart", "f32"): 1e-5, ("restart", "bf16"): 1e-3,
              ("reliable", "f32"): 0.1, ("reliable", "bf16"): 0.1}
@@ -77,7 +89,8 @@ def test_mixed_matches_fp64_oracle(fe, mode, fmt, value):
     xg = x.cpu().numpy()
     tr = oracle.true_relres(sysm["row_ptr"], sysm["cols"], sysm["vals"], sysm["b"], xg)
     assert tr <= 1.5e-10
-    assert rel(xg, x_star) <= 10.0 * rel(x_or, x_star) + 1e-12
+    assert rel(xg, x_star) <= 20.0 * rel(x_or, x_star) + 1e-12
+    assert_forward_error(sysm, xg, x_star, dims)
     assert res.outer_iterations >= 1 and res.inner_iterations >= res.outer_iterations
 
 
@@ -145,7 +158,8 @@ def test_mixed_face_data(fe, mode, value):
     assert res.status == fe.FE_OK
     xg = x.cpu().numpy()
     assert oracle.true_relres(sysm["row_ptr"], sysm["cols"], sysm["vals"], sysm["b"], xg) <= 1.5e-10
-    assert rel(xg, x_star) <= 10.0 * rel(x_or, x_star) + 1e-12
+    assert rel(xg, x_star) <= 20.0 * rel(x_or, x_star) + 1e-12
+    assert_forward_error(sysm, xg, x_star, dims)
 
 
 @pytest.mark.parametrize("mode", ["reliable", "restart"])
@@ -194,11 +208,13 @@ def test_full_size_n400_mixed(fe):
     """N = 400 (64.5M rows, the mixed-precision configuration): sampled assembled
     rows against the oracle, then FP64 CG and the reliable mixed solver with
     FP32 and BF16 values (BCRS3), each to a true relative residual <= 1.5e-10
-    (FP64 residual kernel, pinned against the oracle in test_gpu_cg.py).  Both
-    solutions then differ by at most 2 kappa 1.5e-10 relative, with kappa(A)
-    <= (16h/3) / (3 pi^2 h^3) = 16 / (9 pi^2 h^2) ~ 2.9e4 for this stencil
-    (Gershgorin bound over the smallest continuum eigenvalue times h^3):
-    <= 8.7e-6, asserted as 1e-5."""
+    (FP64 residual kernel, pinned against the oracle in test_gpu_cg.py).  The
+    per-form bars of the mixed form: the forward-error bound every solution
+    meeting its residual obeys, ||x - x*|| <= ||b - A x|| / lambda_min(A) with
+    lambda_min from the closed-form Dirichlet spectrum (4.6e-7 at N = 400;
+    kappa(A) = 2.2e6, the identity rows setting lambda_max = 1), applied to
+    x* = the FP64 solve to 1e-13; and the regression guard ||x - x*|| <=
+    20 ||x_fp64 - x*|| + 1e-12 ||x*||."""
     import torch
     from test_gpu_assembly import oracle_row
     n = 400
@@ -223,15 +239,27 @@ def test_full_size_n400_mixed(fe):
             assert np.abs(vals - ref_vals).max() <= 1e-14 * np.abs(ref_vals).max()
     A64 = s.matrix("bcrs3", "f64")
     rwork = fe.resid_workspace()
+    cwork = fe.cg_workspace(A64)
+    bnorm = float(torch.linalg.norm(s.b))
+    lam_min, _ = oracle.dirichlet_extreme_eigenvalues(n, n, n)
+    xs = torch.zeros(m, dtype=torch.float64, device="cuda")
+    r = fe.fe_cg_solve(A64.desc, s.b, xs, 1e-13, 20000, cwork)
+    rs = fe.fe_true_relres(A64.desc, s.b, xs, rwork) * bnorm
     x64 = torch.zeros(m, dtype=torch.float64, device="cuda")
-    r = fe.fe_cg_solve(A64.desc, s.b, x64, 1e-10, 20000, fe.cg_workspace(A64))
-    assert r.status == fe.FE_OK and fe.fe_true_relres(A64.desc, s.b, x64, rwork) <= 1.5e-10
+    r = fe.fe_cg_solve(A64.desc, s.b, x64, 1e-10, 20000, cwork)
+    tr64 = fe.fe_true_relres(A64.desc, s.b, x64, rwork)
+    assert r.status == fe.FE_OK and tr64 <= 1.5e-10
+    e64 = float(torch.linalg.norm(x64 - xs))
+    assert e64 <= (tr64 * bnorm + rs) / lam_min
     for v in ("f32", "bf16"):
         Alo = s.matrix("bcrs3", v)
         xm = torch.zeros_like(x64)
         rm = fe.fe_cg_solve_mixed(A64.desc, Alo.desc, s.b, xm, 1e-10, fe.FE_MIXED_RELIABLE, 200, 0.1,
                                   20000, fe.mixed_workspace(Alo), check=False)
         assert rm.status == fe.FE_OK, v
-        assert fe.fe_true_relres(A64.desc, s.b, xm, rwork) <= 1.5e-10
-        assert torch.linalg.norm(xm - x64) <= 1e-5 * torch.linalg.norm(x64)
+        trm = fe.fe_true_relres(A64.desc, s.b, xm, rwork)
+        assert trm <= 1.5e-10
+        em = float(torch.linalg.norm(xm - xs))
+        assert em <= (trm * bnorm + rs) / lam_min, v
+        assert em <= 20.0 * e64 + 1e-12 * float(torch.linalg.norm(xs)), (v, em / e64)
         del Alo, xm
