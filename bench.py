@@ -175,7 +175,25 @@ def cg_iteration_model(fmt: str, m: int, n_slices: int, n_stored: int, nnz: int)
     return mat + 80 * m, fma + 5 * m, mat
 
 
+def mixed_bytes_model(m: int, n_slices: int, n_stored: int, value: str, inner_steps: int,
+                      refinements: int):
+    """Algorithmic bytes of a reliable-update mixed solve on BCRS3 matrices.
+    Inner FP32 step: the low-precision matrix once (4 B index + 12 B FP32 or
+    6 B BF16 values per slot, slice pointers) and 44 B of FP32 vectors
+    per row (w = A p: p, w; xs += a p, r -= a w: xs, r, p, w read, xs, r
+    written; p = r + b p: p, r read, p written).  Refinement step: the FP64
+    matrix once (28 B per slot) and 44 B per row (x += xs: x, xs read, x, xs
+    written; r = b - A x: x, b read, r written).  Plus the initial FP64
+    residual."""
+    vb = 6 if value == "bf16" else 12
+    lo = n_stored * (4 + vb) + 8 * (n_slices + 1) + 44 * m
+    hi = 28 * n_stored + 8 * (n_slices + 1) + 44 * m
+    return inner_steps * lo + (refinements + 1) * hi
+
+
 def spmv_bytes(fmt: str, m: int, n_slices: int, n_stored: int, nnz: int, vec_bytes: int = 8):
+    if fmt == "vbcrs":      # values, jas and offsets per segment, the segment row pointer
+        return 8 * nnz + 4 * n_stored + 4 * (n_stored + 1) + 4 * (m + 1) + 2 * vec_bytes * m
     if fmt == "bcrs3":
         return 28 * n_stored + 8 * (n_slices + 1) + 2 * vec_bytes * m
     if fmt == "sell":
@@ -185,24 +203,58 @@ def spmv_bytes(fmt: str, m: int, n_slices: int, n_stored: int, nnz: int, vec_byt
 
 # ------------------------------------------------------------------ CPU oracle sample
 
+def oracle_setup_seconds(sysm, repeats: int = 3) -> float:
+    """Median time of an oracle CG call that takes no step (allocation, first
+    touch of its vectors, ||b||, r = b - A x0 and r.r): the part of every call
+    that does not scale with the step count."""
+    import oracle
+    ts = []
+    for _ in range(repeats):
+        t = time.perf_counter()
+        oracle.cg(sysm["row_ptr"], sysm["cols"], sysm["vals"], sysm["b"], tol=0.0, maxit=0)
+        ts.append(time.perf_counter() - t)
+    return statistics.median(ts)
+
+
 def cpu_oracle_sample(n: int, iters_sample: int, iters_to_tol: int):
     """Oracle (single core) on the N-mesh: build the system (untimed setup),
-    time `iters_sample` CG steps, scale to the iteration count to 1e-10.
-    Returns the baseline entry and the oracle's system (reused by the
-    multi-core leg)."""
+    time a call that takes no step and one that takes `iters_sample` steps;
+    the full solve is modelled as setup + iters_to_tol x per-step cost, the
+    same model the reference arm uses.  Returns the baseline entry and the
+    oracle's system (reused by the multi-core leg)."""
     import oracle
     t0 = time.perf_counter()
     sysm = oracle.build_system(n, n, n)
-    setup = time.perf_counter() - t0
+    build = time.perf_counter() - t0
+    setup = oracle_setup_seconds(sysm)
     t1 = time.perf_counter()
     oracle.cg(sysm["row_ptr"], sysm["cols"], sysm["vals"], sysm["b"], tol=0.0, maxit=iters_sample)
     dt = time.perf_counter() - t1
-    per_it = dt / iters_sample
-    return {"value": per_it * iters_to_tol, "unit": "s", "cores": 1, "kind": "oracle",
-            "sample": (f"oracle (plain C, 1 thread) on the N={n} system: {iters_sample} CG "
-                       f"iterations timed ({dt:.1f} s, {per_it:.3f} s/iteration) and scaled to "
-                       f"{iters_to_tol} iterations; its mesh+pattern+assembly took "
-                       f"{setup:.1f} s (untimed setup)")}, sysm
+    per_it = (dt - setup) / iters_sample
+    return {"value": setup + per_it * iters_to_tol, "unit": "s", "cores": 1, "kind": "oracle",
+            "s_per_iteration": round(per_it, 5), "setup_s": round(setup, 4),
+            "sample": (f"oracle (plain C, 1 thread) on the N={n} system: one call of "
+                       f"{iters_sample} CG iterations ({dt:.1f} s) less the call setup "
+                       f"({setup:.2f} s: vectors, r = b - A x0) gives {per_it:.4f} s/iteration; "
+                       f"value = setup + {iters_to_tol} iterations; its "
+                       f"mesh+pattern+assembly took {build:.1f} s (untimed)")}, sysm
+
+
+def cpu_oracle_full_solve(n: int, repeats: int = 3):
+    """The oracle's whole solve (CG from x0 = 0 to 1e-10) on the N-mesh, timed
+    in full: median of `repeats` runs."""
+    import oracle
+    sysm = oracle.build_system(n, n, n)
+    ts, its = [], None
+    for _ in range(repeats):
+        t = time.perf_counter()
+        _, its, rel, st = oracle.cg(sysm["row_ptr"], sysm["cols"], sysm["vals"], sysm["b"],
+                                    tol=TOL, maxit=MAXIT)
+        ts.append(time.perf_counter() - t)
+    return {"value": round(statistics.median(ts), 5), "unit": "s", "cores": 1, "kind": "oracle",
+            "iterations": its, "status": st, "runs_s": [round(t, 5) for t in ts],
+            "sample": f"oracle CG on the N={n} mesh from x0=0 to 1e-10, timed in full, "
+                      f"median of {repeats} runs"}
 
 
 def cpu_parallel_sample(sysm, n: int, iters_sample: int, iters_to_tol: int):
@@ -239,7 +291,8 @@ def run_reference(args, rank: int, world: int):
     t0 = time.perf_counter()
     sysm = oracle.build_system(n, n, n)
     setup = time.perf_counter() - t0
-    per_step = []
+    setup_s = oracle_setup_seconds(sysm)
+    per_step, per_it_steps = [], []
     for i in range(args.warmup + args.steps):
         t1 = time.perf_counter()
         oracle.cg(sysm["row_ptr"], sysm["cols"], sysm["vals"], sysm["b"], tol=0.0,
@@ -247,18 +300,24 @@ def run_reference(args, rank: int, world: int):
         dt = time.perf_counter() - t1
         if i >= args.warmup:
             per_step.append(dt)
-    per_it = statistics.mean(per_step) / args.ref_iters
-    value = per_it * iters_to_tol
-    sample = (f"each step: {args.ref_iters} oracle CG iterations on the N={n} system "
-              f"({per_it:.3f} s/iteration, 1 thread), scaled to {iters_to_tol} iterations to "
-              f"1e-10; oracle mesh+pattern+assembly {setup:.1f} s (untimed setup)")
+            per_it_steps.append((dt - setup_s) / args.ref_iters)
+    per_it = statistics.mean(per_it_steps)
+    value = setup_s + per_it * iters_to_tol
+    spread = (max(per_it_steps) - min(per_it_steps)) / per_it
+    sample = (f"each step: one oracle call of {args.ref_iters} CG iterations on the N={n} system "
+              f"less the call setup ({setup_s:.2f} s, measured before the steps): "
+              f"{per_it:.4f} s/iteration over {args.steps * args.ref_iters} timed iterations "
+              f"(spread over steps {100 * spread:.1f} %), 1 thread; value = setup + "
+              f"{iters_to_tol} iterations, the model the bench's cpu_baseline uses; oracle "
+              f"mesh+pattern+assembly {setup:.1f} s (untimed)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": statistics.mean(per_step) * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config_dict(args),
             "cpu_baseline": {"value": value, "unit": "s", "cores": 1, "kind": "oracle",
-                             "sample": sample},
+                             "s_per_iteration": round(per_it, 5),
+                             "per_step_spread": round(spread, 4), "sample": sample},
             "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0},
             "gpu_launches": 0}
@@ -297,7 +356,7 @@ def main():
     ap.add_argument("--n", "--elements", dest="n", type=int, default=256,
                     help="elements per axis (--elements: the same, a name torchrun does not take for its own)")
     ap.add_argument("--format", choices=["csr", "sell", "bcrs3"], default="bcrs3")
-    ap.add_argument("--cpu-iters", type=int, default=8, help="oracle CG iterations in the CPU sample")
+    ap.add_argument("--cpu-iters", type=int, default=40, help="oracle CG iterations in the CPU sample")
     ap.add_argument("--cpu-parallel-iters", type=int, default=40,
                     help="OpenMP CG iterations per storage form in the multi-core CPU sample (0: skip)")
     ap.add_argument("--ref-iters", type=int, default=2, help="oracle CG iterations per reference step")
@@ -305,6 +364,7 @@ def main():
     ap.add_argument("--no-spmv", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-warm-start", action="store_true", help="skip the learned warm-start leg")
     ap.add_argument("--no-sr", action="store_true", help="skip the single-reduction CG legs")
     ap.add_argument("--no-n400", action="store_true", help="skip the N=400 mixed-precision leg")
     ap.add_argument("--no-matrix-free", action="store_true", help="skip the matrix-free leg")
@@ -417,40 +477,59 @@ def main():
                      "fp64_flops_per_launch": int(2 * launch_fma),
                      "other": roof_hbm if bound == "alu" else roof_alu})
 
-    # ---- mixed-precision form on the same system (FP32 values, reliable updates)
+    # ---- mixed-precision form on the same system (FP32 and BF16 values, reliable updates)
     mixed = None
     if not args.no_mixed:
         x64_ref = x.clone()                        # the FP64 solve's solution
         A64 = state["A"]
-        Alo = s.convert(args.format, "f32")
-        mwork = fe.mixed_workspace(Alo, dev)
-        xm = torch.zeros(m, dtype=torch.float64, device=dev)
+        acc = MixedAccuracy(fe, torch, A64, s.b, x64_ref, n, dev)
+        mixed = {}
+        for v in ("f32", "bf16"):
+            Alo = s.convert(args.format, v)
+            mwork = fe.mixed_workspace(Alo, dev)
+            xm = torch.zeros(m, dtype=torch.float64, device=dev)
 
-        def mixed_solve():
-            xm.zero_()
-            a, b = EV(), EV()
-            a.record()
-            r = fe.fe_cg_solve_mixed(A64.desc, Alo.desc, s.b, xm, TOL, fe.FE_MIXED_RELIABLE, 200,
-                                     0.1, MAXIT, mwork, check=False)
-            b.record()
-            return a, b, r
+            def mixed_solve():
+                xm.zero_()
+                a, b = EV(), EV()
+                a.record()
+                r = fe.fe_cg_solve_mixed(A64.desc, Alo.desc, s.b, xm, TOL, fe.FE_MIXED_RELIABLE, 200,
+                                         0.1, MAXIT, mwork, check=False)
+                b.record()
+                return a, b, r
 
-        for _ in range(args.warmup):
-            mixed_solve()
-        torch.cuda.synchronize()
-        recs = [mixed_solve() for _ in range(args.steps)]
-        torch.cuda.synchronize()
-        mt = statistics.mean(a.elapsed_time(b) for a, b, _ in recs)
-        r = recs[-1][2]
-        err = float(torch.linalg.norm(xm - x64_ref) / torch.linalg.norm(x64_ref))
-        mixed = {"value": round(mt * 1e-3, 6), "unit": "s", "values": "f32",
-                 "mode": "reliable updates (FP32 CG, FP64 residual/update/dots), delta 0.1",
-                 "speedup_vs_fp64": round(cg_ms / mt, 3), "fp32_iterations": r.inner_iterations,
-                 "refinement_steps": r.outer_iterations, "relres_true": r.relres,
-                 "status": r.status, "rel_diff_vs_fp64_solution": err,
-                 "ms_per_fp32_iteration": round(mt / max(r.inner_iterations, 1), 4)}
-        s._formats.pop((args.format, "f32"), None)
-        del Alo, mwork
+            for _ in range(args.warmup):
+                mixed_solve()
+            torch.cuda.synchronize()
+            recs = [mixed_solve() for _ in range(args.steps)]
+            torch.cuda.synchronize()
+            mt = statistics.mean(a.elapsed_time(b) for a, b, _ in recs)
+            r = recs[-1][2]
+            err = float(torch.linalg.norm(xm - x64_ref) / torch.linalg.norm(x64_ref))
+            entry = {"value": round(mt * 1e-3, 6), "unit": "s", "values": v,
+                     "mode": "reliable updates (FP32 CG, FP64 residual/update/dots), delta 0.1",
+                     "speedup_vs_fp64": round(cg_ms / mt, 3), "fp32_iterations": r.inner_iterations,
+                     "refinement_steps": r.outer_iterations, "relres_true": r.relres,
+                     "status": r.status, "rel_diff_vs_fp64_solution": err,
+                     "ms_per_fp32_iteration": round(mt / max(r.inner_iterations, 1), 4),
+                     "accuracy": acc.entry(xm)}
+            if args.format == "bcrs3":
+                byts = mixed_bytes_model(m, s.sizes.n_slices, Alo.desc.n_stored, v,
+                                         r.inner_iterations, r.outer_iterations)
+                ach = byts / (mt * 1e-3) / 1e9
+                entry["roofline"] = {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm_peak,
+                                     "unit": "GB/s", "frac": round(ach / hbm_peak, 4),
+                                     "algorithmic_bytes": int(byts),
+                                     "model": "inner FP32 steps + FP64 refinement passes"}
+            if v == "f32":
+                mixed.update(entry)       # the FP32-value form is the leg's headline
+            else:
+                mixed["bf16"] = entry
+            s._formats.pop((args.format, v), None)
+            del Alo, mwork, xm
+            torch.cuda.empty_cache()
+        mixed["fp64_accuracy"] = acc.entry(x64_ref)
+        del acc
         torch.cuda.empty_cache()
 
     # ---- single-reduction CG (Chronopoulos-Gear): the same system, and the N=30 mesh
@@ -485,7 +564,15 @@ def main():
         As = small.matrix(args.format, "f64")
         xsm = torch.zeros(small.m, dtype=torch.float64, device=dev)
         out = {}
-        for name, fn, wk in (("textbook", fe.fe_cg_solve, fe.cg_workspace(As, dev)),
+        def form(f):
+            return lambda A_, b_, x_, t_, k_, w_, check=False: fe.fe_cg_solve_form(
+                A_, b_, x_, t_, k_, f, w_, check=check)
+        # fe_cg_solve picks the matrix-resident form on this mesh (one slice per
+        # warp, FP64 BCRS3); the other textbook forms for comparison
+        cw = fe.cg_workspace(As, dev)
+        for name, fn, wk in (("textbook", fe.fe_cg_solve, cw),
+                             ("textbook_two_phase", form(fe.FE_CG_TWO_PHASE), cw),
+                             ("textbook_three_phase", form(fe.FE_CG_THREE_PHASE), cw),
                              ("single_reduction", fe.fe_cg_solve_sr, fe.sr_workspace(As, dev))):
             ts = []
             for _ in range(args.warmup + args.steps):
@@ -512,6 +599,10 @@ def main():
     batched = None
     if not args.no_batched and world == 1:
         batched = run_batched(args, fe, torch, dev, EV)
+    warm = None
+    if not args.no_warm_start and world == 1:
+        warm = run_warm_start(args, fe, torch, dev, EV)
+        torch.cuda.empty_cache()
 
     # ---- the N = 400 mixed-precision configuration (FP32 and BF16 values)
     n400 = None
@@ -562,7 +653,7 @@ def main():
         xv = torch.rand(m, dtype=torch.float64, device=dev)
         yv = torch.empty_like(xv)
         flush = torch.empty(512 * 2 ** 20, dtype=torch.uint8, device=dev)
-        for fmt in ["csr", "sell", "bcrs3"]:
+        for fmt in ["csr", "sell", "bcrs3", "vbcrs"]:
             Af = s.matrix(fmt, "f64")
             ts = []
             for r in range(7):
@@ -581,6 +672,9 @@ def main():
                          "fp64_tflops": round(2 * (3 * Af.desc.n_stored if fmt == "bcrs3" else
                                                    (Af.desc.n_stored if fmt == "sell" else s.sizes.nnz))
                                               / t / 1e9, 4)}
+            if fmt == "vbcrs":
+                spmv[fmt]["segments"] = int(Af.desc.n_stored)
+                spmv[fmt]["what"] = "the paper's BCRS as printed: ptr, jas, offsets over the CRS values"
             if fmt != args.format:
                 s._formats.pop((fmt, "f64"), None)
             del Af
@@ -590,8 +684,9 @@ def main():
     launches_per_step = 7   # mesh 1, assembly 2, slice plan 2, fill 1, CG 1 (timed FP64 steps)
 
     if rank == 0:
-        cpu = cpu_par = None
+        cpu = cpu_par = cpu_n30 = None
         if world == 1 and not args.no_cpu_baseline:
+            cpu_n30 = cpu_oracle_full_solve(30)
             cpu, sysm = cpu_oracle_sample(n, args.cpu_iters, int(round(it)))
             if args.cpu_parallel_iters > 0:
                 cpu_par = cpu_parallel_sample(sysm, n, args.cpu_parallel_iters, int(round(it)))
@@ -604,9 +699,9 @@ def main():
                 "iterations": it, "relres_true": tr, "status": sorted(statuses),
                 "cg_ms_per_iteration": round(cg_ms / max(it, 1), 4),
                 "phase_ms": {k: round(statistics.mean(v), 3) for k, v in phases.items()},
-                "roofline": roofline, "mixed": mixed, "mixed_n400": n400, "single_reduction": single_red,
+                "roofline": roofline, "cpu_baseline_n30": cpu_n30, "mixed": mixed, "mixed_n400": n400, "single_reduction": single_red,
                 "matrix_free": matrix_free,
-                "batched": batched, "spmv": spmv, "e2e": e2e,
+                "batched": batched, "warm_start": warm, "spmv": spmv, "e2e": e2e,
                 "cpu_baseline": cpu, "cpu_parallel": cpu_par,
                 "clocks": clocks, "gpu_launches": launches_per_step * args.steps,
                 "wall_s_timed_region": round(wall, 3)}
@@ -687,6 +782,49 @@ def run_matrix_free(args, fe, torch, dev, EV, n: int, s, x_assembled, cg_ms: flo
     return out
 
 
+def lambda_min_cube(n: int) -> float:
+    """Smallest eigenvalue of the Dirichlet system of the n^3 box mesh: the
+    boundary rows' identity (eigenvalue 1) and the interior block, the Kronecker
+    sum of 1D linear-element stiffness and mass, whose smallest eigenvalue is
+    3 l(1) m(1)^2 with l(1) = (2/h)(1 - cos pi h), m(1) = (h/3)(2 + cos pi h)."""
+    import math
+    h = 1.0 / n
+    c = math.cos(math.pi * h)
+    lam = 3.0 * (2.0 / h) * (1.0 - c) * ((h / 3.0) * (2.0 + c)) ** 2 if n >= 2 else 1.0
+    return min(1.0, lam)
+
+
+class MixedAccuracy:
+    """Errors of a solve against x* (the FP64 solve to 1e-13, untimed) and the
+    per-form bars: the forward-error bound ||x - x*|| <= (||b - A x|| +
+    ||b - A x*||) / lambda_min that every solution meeting the residual test
+    obeys, and the regression guard of 20x the FP64 solve's own error."""
+
+    def __init__(self, fe, torch, A64, b, x64, n, dev):
+        self.fe, self.torch, self.A64, self.b = fe, torch, A64, b
+        self.rwork = fe.resid_workspace(dev)
+        self.xs = torch.zeros_like(x64)
+        w = fe.cg_workspace(A64, dev)
+        fe.fe_cg_solve(A64.desc, b, self.xs, 1e-13, 20000, w, check=False)
+        del w
+        self.bnorm = float(torch.linalg.norm(b))
+        self.xsnorm = float(torch.linalg.norm(self.xs))
+        self.rs = fe.fe_true_relres(A64.desc, b, self.xs, self.rwork) * self.bnorm
+        self.lam = lambda_min_cube(n)
+        self.e64 = float(torch.linalg.norm(x64 - self.xs))
+
+    def entry(self, x):
+        e = float(self.torch.linalg.norm(x - self.xs))
+        rel_res = self.fe.fe_true_relres(self.A64.desc, self.b, x, self.rwork)
+        bound = (rel_res * self.bnorm + self.rs) / self.lam
+        return {"rel_error_vs_xstar": e / self.xsnorm,
+                "ratio_to_fp64_error": e / self.e64 if self.e64 > 0 else None,
+                "forward_error_bound_rel": bound / self.xsnorm,
+                "meets_bound": bool(e <= bound), "meets_guard_20x": bool(e <= 20 * self.e64 + 1e-12 * self.xsnorm),
+                "relres_true": rel_res,
+                "xstar": "FP64 CG to 1e-13 on the same system"}
+
+
 def run_n400(args, fe, torch, dev, EV, n: int = 400):
     """Mixed precision at N = 400 (401^3 = 64.5M rows, 1.73B stored entries):
     FP64 CG (BCRS3) to 1e-10, then the reliable-update mixed solver with FP32
@@ -695,6 +833,7 @@ def run_n400(args, fe, torch, dev, EV, n: int = 400):
     Errors are against the FP64 GPU solve (the same solver checked against
     the oracle in the tests); the true residuals come from the FP64 residual
     kernel."""
+    hbm_peak, _ = load_peaks()
     s = fe.System(n, device=dev).build()
     A64 = s.matrix("bcrs3", "f64")
     lo = {v: s.matrix("bcrs3", v) for v in ("f32", "bf16")}
@@ -723,8 +862,10 @@ def run_n400(args, fe, torch, dev, EV, n: int = 400):
         return fe.fe_cg_solve(A64.desc, s.b, x64, TOL, 20000, w64, check=False)
 
     t, r = timed(fp64)
+    acc = MixedAccuracy(fe, torch, A64, s.b, x64, n, dev)
     out["fp64"] = {"value": round(t, 4), "iterations": r.iterations, "status": r.status,
-                   "relres_true": fe.fe_true_relres(A64.desc, s.b, x64, rwork)}
+                   "relres_true": fe.fe_true_relres(A64.desc, s.b, x64, rwork),
+                   "accuracy": acc.entry(x64)}
     for v, Alo in lo.items():
         xm = torch.zeros(m, dtype=torch.float64, device=dev)
         mw = fe.mixed_workspace(Alo, dev)
@@ -739,11 +880,94 @@ def run_n400(args, fe, torch, dev, EV, n: int = 400):
                   "refinement_steps": r.outer_iterations,
                   "relres_true": fe.fe_true_relres(A64.desc, s.b, xm, rwork),
                   "rel_error_vs_fp64": float(torch.linalg.norm(xm - x64) / torch.linalg.norm(x64)),
+                  "accuracy": acc.entry(xm),
                   "speedup_vs_fp64": round(out["fp64"]["value"] / t, 3)}
+        byts = mixed_bytes_model(m, s.sizes.n_slices, Alo.desc.n_stored, v, r.inner_iterations,
+                                 r.outer_iterations)
+        out[v]["roofline"] = {"bound": "hbm", "achieved": round(byts / t / 1e9, 1), "peak": hbm_peak,
+                              "unit": "GB/s", "frac": round(byts / t / 1e9 / hbm_peak, 4),
+                              "algorithmic_bytes": int(byts)}
         del xm, mw
-    del s, A64, lo, x64, w64
+    del s, A64, lo, x64, w64, acc
     torch.cuda.empty_cache()
     return out
+
+
+def run_warm_start(args, fe, torch, dev, EV, n_eval: int = 50, n_accuracy: int = 2):
+    """Learned warm start (N = 128, 129^3 nodes): the committed trained network
+    (paper_1505_08023_gb300/weights/warmstart_n128.blob, trained on 2,000 CG
+    solutions for face data PCG64(1000, 0..1999)) on held-out face data
+    PCG64(2000, 0..n_eval-1).  Per problem: FP64 CG (BCRS3) from x0 = 0, and
+    the network's x0 (one fe_warmstart_infer call) checked by its true
+    residual (x0 = 0 as the fallback when it is not below 1) then FP64 CG to
+    the same tolerance; CUDA events around each, the warm time including
+    inference and the check.  On the first n_accuracy problems both solutions
+    are compared with x* (the FP64 solve to 1e-13) and their true residuals
+    reported."""
+    import fe_inputs
+    from paper_1505_08023_gb300 import warmstart as ws
+    if not os.path.exists(ws.DEFAULT_BLOB):
+        return {"unavailable": "no trained network blob"}
+    net = ws.TrainedWarmStart(ws.DEFAULT_BLOB, dev)
+    N = net.n_nodes - 1
+    prob = ws.Problem(N, dev)
+    m = prob.sys.m
+    rwork = fe.resid_workspace(dev)
+    x = torch.zeros(m, dtype=torch.float64, device=dev)
+    x0 = torch.empty_like(x)
+    lam = lambda_min_cube(N)
+    rows, acc = [], []
+    for i in range(n_eval):
+        prob.set_faces(fe_inputs.face_data(2000, i, N, N, N))
+        for _ in range(2 if i == 0 else 1):          # the first problem once untimed
+            x.zero_()
+            a, b = EV(), EV()
+            a.record()
+            r0 = fe.fe_cg_solve(prob.A.desc, prob.sys.b, x, TOL, MAXIT, prob.work, check=False)
+            b.record()
+            a2, b2, c2 = EV(), EV(), EV()
+            a2.record()
+            net.predict(prob.sys, x0)
+            b2.record()
+            start_res = fe.fe_true_relres(prob.A.desc, prob.sys.b, x0, rwork)
+            fallback = not (start_res < 1.0)
+            if fallback:
+                x0.zero_()
+            r1 = fe.fe_cg_solve(prob.A.desc, prob.sys.b, x0, TOL, MAXIT, prob.work, check=False)
+            c2.record()
+            torch.cuda.synchronize()
+        rows.append((r0.iterations, r1.iterations, a.elapsed_time(b), a2.elapsed_time(c2),
+                     a2.elapsed_time(b2), start_res, fallback, r0.status == 0 and r1.status == 0))
+        if i < n_accuracy:
+            xs = torch.zeros_like(x)
+            fe.fe_cg_solve(prob.A.desc, prob.sys.b, xs, 1e-13, MAXIT, prob.work, check=False)
+            xsn = float(torch.linalg.norm(xs))
+            bn = float(torch.linalg.norm(prob.sys.b))
+            rs = fe.fe_true_relres(prob.A.desc, prob.sys.b, xs, rwork) * bn
+            entry = {"seed": f"PCG64(2000, {i})"}
+            for name, v in (("cold", x), ("warm", x0)):
+                tr = fe.fe_true_relres(prob.A.desc, prob.sys.b, v, rwork)
+                e = float(torch.linalg.norm(v - xs))
+                entry[name] = {"relres_true": tr, "rel_error_vs_xstar": e / xsn,
+                               "forward_error_bound_rel": (tr * bn + rs) / lam / xsn}
+            acc.append(entry)
+    ic = [r[0] for r in rows]
+    iw = [r[1] for r in rows]
+    tc = [r[2] for r in rows]
+    tw = [r[3] for r in rows]
+    return {"workload": (f"MiniFE N={N} ({m:,} rows), random face data, {n_eval} held-out problems; "
+                         f"FP64 CG (BCRS3) to 1e-10 from x0 = 0 and from the network's x0"),
+            "unit": "ms", "samples": n_eval,
+            "mean_iterations_cold": statistics.mean(ic), "mean_iterations_warm": statistics.mean(iw),
+            "iterations_saved_frac": round(1 - statistics.mean(iw) / statistics.mean(ic), 4),
+            "mean_ms_cold": round(statistics.mean(tc), 4),
+            "mean_ms_warm_incl_inference": round(statistics.mean(tw), 4),
+            "time_saved_frac": round(1 - statistics.mean(tw) / statistics.mean(tc), 4),
+            "mean_ms_inference": round(statistics.mean(r[4] for r in rows), 4),
+            "mean_start_relres": statistics.mean(r[5] for r in rows),
+            "fallbacks": sum(r[6] for r in rows), "all_converged": all(r[7] for r in rows),
+            "accuracy": acc,
+            "network": {k: net.meta.get(k) for k in ("channels", "n_train", "epochs", "train_seeds")}}
 
 
 def run_batched(args, fe, torch, dev, EV):

@@ -9,7 +9,9 @@ single-reduction CG for --sr-steps steps, and the mixed-precision
 reliable-update solve for --mixed-steps FP32 steps; or, with
 --stencil-steps, the matrix-free operator and CG; or, with --conv, one
 stride-1 convolution of the warm-start network (tensor-core kernels with
-TMA-staged BF16 input and with FP32 input, then the CUDA-core kernel); or, with --batch, the batched solver on a seeded batch of meshes.  With
+TMA-staged BF16 input and with FP32 input, then the CUDA-core kernel); or, with
+--wgrad, one layer's weight gradient (tensor-core kernel, then CUDA-core
+kernel); or, with --batch, the batched solver on a seeded batch of meshes.  With
 --drop-csr the CSR arrays are released after conversion (smaller footprint
 for profiler captures that save and restore device memory).  Prints one line
 per step taken.
@@ -26,7 +28,7 @@ from . import fe
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--n", type=int, default=128)
-    ap.add_argument("--format", choices=["csr", "sell", "bcrs3"], default="bcrs3")
+    ap.add_argument("--format", choices=["csr", "sell", "bcrs3", "vbcrs"], default="bcrs3")
     ap.add_argument("--spmv", action="store_true")
     ap.add_argument("--cg-steps", type=int, default=20)
     ap.add_argument("--tol", type=float, default=1e-10)
@@ -41,6 +43,9 @@ def main():
     ap.add_argument("--conv", type=int, nargs=3, metavar=("CIN", "COUT", "N"), default=None,
                     help="instead of the solver: one stride-1 conv of the warm-start network on an "
                          "N^3 grid, tensor-core kernel then CUDA-core kernel")
+    ap.add_argument("--wgrad", nargs=4, metavar=("MODE", "CIN", "COUT", "N"), default=None,
+                    help="instead of the solver: the weight gradient of one layer (s1, s2 or t2) on an "
+                         "N^3 input grid, tensor-core kernel then CUDA-core kernel")
     ap.add_argument("--stencil-steps", type=int, default=None,
                     help="instead of the stored matrix: the matrix-free operator once, then this many "
                          "matrix-free CG steps (tol 0; 0: solve to --tol)")
@@ -51,6 +56,9 @@ def main():
     if a.conv is not None:
         run_conv(*a.conv)
         return
+    if a.wgrad is not None:
+        run_wgrad(a.wgrad[0], *map(int, a.wgrad[1:]))
+        return
     if a.batch is not None:
         run_batch(*a.batch, fmt=a.format, steps=a.cg_steps)
         return
@@ -58,7 +66,7 @@ def main():
     s = fe.System(a.n).build()
     A = s.matrix(a.format, "f64")
     Alo = s.matrix(a.format, a.mixed_values) if a.mixed_steps > 0 else None
-    if a.drop_csr and a.format != "csr":
+    if a.drop_csr and a.format not in ("csr", "vbcrs"):
         s.cols = s.vals = None
         s.coords = None
         torch.cuda.empty_cache()
@@ -129,6 +137,29 @@ def run_conv(cin: int, cout: int, n: int):
     fe.fe_nn_conv3d(fe.NN_MODES["s1"], x, cin, dims, w16, b, y, cout, dims, 1)
     torch.cuda.synchronize()
     print(f"CUDA-core conv {cin}->{cout} on {n}^3 done")
+
+
+def run_wgrad(mode: str, cin: int, cout: int, n: int):
+    din = (n, n, n)
+    dout = din if mode == "s1" else (tuple((v - 1) // 2 + 1 for v in din) if mode == "s2"
+                                     else tuple(2 * (v - 1) + 1 for v in din))
+    g = torch.Generator(device="cuda").manual_seed(0)
+    x = torch.randn((cin,) + din, device="cuda", generator=g)
+    dy = torch.randn((cout,) + dout, device="cuda", generator=g)
+    dw = torch.empty((cin, 27, cout), device="cuda")
+    M = fe.NN_MODES[mode]
+    work = torch.empty(fe.fe_nn_wgrad_tc_workspace(M, cin, din, cout, dout) // 4 + 1, device="cuda")
+    fe.fe_nn_conv3d_weight_grad_tc(M, x, cin, din, dy, cout, dout, dw, work)
+    torch.cuda.synchronize()
+    print(f"tensor-core weight gradient {mode} {cin}->{cout} on {n}^3 done, wait flag {fe.fe_nn_tc_check()}")
+    if mode == "t2":
+        need, _ = fe.fe_nn_corr_workspace(2, cin, din, cout)
+    else:
+        need, _ = fe.fe_nn_corr_workspace(1 if mode == "s1" else 2, cout, dout, cin)
+    work = torch.empty(need // 4 + 1, device="cuda")
+    fe.fe_nn_conv3d_weight_grad(M, x, cin, din, dy, cout, dout, dw, work)
+    torch.cuda.synchronize()
+    print(f"CUDA-core weight gradient {mode} {cin}->{cout} on {n}^3 done")
 
 
 if __name__ == "__main__":

@@ -162,14 +162,26 @@ class WarmStartNet:
         """Weight/bias gradients of layer lname; data gradient into dx (if given)."""
         l = self.layers[lname]
         stride = 1 if l.mode == "s1" else 2
-        if l.mode == "t2":
-            need, _ = fe.fe_nn_corr_workspace(2, l.cin, self.dims[lin], l.cout)
+        # the weight gradient on the tensor cores where the correlation's N
+        # dimension (input channels; output channels of a transposed layer)
+        # is 16, 32 or 64, else on the CUDA cores
+        nb = l.cout if l.mode == "t2" else l.cin
+        if self.tensor_cores and nb in (16, 32, 64):
+            M = fe.NN_MODES[l.mode]
+            need = fe.fe_nn_wgrad_tc_workspace(M, l.cin, self.dims[lin], l.cout, self.dims[lout])
+            if self.corr_work is None or self.corr_work.numel() * 4 < need:
+                self.corr_work = torch.empty(max(need // 4, 1) * 2, dtype=torch.float32, device=self.dev)
+            fe.fe_nn_conv3d_weight_grad_tc(M, x, l.cin, self.dims[lin], dy, l.cout, self.dims[lout], l.gw,
+                                           self.corr_work)
         else:
-            need, _ = fe.fe_nn_corr_workspace(stride, l.cout, self.dims[lout], l.cin)
-        if self.corr_work is None or self.corr_work.numel() * 4 < need:
-            self.corr_work = torch.empty(max(need // 4, 1) * 2, dtype=torch.float32, device=self.dev)
-        fe.fe_nn_conv3d_weight_grad(fe.NN_MODES[l.mode], x, l.cin, self.dims[lin], dy, l.cout,
-                                    self.dims[lout], l.gw, self.corr_work)
+            if l.mode == "t2":
+                need, _ = fe.fe_nn_corr_workspace(2, l.cin, self.dims[lin], l.cout)
+            else:
+                need, _ = fe.fe_nn_corr_workspace(stride, l.cout, self.dims[lout], l.cin)
+            if self.corr_work is None or self.corr_work.numel() * 4 < need:
+                self.corr_work = torch.empty(max(need // 4, 1) * 2, dtype=torch.float32, device=self.dev)
+            fe.fe_nn_conv3d_weight_grad(fe.NN_MODES[l.mode], x, l.cin, self.dims[lin], dy, l.cout,
+                                        self.dims[lout], l.gw, self.corr_work)
         fe.fe_nn_channel_sum(dy, l.cout, self.dims[lout], l.gb)
         if dx is not None:
             if l.imgt is not None:

@@ -453,9 +453,10 @@ WG_TC_CASES = [("s1", 16, 20, (9, 7, 11)), ("s1", 32, 16, (17, 17, 17)), ("s1", 
 def test_conv_weight_gradient_tensor_cores(fe, mode, cin, cout, dims):
     """Weight gradient on tcgen05 (per tap a GEMM over the voxels, both operands
     rounded to BF16, FP32 accumulation, per-block partials summed in a fixed
-    order) against the FP64 oracle: each product's relative error is at most
-    (1 + 2^-9)^2 - 1 < 2^-8 + 2^-16, the FP32 sums add 2 (K + splits) 2^-24,
-    all times sum |x||dy|.  Covers one, two and four groups of taps (input
+    order) against the FP64 oracle: both operands are rounded to BF16 (8
+    significant bits, relative error at most 2^-8 each), so each product's
+    relative error is at most (1 + 2^-8)^2 - 1 = 2^-7 + 2^-16; the FP32 sums
+    add 2 (K + splits) 2^-24, all times sum |x||dy|.  Covers one, two and four groups of taps (input
     channels of the correlation 16, 32, 64) and the three layer kinds."""
     x, W, b = layer_setup(mode, cin, cout, dims, 6)
     dout = onn.out_dims(mode, dims)
@@ -470,7 +471,7 @@ def test_conv_weight_gradient_tensor_cores(fe, mode, cin, cout, dims):
     bound = onn.conv_grad_w(mode, np.abs(x).astype(np.float64), np.abs(dy).astype(np.float64))
     K = int(np.prod(dout)) if mode != "t2" else int(np.prod(dims))
     splits = need // (4 * cin * cout * 27)
-    tol = (2.0 ** -8 + 2.0 ** -16 + 2 * (K + splits) * U32) * bound
+    tol = (2.0 ** -7 + 2.0 ** -16 + 2 * (K + splits) * U32) * bound
     assert np.all(np.abs(dw.cpu().numpy() - ref) <= tol + 1e-30)
 
 
