@@ -227,10 +227,13 @@ __device__ __forceinline__ AT slice_spmv_csr(const fe_matrix &A, int64_t s, int 
 // segment's first column and value offset and its (up to three, then a loop)
 // values, which are contiguous in the CSR value array.  Every load of a trip
 // is issued before the first FMA; the four lane partials of a row are then
-// combined by the same fixed transpose-reduce as the CSR kernel.
-template <class VT, class XT, class AT, class G>
+// combined by the same fixed transpose-reduce as the CSR kernel.  S = segments
+// per lane per trip: 3 covers a 27-point row (nine segments) in one trip --
+// the stand-alone SpMV's choice; the CG kernels, which hold more state, take
+// 2 (two trips per row, no spills at their register budgets).
+template <class VT, class XT, class AT, int S = 2, class G>
 __device__ __forceinline__ AT slice_spmv_vbcrs(const fe_matrix &A, int64_t s, int lane, const G &x) {
-    constexpr int S = 2, L = 3;       // segments per lane per trip, values unrolled per segment
+    constexpr int L = 3;              // values unrolled per segment
     const int g = lane >> 2, j = lane & 3;
     const int64_t r0 = s * kSlice;
     const int64_t nrows = A.n_rows;
@@ -286,17 +289,17 @@ __device__ __forceinline__ AT slice_spmv_vbcrs(const fe_matrix &A, int64_t s, in
     return __shfl_sync(0xffffffffu, row_sum, src);
 }
 
-template <int FMT, class VT, class XT, class AT, class G>
+template <int FMT, class VT, class XT, class AT, class G, int VBS = 2>
 __device__ __forceinline__ AT slice_spmv_g(const fe_matrix &A, int64_t s, int lane, const G &x) {
     if constexpr (FMT == FE_FMT_CSR) return slice_spmv_csr<VT, XT, AT>(A, s, lane, x);
-    else if constexpr (FMT == FE_FMT_VBCRS) return slice_spmv_vbcrs<VT, XT, AT>(A, s, lane, x);
+    else if constexpr (FMT == FE_FMT_VBCRS) return slice_spmv_vbcrs<VT, XT, AT, VBS>(A, s, lane, x);
     else if constexpr (FMT == FE_FMT_SELL) return slice_spmv_sell<VT, XT, AT>(A, s, lane, x);
     else return slice_spmv_bcrs3<VT, XT, AT>(A, s, lane, x);
 }
 
-template <int FMT, class VT, class XT, class AT, bool kReadOnlyX>
+template <int FMT, class VT, class XT, class AT, bool kReadOnlyX, int VBS = 2>
 __device__ __forceinline__ AT slice_spmv(const fe_matrix &A, int64_t s, int lane, const XT *x) {
-    return slice_spmv_g<FMT, VT, XT, AT>(A, s, lane, PtrGather<kReadOnlyX, XT>{x});
+    return slice_spmv_g<FMT, VT, XT, AT, PtrGather<kReadOnlyX, XT>, VBS>(A, s, lane, PtrGather<kReadOnlyX, XT>{x});
 }
 
 }  // namespace fe
