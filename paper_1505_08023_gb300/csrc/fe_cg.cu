@@ -25,8 +25,17 @@
 
 namespace fe {
 
+// The three-phase kernel's BCRS3 SpMV issues the loads of all nine slots of
+// a 27-point row in one trip and runs three blocks per SM (80 registers, no
+// spills; four blocks at 64 registers spill): 1 % less time per step at
+// N = 256 than three slots per trip at four blocks per SM.  The two-phase
+// kernel runs the same block count, so both forms split the slices and the
+// dot products the same way (their results are bitwise equal).
+template <int FMT> constexpr int k_cg_unroll() { return FMT == FE_FMT_BCRS3 ? 9 : 0; }
+template <int FMT> constexpr int k_cg_min_blocks() { return FMT == FE_FMT_BCRS3 ? 3 : cg_min_blocks<FMT>(); }
+
 template <int FMT, class VT, class XT>
-__global__ void __launch_bounds__(kCgThreads, cg_min_blocks<FMT>()) k_cg(const CgArgs<XT> a) {
+__global__ void __launch_bounds__(kCgThreads, k_cg_min_blocks<FMT>()) k_cg(const CgArgs<XT> a) {
     __shared__ CgBlockState st;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     // rows fit int32 (check_matrix); slices are walked in a grid-stride order
@@ -83,7 +92,7 @@ __global__ void __launch_bounds__(kCgThreads, cg_min_blocks<FMT>()) k_cg(const C
             // A: w = A p, p.w
             XT pw_part = XT(0);
             for (int s = blockIdx.x * kCgWarps + warp; s < ns; s += tw) {
-                const XT y = slice_spmv<FMT, VT, XT, XT, false>(a.A, s, lane, a.p);
+                const XT y = slice_spmv<FMT, VT, XT, XT, false, k_cg_unroll<FMT>()>(a.A, s, lane, a.p);
                 const int row = s * kSlice + lane;
                 if (row < m) {
                     a.w[row] = y;
@@ -154,7 +163,7 @@ __global__ void __launch_bounds__(kCgThreads, cg_min_blocks<FMT>()) k_cg(const C
 // does one more FMA there, which costs more than a barrier once the FP64
 // pipe, not latency, bounds the step.
 template <int FMT, class VT>
-__global__ void __launch_bounds__(kCgThreads, cg_min_blocks<FMT>()) k_cg2(const CgArgs<double> a) {
+__global__ void __launch_bounds__(kCgThreads, k_cg_min_blocks<FMT>()) k_cg2(const CgArgs<double> a) {
     __shared__ CgBlockState st;
     __shared__ double coef[2];           // alpha of the last step, beta
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -277,7 +286,8 @@ static size_t cg_workspace_bytes(const fe_matrix &A) {
 static int cg_pick_form(const fe_matrix &A, int form) {
     if (form != FE_CG_AUTO) return form;
     if (resident_cg_fits(A)) return FE_CG_RESIDENT;
-    const int64_t warps = (int64_t)sm_count() * kCgBlocksPerSm * kCgWarps;
+    const int blocks_per_sm = A.format == FE_FMT_BCRS3 ? k_cg_min_blocks<FE_FMT_BCRS3>() : kCgBlocksPerSm;
+    const int64_t warps = (int64_t)sm_count() * blocks_per_sm * kCgWarps;
     return A.n_slices <= warps ? FE_CG_TWO_PHASE : FE_CG_THREE_PHASE;
 }
 

@@ -126,7 +126,7 @@ __device__ __forceinline__ AT slice_spmv_sell(const fe_matrix &A, int64_t s, int
     return acc;
 }
 
-template <class VT, class XT, class AT, class G>
+template <class VT, class XT, class AT, int U = 3, class G>
 __device__ __forceinline__ AT slice_spmv_bcrs3(const fe_matrix &A, int64_t s, int lane, const G &x) {
     const int64_t b = A.d_slice_ptr[s];
     const int w = (int)((A.d_slice_ptr[s + 1] - b) >> 5);
@@ -134,8 +134,7 @@ __device__ __forceinline__ AT slice_spmv_bcrs3(const fe_matrix &A, int64_t s, in
     const VT *v = reinterpret_cast<const VT *>(A.d_vals) + 3 * b + lane;
     AT acc = AT(0);
     int k = 0;
-    constexpr int U = 3;
-    for (; k + U <= w; k += U) {
+    for (; k + U <= w; k += U) {     // U slots' loads in flight per trip
         int32_t jj[U];
         VT vv[U][3];
 #pragma unroll
@@ -289,17 +288,19 @@ __device__ __forceinline__ AT slice_spmv_vbcrs(const fe_matrix &A, int64_t s, in
     return __shfl_sync(0xffffffffu, row_sum, src);
 }
 
-template <int FMT, class VT, class XT, class AT, class G, int VBS = 2>
+// UN: loads in flight per lane and trip where the format has the choice --
+// VBCRS segments (default 2), BCRS3 slots (default 3); 0 takes the default.
+template <int FMT, class VT, class XT, class AT, class G, int UN = 0>
 __device__ __forceinline__ AT slice_spmv_g(const fe_matrix &A, int64_t s, int lane, const G &x) {
     if constexpr (FMT == FE_FMT_CSR) return slice_spmv_csr<VT, XT, AT>(A, s, lane, x);
-    else if constexpr (FMT == FE_FMT_VBCRS) return slice_spmv_vbcrs<VT, XT, AT, VBS>(A, s, lane, x);
+    else if constexpr (FMT == FE_FMT_VBCRS) return slice_spmv_vbcrs<VT, XT, AT, UN ? UN : 2>(A, s, lane, x);
     else if constexpr (FMT == FE_FMT_SELL) return slice_spmv_sell<VT, XT, AT>(A, s, lane, x);
-    else return slice_spmv_bcrs3<VT, XT, AT>(A, s, lane, x);
+    else return slice_spmv_bcrs3<VT, XT, AT, UN ? UN : 3>(A, s, lane, x);
 }
 
-template <int FMT, class VT, class XT, class AT, bool kReadOnlyX, int VBS = 2>
+template <int FMT, class VT, class XT, class AT, bool kReadOnlyX, int UN = 0>
 __device__ __forceinline__ AT slice_spmv(const fe_matrix &A, int64_t s, int lane, const XT *x) {
-    return slice_spmv_g<FMT, VT, XT, AT, PtrGather<kReadOnlyX, XT>, VBS>(A, s, lane, PtrGather<kReadOnlyX, XT>{x});
+    return slice_spmv_g<FMT, VT, XT, AT, PtrGather<kReadOnlyX, XT>, UN>(A, s, lane, PtrGather<kReadOnlyX, XT>{x});
 }
 
 }  // namespace fe

@@ -14,7 +14,8 @@ k_spmv(const fe_matrix A, const XT *__restrict__ x, XT *__restrict__ y) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t tw = (int64_t)gridDim.x * kSpmvWarps;
     for (int64_t s = (int64_t)blockIdx.x * kSpmvWarps + warp; s < A.n_slices; s += tw) {
-        const AT v = slice_spmv<FMT, VT, XT, AT, true, 3>(A, s, lane, x);
+        // VBCRS: three segments per lane and trip (one trip per 27-point row)
+        const AT v = slice_spmv<FMT, VT, XT, AT, true, FMT == FE_FMT_VBCRS ? 3 : 0>(A, s, lane, x);
         const int64_t row = s * kSlice + lane;
         if (row < A.n_rows) y[row] = (XT)v;
     }
