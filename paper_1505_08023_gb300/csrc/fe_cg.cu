@@ -25,15 +25,6 @@
 
 namespace fe {
 
-// The three-phase kernel's BCRS3 SpMV issues the loads of all nine slots of
-// a 27-point row in one trip and runs three blocks per SM (80 registers, no
-// spills; four blocks at 64 registers spill): 1 % less time per step at
-// N = 256 than three slots per trip at four blocks per SM.  The two-phase
-// kernel runs the same block count, so both forms split the slices and the
-// dot products the same way (their results are bitwise equal).
-template <int FMT> constexpr int k_cg_unroll() { return FMT == FE_FMT_BCRS3 ? 9 : 0; }
-template <int FMT> constexpr int k_cg_min_blocks() { return FMT == FE_FMT_BCRS3 ? 3 : cg_min_blocks<FMT>(); }
-
 template <int FMT, class VT, class XT>
 __global__ void __launch_bounds__(kCgThreads, k_cg_min_blocks<FMT>()) k_cg(const CgArgs<XT> a) {
     __shared__ CgBlockState st;

@@ -19,6 +19,14 @@ constexpr int kCgBlocksPerSm = 4;
 template <int FMT> constexpr int cg_min_blocks() {
     return (FMT == FE_FMT_CSR || FMT == FE_FMT_VBCRS) ? 3 : kCgBlocksPerSm;
 }
+// The streaming CG kernels' BCRS3 SpMV issues the loads of all nine slots of
+// a 27-point row in one trip and runs three blocks per SM (80 registers, no
+// spills; four blocks at 64 registers spill): 1 % less time per step at
+// N = 256 than three slots per trip at four blocks per SM.  The three- and
+// two-phase kernels run the same block count, so both split the slices and
+// the dot products the same way (their results are bitwise equal).
+template <int FMT> constexpr int k_cg_unroll() { return FMT == FE_FMT_BCRS3 ? 9 : 0; }
+template <int FMT> constexpr int k_cg_min_blocks() { return FMT == FE_FMT_BCRS3 ? 3 : cg_min_blocks<FMT>(); }
 constexpr unsigned kMaxPolls = 1u << 28;
 
 struct CgCtrl {

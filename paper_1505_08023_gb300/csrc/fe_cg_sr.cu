@@ -71,7 +71,7 @@ __device__ __forceinline__ void update_sr(double *x, double *r, double *p, doubl
 }
 
 template <int FMT, class VT>
-__global__ void __launch_bounds__(kCgThreads, cg_min_blocks<FMT>()) k_cg_sr(const CgSrArgs a) {
+__global__ void __launch_bounds__(kCgThreads, k_cg_min_blocks<FMT>()) k_cg_sr(const CgSrArgs a) {
     __shared__ CgBlockState st;
     __shared__ SrState sr;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(kCgThreads, cg_min_blocks<FMT>()) k_cg_sr(cons
             // S: w = A r, gamma = r.r, delta = w.r
             double g_part = 0.0, d_part = 0.0;
             for (int sl = blockIdx.x * kCgWarps + warp; sl < ns; sl += tw) {
-                const double y = slice_spmv<FMT, VT, double, double, false>(a.A, sl, lane, a.r);
+                const double y = slice_spmv<FMT, VT, double, double, false, k_cg_unroll<FMT>()>(a.A, sl, lane, a.r);
                 const int row = sl * kSlice + lane;
                 if (row < m) {
                     a.w[row] = y;
