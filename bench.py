@@ -288,6 +288,8 @@ def run_reference(args, rank: int, world: int):
     import oracle
     n = args.n
     iters_to_tol = ITERS_TO_TOL.get(n, int(round(2.08 * n)))
+    if args.ref_iters is None:   # at least 40 timed iterations, as the cpu_baseline leg's sample
+        args.ref_iters = max(2, -(-40 // max(1, args.steps)))
     t0 = time.perf_counter()
     sysm = oracle.build_system(n, n, n)
     setup = time.perf_counter() - t0
@@ -359,7 +361,9 @@ def main():
     ap.add_argument("--cpu-iters", type=int, default=40, help="oracle CG iterations in the CPU sample")
     ap.add_argument("--cpu-parallel-iters", type=int, default=40,
                     help="OpenMP CG iterations per storage form in the multi-core CPU sample (0: skip)")
-    ap.add_argument("--ref-iters", type=int, default=2, help="oracle CG iterations per reference step")
+    ap.add_argument("--ref-iters", type=int, default=None,
+                    help="oracle CG iterations per reference step (default: enough for 40 timed "
+                         "iterations over the timed steps, the cpu_baseline leg's sample)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-spmv", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
