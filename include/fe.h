@@ -513,8 +513,11 @@ fe_status fe_nn_conv3d_weight_grad(int mode, const float *d_x, int cin, const in
                                    float *d_work, size_t work_bytes, fe_stream_t stream);
 /* The same weight gradient on the tensor cores (tcgen05): per tap a GEMM over
  * the voxels, operands rounded to BF16 (nearest even), FP32 accumulation in
- * tensor memory, per-block partials (d_work: fe_nn_wgrad_tc_workspace()
- * bytes) summed in a fixed order.  The channels of the layer's input (S1,
+ * tensor memory, per-block partials summed in a fixed order.  d_work
+ * (fe_nn_wgrad_tc_workspace() bytes, 16-byte aligned) holds the partials and,
+ * unless the grid is too wide for a 256-point box, a BF16 8-channel-interleaved
+ * copy of the second operand (X for S1/S2, dY for T2) that the kernel stages
+ * with tensor-map box loads.  The channels of the layer's input (S1,
  * S2) or output (T2) must be 16, 32 or 64, the others at most 128; other
  * shapes: FE_ERR_ARG (the CUDA-core fe_nn_conv3d_weight_grad takes them). */
 fe_status fe_nn_wgrad_tc_workspace(int mode, int cin, const int *h_dims_in, int cout, const int *h_dims_out,

@@ -492,24 +492,28 @@ static TensorMapEncodeFn tensor_map_encoder() {
     return fn;
 }
 
-// Tensor map of a BF16 8-channel-interleaved volume [G][D][H][W][8] with the
-// staging box of `mode` (elements traversed; element stride 2 on the spatial
-// axes for the stride-2 parity sub-boxes).
-static bool encode_input_map(CUtensorMap *tm, int mode, const void *d_in16, int cin, const int *dims,
-                             const TcGeom &g) {
+// Tensor map of a BF16 8-channel-interleaved volume [G][D][H][W][8] whose
+// box is pz planes x ly lines x w2 points (elements traversed, so twice that
+// with element stride 2 on the spatial axes for the stride-2 parity sub-boxes).
+static bool encode_box_map(CUtensorMap *tm, bool s2, const void *d_in16, int c, const int *dims, int w2, int ly,
+                           int pz) {
     TensorMapEncodeFn enc = tensor_map_encoder();
     if (!enc) return false;
     const cuuint64_t W = (cuuint64_t)dims[2], H = (cuuint64_t)dims[1], D = (cuuint64_t)dims[0];
-    const cuuint64_t G = (cuuint64_t)((cin + 7) / 8);
+    const cuuint64_t G = (cuuint64_t)((c + 7) / 8);
     const cuuint64_t gdim[5] = {8, W, H, D, G};
     const cuuint64_t gstr[4] = {16, 16 * W, 16 * W * H, 16 * W * H * D};
-    const bool s2 = mode == FE_NN_S2;
-    const cuuint32_t box[5] = {8, (cuuint32_t)(s2 ? 2 * g.w2 : g.w2), (cuuint32_t)(s2 ? 2 * g.ly : g.ly),
-                               (cuuint32_t)(s2 ? 2 * g.pz : g.pz), 1};
+    const cuuint32_t box[5] = {8, (cuuint32_t)(s2 ? 2 * w2 : w2), (cuuint32_t)(s2 ? 2 * ly : ly),
+                               (cuuint32_t)(s2 ? 2 * pz : pz), 1};
     const cuuint32_t es[5] = {1, s2 ? 2u : 1u, s2 ? 2u : 1u, s2 ? 2u : 1u, 1};
     return enc(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void *>(d_in16), gdim, gstr, box, es,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+static bool encode_input_map(CUtensorMap *tm, int mode, const void *d_in16, int cin, const int *dims,
+                             const TcGeom &g) {
+    return encode_box_map(tm, mode == FE_NN_S2, d_in16, cin, dims, g.w2, g.ly, g.pz);
 }
 
 template <int MODE, bool TMA>
@@ -597,14 +601,21 @@ struct WgGeom {
     size_t smem;
 };
 
-template <int S>
+//
+// TMA = true: B comes as BF16 in the 8-channel-interleaved layout (a copy in
+// the workspace) and thread 0 stages each tile's box with tensor-map box loads
+// issued before the threads stage A, so the two overlap; the box is the
+// forward layer's (halo box, or the eight parity sub-boxes with element
+// stride 2), zero filled outside the grid.  TMA = false: every thread loads
+// FP32 B and converts (grids too wide for a 256-point box).
+template <int S, bool TMA>
 __global__ void __launch_bounds__(kTcThreads, 1)
 k_wgrad_tc(const float *__restrict__ A, int ca, TcDims da, const float *__restrict__ B, int cb, TcDims db,
-           float *__restrict__ part, WgGeom g) {
+           float *__restrict__ part, WgGeom g, const __grid_constant__ CUtensorMap tmap) {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) uint64_t mbar;
+    __shared__ __align__(8) uint64_t mbar_b;     // TMA staging of B
     __shared__ uint32_t tmem_base;
-    __shared__ int s_ok;
     __shared__ int s_shift[27];
     unsigned char *sA = smem;                                   // [16][nk] rows of 16 bytes
     unsigned char *sB = smem + (size_t)16 * g.nk * 16;          // [cb/8][rows_pad] rows of 16 bytes
@@ -628,13 +639,19 @@ k_wgrad_tc(const float *__restrict__ A, int ca, TcDims da, const float *__restri
         s_shift[tid] = shift;
     }
     if (tid == 0) {
-        s_ok = 1;
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar_a), "r"(1));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar_b)), "r"(1));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     // A's channel groups past ca and every row stay zero unless staged
     for (size_t i = tid; i < (size_t)16 * g.nk; i += kTcThreads)
         reinterpret_cast<uint4 *>(sA)[i] = make_uint4(0u, 0u, 0u, 0u);
+    if (TMA) {
+        // B rows the box loads never write (padding, sub-box gaps) stay zero
+        for (size_t i = tid; i < (size_t)gb * g.rows_pad; i += kTcThreads)
+            reinterpret_cast<uint4 *>(sB)[i] = make_uint4(0u, 0u, 0u, 0u);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
                      "r"(g.tmem_cols));
@@ -646,11 +663,40 @@ k_wgrad_tc(const float *__restrict__ A, int ca, TcDims da, const float *__restri
     const uint32_t tmem = tmem_base;
     // both operands MN-major (transpose bits of the instruction descriptor)
     const uint32_t idesc = umma_idesc_bf16(128, cb) | (1u << 15) | (1u << 16);
-    uint32_t phase = 0;
-    bool ok = true, first = true;
+    uint32_t phase = 0, phase_b = 0;
+    bool ok = true, first = true, b_pending = false;
 
     for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
         const int z = tile / nty, y0 = (tile % nty) * TY;
+        if (TMA && tid == 0) {
+            // B's box, one load per 8-channel group (and parity sub-box), on mbar_b;
+            // the previous tile's MMAs, which read sB, completed before this trip
+            const uint32_t mb = smem_u32(&mbar_b);
+            const int nsub = S == 2 ? 8 : 1;
+            const uint32_t tx = (uint32_t)(gb * nsub * g.pz * LY * W2 * 16);
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(tx) : "memory");
+            const uint64_t tm = reinterpret_cast<uint64_t>(&tmap);
+            for (int q = 0; q < gb; ++q)
+                for (int sb = 0; sb < nsub; ++sb) {
+                    int cx, cy, cz;
+                    if (S == 2) {
+                        cx = -2 + (sb & 1);
+                        cy = 2 * (y0 - 1) + ((sb >> 1) & 1);
+                        cz = 2 * (z - 1) + ((sb >> 2) & 1);
+                    } else {
+                        cx = -1;
+                        cy = y0 - 1;
+                        cz = z - 1;
+                    }
+                    const uint32_t dst = smem_u32(sB) + (uint32_t)(((size_t)q * g.rows_pad + (size_t)sb * g.rsub) * 16);
+                    asm volatile(
+                        "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes "
+                        "[%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(dst),
+                        "l"(tm), "r"(0), "r"(cx), "r"(cy), "r"(cz), "r"(q), "r"(mb)
+                        : "memory");
+                }
+        }
+        if (TMA) b_pending = true;
         // A over the tile's positions: row j = (line j / W2, point j % W2);
         // the points past the line's end (the box's halo columns) are zero
         for (int j = tid; j < g.nk; j += kTcThreads) {
@@ -670,7 +716,7 @@ k_wgrad_tc(const float *__restrict__ A, int ca, TcDims da, const float *__restri
             }
         }
         // B's box (zero outside the grid and in the padding rows)
-        for (int r = tid; r < g.rows_pad; r += kTcThreads) {
+        for (int r = tid; r < (TMA ? 0 : g.rows_pad); r += kTcThreads) {
             bool inb = false;
             size_t gidx = 0;
             if (r < g.rows) {
@@ -705,9 +751,22 @@ k_wgrad_tc(const float *__restrict__ A, int ca, TcDims da, const float *__restri
                 *reinterpret_cast<uint4 *>(sB + ((size_t)q * g.rows_pad + r) * 16) = *reinterpret_cast<const uint4 *>(h);
             }
         }
+        bool bfail = false;
+        if (TMA) {
+            if (mbar_wait(smem_u32(&mbar_b), phase_b & 1u)) {
+                b_pending = false;
+            } else {
+                atomicExch(&g_tc_err, 1);
+                bfail = true;
+            }
+            phase_b += 1;
+        }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
+        if (__syncthreads_or(bfail)) {   // every thread takes the same branch
+            ok = false;
+            break;
+        }
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
@@ -727,15 +786,14 @@ k_wgrad_tc(const float *__restrict__ A, int ca, TcDims da, const float *__restri
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar_a)
                          : "memory");
         }
-        if (!mbar_wait(mbar_a, phase & 1u)) {
-            atomicExch(&g_tc_err, 1);
-            s_ok = 0;
-        }
+        const bool mfail = !mbar_wait(mbar_a, phase & 1u);
+        if (mfail) atomicExch(&g_tc_err, 1);
         phase += 1;
         first = false;
-        __syncthreads();
-        ok = s_ok != 0;
+        ok = !__syncthreads_or(mfail);   // every thread takes the same value
     }
+    // after an error, B loads still in flight land before the block exits
+    if (TMA && b_pending) (void)mbar_wait(smem_u32(&mbar_b), (phase_b - 1) & 1u);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     // partial R of this block's taps: warp q (mod 4) reads lanes 32q..32q+31
     // (a = 32q + lane); the two warpgroups take alternate 8-column chunks
@@ -808,6 +866,9 @@ struct WgradPlan {
     const float *A, *B;
     TcDims da, db;
     WgGeom g;
+    bool tma;                // B staged by tensor-map box loads from a BF16 copy
+    size_t part_bytes;       // per-block partials, rounded up to 256 bytes
+    size_t b16_bytes;        // the BF16 8-channel-interleaved copy of B (TMA only)
 };
 
 static fe_status wgrad_plan(int mode, const float *d_x, int cin, const int *dims_in, const float *d_dy, int cout,
@@ -838,6 +899,11 @@ static fe_status wgrad_plan(int mode, const float *d_x, int cin, const int *dims
     if (nx < 1) nx = 1;
     if (nx > ntiles) nx = ntiles;
     p->nx = nx;
+    // B's box by tensor map when each box dimension (elements traversed) fits 256
+    const int bx = p->S == 2 ? 2 * p->g.w2 : p->g.w2, by = p->S == 2 ? 2 * p->g.ly : p->g.ly;
+    p->tma = bx <= 256 && by <= 256;
+    p->part_bytes = ((size_t)nx * p->ca * p->cb * 27 * sizeof(float) + 255) & ~(size_t)255;
+    p->b16_bytes = p->tma ? (size_t)(p->cb / 8) * db[0] * db[1] * db[2] * 16 : 0;
     return FE_OK;
 }
 
@@ -936,7 +1002,7 @@ fe_status fe_nn_wgrad_tc_workspace(int mode, int cin, const int *h_dims_in, int 
     const float dummy = 0.0f;
     fe_status st = wgrad_plan(mode, &dummy, cin, h_dims_in, &dummy, cout, h_dims_out, &p);
     if (st != FE_OK) return st;
-    *h_bytes = (size_t)p.nx * p.ca * p.cb * 27 * sizeof(float);
+    *h_bytes = p.part_bytes + p.b16_bytes;
     return FE_OK;
 }
 
@@ -947,19 +1013,39 @@ fe_status fe_nn_conv3d_weight_grad_tc(int mode, const float *d_x, int cin, const
     WgradPlan p;
     fe_status st = wgrad_plan(mode, d_x, cin, h_dims_in, d_dy, cout, h_dims_out, &p);
     if (st != FE_OK) return st;
-    if (work_bytes < (size_t)p.nx * p.ca * p.cb * 27 * sizeof(float)) return FE_ERR_WORKSPACE;
+    if (work_bytes < p.part_bytes + p.b16_bytes) return FE_ERR_WORKSPACE;
     cudaStream_t s = (cudaStream_t)stream;
     // one block per SM: request enough shared memory that no second block
     // (and no second 512-column tensor-memory allocation) shares it
     size_t smem = p.g.smem;
     if (smem < (size_t)120 * 1024) smem = (size_t)120 * 1024;
     const dim3 grid((unsigned)p.nx, (unsigned)p.g.n_groups);
-    if (p.S == 1) {
-        FE_TRY_CUDA(cudaFuncSetAttribute(k_wgrad_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_wgrad_tc<1><<<grid, kTcThreads, smem, s>>>(p.A, p.ca, p.da, p.B, p.cb, p.db, d_work, p.g);
+    CUtensorMap tm;
+    memset(&tm, 0, sizeof(tm));
+    if (p.tma) {
+        // B as BF16 [cb/8][D][H][W][8] after the partials, then its box tensor map
+        void *b16 = reinterpret_cast<unsigned char *>(d_work) + p.part_bytes;
+        if (!aligned(b16, 16)) return FE_ERR_ARG;
+        const int dims_b[3] = {p.db.d, p.db.h, p.db.w};
+        const size_t v = (size_t)p.db.d * p.db.h * p.db.w;
+        const size_t n = (size_t)(p.cb / 8) * v;
+        const int blocks = (int)((n + 255) / 256 < 8192 ? (n + 255) / 256 : 8192);
+        k_to_bf16i<<<blocks, 256, 0, s>>>(p.B, p.cb, v, (__nv_bfloat16 *)b16);
+        FE_TRY_LAUNCH();
+        if (!encode_box_map(&tm, p.S == 2, b16, p.cb, dims_b, p.g.w2, p.g.ly, p.g.pz)) return FE_ERR_CUDA;
+    }
+    if (p.S == 1 && p.tma) {
+        FE_TRY_CUDA(cudaFuncSetAttribute(k_wgrad_tc<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_wgrad_tc<1, true><<<grid, kTcThreads, smem, s>>>(p.A, p.ca, p.da, p.B, p.cb, p.db, d_work, p.g, tm);
+    } else if (p.S == 1) {
+        FE_TRY_CUDA(cudaFuncSetAttribute(k_wgrad_tc<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_wgrad_tc<1, false><<<grid, kTcThreads, smem, s>>>(p.A, p.ca, p.da, p.B, p.cb, p.db, d_work, p.g, tm);
+    } else if (p.tma) {
+        FE_TRY_CUDA(cudaFuncSetAttribute(k_wgrad_tc<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_wgrad_tc<2, true><<<grid, kTcThreads, smem, s>>>(p.A, p.ca, p.da, p.B, p.cb, p.db, d_work, p.g, tm);
     } else {
-        FE_TRY_CUDA(cudaFuncSetAttribute(k_wgrad_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_wgrad_tc<2><<<grid, kTcThreads, smem, s>>>(p.A, p.ca, p.da, p.B, p.cb, p.db, d_work, p.g);
+        FE_TRY_CUDA(cudaFuncSetAttribute(k_wgrad_tc<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_wgrad_tc<2, false><<<grid, kTcThreads, smem, s>>>(p.A, p.ca, p.da, p.B, p.cb, p.db, d_work, p.g, tm);
     }
     FE_TRY_LAUNCH();
     return launch_corr_reduce(d_work, p.nx, p.ca, p.cb, p.a_is_co, d_dw, s);
