@@ -68,3 +68,21 @@ def test_vbcrs_byte_model_counts_the_paper_arrays():
     m, nnz = ptr.size - 1, s["cols"].size
     want = s["vals"].nbytes + jas.nbytes + off.nbytes + ptr.nbytes + 2 * 8 * m
     assert bench.spmv_bytes("vbcrs", m, (m + 31) // 32, jas.size, nnz) == want
+
+
+def test_reference_arm_times_at_least_40_oracle_iterations(capsys):
+    """--impl reference splits at least 40 timed oracle iterations over the timed
+    steps (the cpu_baseline leg's sample), on a tiny mesh here."""
+    import json
+    import sys
+    for steps, per_step in ((2, 20), (3, 14), (50, 2)):
+        argv = sys.argv
+        sys.argv = ["bench.py", "--impl", "reference", "--n", "4", "--steps", str(steps), "--warmup", "0"]
+        try:
+            bench.main()
+        finally:
+            sys.argv = argv
+        line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+        assert line["impl"] == "reference" and line["gpu_launches"] == 0
+        assert f"one oracle call of {per_step} CG iterations" in line["cpu_baseline"]["sample"]
+        assert steps * per_step >= 40
