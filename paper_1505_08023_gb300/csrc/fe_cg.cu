@@ -90,14 +90,14 @@ __global__ void __launch_bounds__(kCgThreads, k_cg_min_blocks<FMT>()) k_cg(const
                     pw_part = fma(a.p[row], y, pw_part);
                 }
             }
-            double pw, unused;
-            if (!(alive = grid_sum2(a, &st, (double)pw_part, 0.0, pw, unused))) break;
+            double pw;
+            if (!(alive = grid_sum1(a, &st, (double)pw_part, pw))) break;
             if (!(pw > 0.0) || !(pw < INFINITY)) { status = FE_ERR_BREAKDOWN; break; }
             // B: r -= alpha w, r.r (x += alpha p is applied in C, where p is read anyway)
             const XT alpha = (XT)(st.rr / pw);
             const XT rr_part = update_r<XT>(a.r, a.w, m, alpha);
             double rr_new;
-            if (!(alive = grid_sum2(a, &st, (double)rr_part, 0.0, rr_new, unused))) break;
+            if (!(alive = grid_sum1(a, &st, (double)rr_part, rr_new))) break;
             const double beta = rr_new / st.rr;
             __syncthreads();                 // every thread has read st.rr
             if (threadIdx.x == 0) {
@@ -227,14 +227,14 @@ __global__ void __launch_bounds__(kCgThreads, k_cg_min_blocks<FMT>()) k_cg2(cons
                     pw_part = fma(pk, y, pw_part);
                 }
             }
-            double pw, unused;
-            if (!(alive = grid_sum2(a, &st, pw_part, 0.0, pw, unused))) break;
+            double pw;
+            if (!(alive = grid_sum1(a, &st, pw_part, pw))) break;
             if (!(pw > 0.0) || !(pw < INFINITY)) { status = FE_ERR_BREAKDOWN; break; }
             // B: r -= alpha w, r.r
             const double alpha = st.rr / pw;
             const double rr_part = update_r<double>(a.r, a.w, m, alpha);
             double rr_new;
-            if (!(alive = grid_sum2(a, &st, rr_part, 0.0, rr_new, unused))) break;
+            if (!(alive = grid_sum1(a, &st, rr_part, rr_new))) break;
             __syncthreads();                 // every thread has read st.rr and coef
             if (threadIdx.x == 0) {
                 coef[0] = alpha;

@@ -81,10 +81,12 @@ struct CgBlockState {
 };
 
 // Grid barrier with a bounded wait.  Returns true (uniformly in the block) if
-// all blocks arrived and nobody aborted.
+// all blocks arrived and nobody aborted.  SYNC_FIRST = false for a caller whose
+// block is already synchronised and whose only work since is thread 0's.
+template <bool SYNC_FIRST = true>
 __device__ __forceinline__ bool grid_barrier(CgCtrl *ctrl, CgBlockState *st, long long timeout_ns,
                                              long long stall_barrier) {
-    __syncthreads();
+    if (SYNC_FIRST) __syncthreads();
     if (threadIdx.x == 0) {
         const long long index = (long long)(st->target / gridDim.x);  // barriers passed so far
         const unsigned long long target = st->target + gridDim.x;
@@ -93,18 +95,23 @@ __device__ __forceinline__ bool grid_barrier(CgCtrl *ctrl, CgBlockState *st, lon
         if (!(blockIdx.x == 0 && index == stall_barrier)) red_release_add(&ctrl->bar, 1ull);
         const long long t0 = global_ns();
         unsigned polls = 0;
+        // one load in flight per poll; the abort flag and the clock every 8th
+        // poll.  The acquire load that sees the count orders what the block
+        // reads after the __syncthreads below (partials by ld.global.cg, the
+        // gathers after the acquire has invalidated L1), so no fence follows.
+        // A block that gave up has already arrived here; the others see its
+        // abort flag at their next barrier and leave too (bounded either way).
         while (ld_acquire(&ctrl->bar) < target) {
-            if (*(volatile int *)&ctrl->abort) { ok = 0; break; }
-            if (((++polls) & 7u) == 0 &&
-                (global_ns() - t0 > timeout_ns || polls > kMaxPolls)) {
-                atomicExch(&ctrl->abort, 1);
-                ok = 0;
-                break;
+            if (((++polls) & 7u) == 0) {
+                if (*(volatile int *)&ctrl->abort) { ok = 0; break; }
+                if (global_ns() - t0 > timeout_ns || polls > kMaxPolls) {
+                    atomicExch(&ctrl->abort, 1);
+                    ok = 0;
+                    break;
+                }
             }
             __nanosleep(32);
         }
-        if (ok && *(volatile int *)&ctrl->abort) ok = 0;
-        __threadfence();
         st->ok = ok;
     }
     __syncthreads();
@@ -117,15 +124,15 @@ __device__ __forceinline__ bool grid_barrier(CgCtrl *ctrl, CgBlockState *st, lon
 // result through shared memory.  One reading warp per block keeps the number
 // of requests to the hot partial lines at G per block instead of 8 G.
 // `a` is any argument block with part, ctrl, timeout_ns and stall_barrier.
-template <class Args>
+template <class Args, bool TWO = true>
 __device__ __forceinline__ bool grid_sum2(const Args &a, CgBlockState *st, double v0,
                                           double v1, double &o0, double &o1) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     v0 = warp_sum(v0);
-    v1 = warp_sum(v1);
+    if (TWO) v1 = warp_sum(v1);
     if (lane == 0) {
         st->red[warp][0] = v0;
-        st->red[warp][1] = v1;
+        st->red[warp][1] = TWO ? v1 : 0.0;
     }
     __syncthreads();
     double2 *part = reinterpret_cast<double2 *>(a.part + (size_t)(st->round & 1) * 2 * kCgMaxBlocks);
@@ -138,9 +145,10 @@ __device__ __forceinline__ bool grid_sum2(const Args &a, CgBlockState *st, doubl
         }
         __stcg(part + blockIdx.x, make_double2(t0, t1));
     }
-    // the barrier's __syncthreads also orders every thread's read of st->sum
-    // from the previous reduction before warp 0 overwrites it below
-    if (!grid_barrier(a.ctrl, st, a.timeout_ns, a.stall_barrier)) return false;
+    // the __syncthreads above orders every thread's read of st->sum from the
+    // previous reduction before warp 0 overwrites it below, and since then only
+    // thread 0 has worked, so the barrier needs no block barrier of its own
+    if (!grid_barrier<false>(a.ctrl, st, a.timeout_ns, a.stall_barrier)) return false;
     if (warp == 0) {
         // lane-strided partials, four loads in flight per lane (a loop of one
         // dependent load per trip costs an L2 round trip per 32 blocks); the
@@ -156,12 +164,12 @@ __device__ __forceinline__ bool grid_sum2(const Args &a, CgBlockState *st, doubl
             for (int u = 0; u < 4; ++u) {
                 if (i + 32 * u < G) {
                     t0 += v[u].x;
-                    t1 += v[u].y;
+                    if (TWO) t1 += v[u].y;
                 }
             }
         }
         t0 = warp_sum(t0);
-        t1 = warp_sum(t1);
+        if (TWO) t1 = warp_sum(t1);
         if (lane == 0) {
             st->sum[0] = t0;
             st->sum[1] = t1;
@@ -172,6 +180,13 @@ __device__ __forceinline__ bool grid_sum2(const Args &a, CgBlockState *st, doubl
     o0 = st->sum[0];
     o1 = st->sum[1];
     return true;
+}
+
+// One value: grid_sum2 without the second sum's shuffles.
+template <class Args>
+__device__ __forceinline__ bool grid_sum1(const Args &a, CgBlockState *st, double v0, double &o0) {
+    double unused;
+    return grid_sum2<Args, false>(a, st, v0, 0.0, o0, unused);
 }
 
 // 16-byte packs of the vector phases: the streaming passes (x, r update and

@@ -154,13 +154,13 @@ k_cg_reliable(const MixArgs a) {
                     pw_part = fmaf(a.p[row], y, pw_part);
                 }
             }
-            double pw, unused;
-            if (!(alive = grid_sum2(a, &st, (double)pw_part, 0.0, pw, unused))) break;
+            double pw;
+            if (!(alive = grid_sum1(a, &st, (double)pw_part, pw))) break;
             if (!(pw > 0.0) || !(pw < INFINITY)) { status = FE_ERR_BREAKDOWN; break; }
             // B: xs += alpha p, r -= alpha w, r.r
             const float rr_part = update_xr<float>(a.xs, a.r, a.p, a.w, m, (float)(st.rr / pw));
             double rr_new;
-            if (!(alive = grid_sum2(a, &st, (double)rr_part, 0.0, rr_new, unused))) break;
+            if (!(alive = grid_sum1(a, &st, (double)rr_part, rr_new))) break;
             __syncthreads();
             if (threadIdx.x == 0) st.k += 1;
             __syncthreads();
@@ -171,7 +171,7 @@ k_cg_reliable(const MixArgs a) {
                 fold_correction(a.x, a.xs, m);
                 if (!(alive = grid_barrier(a.ctrl, &st, a.timeout_ns, a.stall_barrier))) break;
                 fp64_residual<FH>(a, m, ns, false, s0, s1);
-                if (!(alive = grid_sum2(a, &st, s0, 0.0, rr_true, unused))) break;
+                if (!(alive = grid_sum1(a, &st, s0, rr_true))) break;
                 __syncthreads();
                 if (threadIdx.x == 0) {
                     s_updates += 1;

@@ -30,7 +30,6 @@ template <int FMT>
 __global__ void __launch_bounds__(kCgThreads, 1) k_cg_resident(const CgArgs<double> a) {
     constexpr int W = ResidentShape<FMT>::W, T = ResidentShape<FMT>::T;
     __shared__ CgBlockState st;
-    __shared__ double coef[2];           // alpha of the last step, beta
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int m = (int)a.A.n_rows;
     const int slice = blockIdx.x * kCgWarps + warp;          // at most one per warp
@@ -42,7 +41,6 @@ __global__ void __launch_bounds__(kCgThreads, 1) k_cg_resident(const CgArgs<doub
         st.round = 0;
         st.k = 0;
         st.ok = 1;
-        coef[0] = coef[1] = 0.0;
     }
     // the slice's entries: column (BCRS3: first of three) and values per slot
     int w = 0;
@@ -91,6 +89,10 @@ __global__ void __launch_bounds__(kCgThreads, 1) k_cg_resident(const CgArgs<doub
     int status = FE_ERR_MAXIT;
     bool alive = true;
     double xr = 0.0, rr_ = 0.0, pr = 0.0, wr = 0.0;    // own row: x, r, p_{k-1}, w
+    // the scalars of the recurrence, the same in every thread (each computes
+    // them from the same reduced sums), so no block barrier publishes them
+    double rr_cur = 0.0, bb = 0.0, alpha_old = 0.0, beta = 0.0;
+    int k = 0;
     {
         const PtrGather<false, double> gx{a.x};
         const double ax = has ? row_product(gx) : 0.0;
@@ -105,26 +107,18 @@ __global__ void __launch_bounds__(kCgThreads, 1) k_cg_resident(const CgArgs<doub
             s0 = rr_ * rr_;
             s1 = bi * bi;
         }
-        double rr0, bb0;
-        alive = grid_sum2(a, &st, s0, s1, rr0, bb0);
-        if (threadIdx.x == 0) {
-            st.rr = rr0;
-            st.bb = bb0;
-        }
-        __syncthreads();
+        alive = grid_sum2(a, &st, s0, s1, rr_cur, bb);
     }
-    if (alive && st.bb == 0.0) {           // b = 0: the solution is 0
+    if (alive && bb == 0.0) {              // b = 0: the solution is 0
         xr = 0.0;
-        if (threadIdx.x == 0) st.rr = 0.0;
+        rr_cur = 0.0;
         status = FE_OK;
     } else {
         while (alive) {
-            if (st.rr <= a.tol2 * st.bb) { status = FE_OK; break; }
-            if (st.k >= a.maxit) { status = FE_ERR_MAXIT; break; }
-            const int k = st.k;
+            if (rr_cur <= a.tol2 * bb) { status = FE_OK; break; }
+            if (k >= a.maxit) { status = FE_ERR_MAXIT; break; }
             double *pnew = (k & 1) ? a.p2 : a.p;
             const double *pold = (k & 1) ? a.p : a.p2;
-            const double beta = coef[1], alpha_old = coef[0];
             // A: p_k at the gathered columns, w = A p_k; own row in registers
             const AxpyGather<double> gat{a.r, pold, beta};
             double pw_part = 0.0;
@@ -139,11 +133,11 @@ __global__ void __launch_bounds__(kCgThreads, 1) k_cg_resident(const CgArgs<doub
                     pw_part = pk * y;
                 }
             }
-            double pw, unused;
-            if (!(alive = grid_sum2(a, &st, pw_part, 0.0, pw, unused))) break;
+            double pw;
+            if (!(alive = grid_sum1(a, &st, pw_part, pw))) break;
             if (!(pw > 0.0) || !(pw < INFINITY)) { status = FE_ERR_BREAKDOWN; break; }
             // B: r -= alpha w in registers, stored for the next gathers; r.r
-            const double alpha = st.rr / pw;
+            const double alpha = rr_cur / pw;
             double rr_part = 0.0;
             if (live) {
                 rr_ = fma(-alpha, wr, rr_);
@@ -151,27 +145,23 @@ __global__ void __launch_bounds__(kCgThreads, 1) k_cg_resident(const CgArgs<doub
                 rr_part = rr_ * rr_;
             }
             double rr_new;
-            if (!(alive = grid_sum2(a, &st, rr_part, 0.0, rr_new, unused))) break;
-            __syncthreads();                 // every thread has read st.rr and coef
-            if (threadIdx.x == 0) {
-                coef[0] = alpha;
-                coef[1] = rr_new / st.rr;
-                st.rr = rr_new;
-                st.k += 1;
-            }
-            __syncthreads();
-            if (rr_new <= a.tol2 * st.bb) { status = FE_OK; break; }
-            if (st.k >= a.maxit) { status = FE_ERR_MAXIT; break; }
+            if (!(alive = grid_sum1(a, &st, rr_part, rr_new))) break;
+            alpha_old = alpha;
+            beta = rr_new / rr_cur;
+            rr_cur = rr_new;
+            k += 1;
+            if (rr_new <= a.tol2 * bb) { status = FE_OK; break; }
+            if (k >= a.maxit) { status = FE_ERR_MAXIT; break; }
         }
     }
     // the last step's x update (x += alpha_{k-1} p_{k-1}), then x to memory
-    if (alive && st.k > 0 && (status == FE_OK || status == FE_ERR_MAXIT)) xr = fma(coef[0], pr, xr);
+    if (alive && k > 0 && (status == FE_OK || status == FE_ERR_MAXIT)) xr = fma(alpha_old, pr, xr);
     if (live) a.x[row] = xr;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         a.ctrl->status = alive ? status : FE_ERR_TIMEOUT;
-        a.ctrl->iterations = st.k;
-        a.ctrl->rr = st.rr;
-        a.ctrl->bb = st.bb;
+        a.ctrl->iterations = k;
+        a.ctrl->rr = rr_cur;
+        a.ctrl->bb = bb;
     }
 }
 
@@ -180,6 +170,8 @@ static fe_status launch_resident(const CgArgs<double> &args, cudaStream_t s, boo
     auto kern = k_cg_resident<FMT>;
     int per_sm = 0;
     FE_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kCgThreads, 0));
+    // 8 slices per block: fewer blocks in each grid reduction (spreading N = 30's
+    // 931 slices 7 per block over 133 SMs, less FP64 work per SM, was slower)
     const int64_t blocks = (args.A.n_slices + kCgWarps - 1) / kCgWarps;
     if (per_sm < 1 || blocks > (int64_t)sm_count() * per_sm || blocks > kCgMaxBlocks) {
         *taken = false;                  // the grid would not be co-resident

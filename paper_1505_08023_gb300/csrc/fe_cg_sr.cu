@@ -102,8 +102,8 @@ __global__ void __launch_bounds__(kCgThreads, k_cg_min_blocks<FMT>()) k_cg_sr(co
                 bb_part = fma(bi, bi, bb_part);
             }
         }
-        double bb, unused;
-        alive = grid_sum2(a, &st, bb_part, 0.0, bb, unused);
+        double bb;
+        alive = grid_sum1(a, &st, bb_part, bb);
         if (threadIdx.x == 0) st.bb = bb;
         __syncthreads();
     }
