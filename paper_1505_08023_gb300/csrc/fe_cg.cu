@@ -90,15 +90,14 @@ __global__ void __launch_bounds__(kCgThreads, k_cg_min_blocks<FMT>()) k_cg(const
                     pw_part = fma(a.p[row], y, pw_part);
                 }
             }
-            double pw;
-            if (!(alive = grid_sum1(a, &st, (double)pw_part, pw))) break;
+            double pw, alpha_d;              // alpha = rr / (p.w), formed once per block
+            if (!(alive = grid_sum1_div<1>(a, &st, (double)pw_part, st.rr, pw, alpha_d))) break;
             if (!(pw > 0.0) || !(pw < INFINITY)) { status = FE_ERR_BREAKDOWN; break; }
             // B: r -= alpha w, r.r (x += alpha p is applied in C, where p is read anyway)
-            const XT alpha = (XT)(st.rr / pw);
+            const XT alpha = (XT)alpha_d;
             const XT rr_part = update_r<XT>(a.r, a.w, m, alpha);
-            double rr_new;
-            if (!(alive = grid_sum1(a, &st, (double)rr_part, rr_new))) break;
-            const double beta = rr_new / st.rr;
+            double rr_new, beta;             // beta = r.r / rr, formed once per block
+            if (!(alive = grid_sum1_div<2>(a, &st, (double)rr_part, st.rr, rr_new, beta))) break;
             __syncthreads();                 // every thread has read st.rr
             if (threadIdx.x == 0) {
                 st.rr = rr_new;
@@ -227,11 +226,10 @@ __global__ void __launch_bounds__(kCgThreads, k_cg_min_blocks<FMT>()) k_cg2(cons
                     pw_part = fma(pk, y, pw_part);
                 }
             }
-            double pw;
-            if (!(alive = grid_sum1(a, &st, pw_part, pw))) break;
+            double pw, alpha;                // alpha = rr / (p.w), formed once per block
+            if (!(alive = grid_sum1_div<1>(a, &st, pw_part, st.rr, pw, alpha))) break;
             if (!(pw > 0.0) || !(pw < INFINITY)) { status = FE_ERR_BREAKDOWN; break; }
             // B: r -= alpha w, r.r
-            const double alpha = st.rr / pw;
             const double rr_part = update_r<double>(a.r, a.w, m, alpha);
             double rr_new;
             if (!(alive = grid_sum1(a, &st, rr_part, rr_new))) break;

@@ -124,9 +124,9 @@ __device__ __forceinline__ bool grid_barrier(CgCtrl *ctrl, CgBlockState *st, lon
 // result through shared memory.  One reading warp per block keeps the number
 // of requests to the hot partial lines at G per block instead of 8 G.
 // `a` is any argument block with part, ctrl, timeout_ns and stall_barrier.
-template <class Args, bool TWO = true>
+template <class Args, bool TWO = true, int DIV = 0>
 __device__ __forceinline__ bool grid_sum2(const Args &a, CgBlockState *st, double v0,
-                                          double v1, double &o0, double &o1) {
+                                          double v1, double &o0, double &o1, double x = 0.0) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     v0 = warp_sum(v0);
     if (TWO) v1 = warp_sum(v1);
@@ -172,7 +172,7 @@ __device__ __forceinline__ bool grid_sum2(const Args &a, CgBlockState *st, doubl
         if (TWO) t1 = warp_sum(t1);
         if (lane == 0) {
             st->sum[0] = t0;
-            st->sum[1] = t1;
+            st->sum[1] = DIV == 1 ? x / t0 : (DIV == 2 ? t0 / x : t1);
             st->round += 1;            // every thread read st->round before the barrier
         }
     }
@@ -187,6 +187,16 @@ template <class Args>
 __device__ __forceinline__ bool grid_sum1(const Args &a, CgBlockState *st, double v0, double &o0) {
     double unused;
     return grid_sum2<Args, false>(a, st, v0, 0.0, o0, unused);
+}
+
+// One value and a quotient with it: x / sum (DIV = 1) or sum / x (DIV = 2),
+// formed once per block by the warp that finishes the sum and published with
+// it, so the other warps spend no FP64 division (each warp-wide FP64
+// instruction costs the SM 16 cycles of its 2-per-clock FP64 pipe).
+template <int DIV, class Args>
+__device__ __forceinline__ bool grid_sum1_div(const Args &a, CgBlockState *st, double v0, double x, double &sum,
+                                              double &quot) {
+    return grid_sum2<Args, false, DIV>(a, st, v0, 0.0, sum, quot, x);
 }
 
 // 16-byte packs of the vector phases: the streaming passes (x, r update and

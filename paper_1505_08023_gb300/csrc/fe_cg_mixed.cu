@@ -154,11 +154,11 @@ k_cg_reliable(const MixArgs a) {
                     pw_part = fmaf(a.p[row], y, pw_part);
                 }
             }
-            double pw;
-            if (!(alive = grid_sum1(a, &st, (double)pw_part, pw))) break;
+            double pw, alpha;                // alpha = rr / (p.w), formed once per block
+            if (!(alive = grid_sum1_div<1>(a, &st, (double)pw_part, st.rr, pw, alpha))) break;
             if (!(pw > 0.0) || !(pw < INFINITY)) { status = FE_ERR_BREAKDOWN; break; }
             // B: xs += alpha p, r -= alpha w, r.r
-            const float rr_part = update_xr<float>(a.xs, a.r, a.p, a.w, m, (float)(st.rr / pw));
+            const float rr_part = update_xr<float>(a.xs, a.r, a.p, a.w, m, (float)alpha);
             double rr_new;
             if (!(alive = grid_sum1(a, &st, (double)rr_part, rr_new))) break;
             __syncthreads();

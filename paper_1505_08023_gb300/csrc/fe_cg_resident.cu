@@ -133,21 +133,19 @@ __global__ void __launch_bounds__(kCgThreads, 1) k_cg_resident(const CgArgs<doub
                     pw_part = pk * y;
                 }
             }
-            double pw;
-            if (!(alive = grid_sum1(a, &st, pw_part, pw))) break;
+            double pw, alpha;                // alpha = rr / (p.w), formed once per block
+            if (!(alive = grid_sum1_div<1>(a, &st, pw_part, rr_cur, pw, alpha))) break;
             if (!(pw > 0.0) || !(pw < INFINITY)) { status = FE_ERR_BREAKDOWN; break; }
             // B: r -= alpha w in registers, stored for the next gathers; r.r
-            const double alpha = rr_cur / pw;
             double rr_part = 0.0;
             if (live) {
                 rr_ = fma(-alpha, wr, rr_);
                 a.r[row] = rr_;
                 rr_part = rr_ * rr_;
             }
-            double rr_new;
-            if (!(alive = grid_sum1(a, &st, rr_part, rr_new))) break;
+            double rr_new;                   // beta = r.r / rr, formed once per block
+            if (!(alive = grid_sum1_div<2>(a, &st, rr_part, rr_cur, rr_new, beta))) break;
             alpha_old = alpha;
-            beta = rr_new / rr_cur;
             rr_cur = rr_new;
             k += 1;
             if (rr_new <= a.tol2 * bb) { status = FE_OK; break; }

@@ -31,6 +31,7 @@ struct CgSrArgs : CgArgs<double> {
 // Block-uniform scalars of the recurrences (identical in every block).
 struct SrState {
     double gamma, gamma_prev, delta, alpha_prev;
+    double alpha, beta, curv;   // the step's scalars, formed once per block by thread 0
 };
 
 // U: p = r + beta p, s = w + beta s, x += alpha p, r -= alpha s.  One 16-byte
@@ -132,26 +133,32 @@ __global__ void __launch_bounds__(kCgThreads, k_cg_min_blocks<FMT>()) k_cg_sr(co
             double gamma, delta;
             if (!(alive = grid_sum2(a, &st, g_part, d_part, gamma, delta))) break;
             // every thread read sr at the top of the previous step; grid_sum2 synchronised the block
+            // thread 0 forms the step's scalars (three FP64 divisions once per
+            // block instead of in every warp) and the barrier below publishes them
             if (threadIdx.x == 0) {
                 if (!first) st.k += 1;
                 sr.gamma_prev = first ? 0.0 : sr.gamma;
                 sr.gamma = gamma;
                 sr.delta = delta;
+                double beta = 0.0, curv = delta;
+                if (!first) {
+                    beta = gamma / sr.gamma_prev;
+                    curv = delta - beta * gamma / sr.alpha_prev;
+                    if (!(curv > 0.0) || !(curv < INFINITY)) {  // lost its sign: restart the direction
+                        beta = 0.0;
+                        curv = delta;
+                    }
+                }
+                sr.beta = beta;
+                sr.curv = curv;
+                sr.alpha = gamma / curv;
             }
             __syncthreads();
             if (sr.gamma <= a.tol2 * st.bb) { status = FE_OK; break; }
             if (st.k >= a.maxit) { status = FE_ERR_MAXIT; break; }
-            double beta = 0.0, curv = sr.delta;
-            if (!first) {
-                beta = sr.gamma / sr.gamma_prev;
-                curv = sr.delta - beta * sr.gamma / sr.alpha_prev;
-                if (!(curv > 0.0) || !(curv < INFINITY)) {  // lost its sign: restart the direction
-                    beta = 0.0;
-                    curv = sr.delta;
-                }
-            }
+            const double beta = sr.beta, curv = sr.curv;
             if (!(curv > 0.0) || !(curv < INFINITY)) { status = FE_ERR_BREAKDOWN; break; }
-            const double alpha = sr.gamma / curv;
+            const double alpha = sr.alpha;
             // U
             update_sr(a.x, a.r, a.p, a.s, a.w, m, alpha, beta);
             if (!(alive = grid_barrier(a.ctrl, &st, a.timeout_ns, a.stall_barrier))) break;

@@ -325,11 +325,10 @@ __global__ void __launch_bounds__(kCgThreads, 2) k_cg_stencil(const StencilCgArg
             const double *pold = k > 0 ? ((k & 1) ? a.p0 : a.p1) : nullptr;
             const StencilIO io{a.r, pold, pcur, a.x, a.w, coef[1], coef[0]};
             const double pw_part = stencil_pass<ISO, true>(a.g, io, buf);
-            double pw;
-            if (!(alive = grid_sum1(a, &st, pw_part, pw))) break;
+            double pw, alpha;                // alpha = rr / (p.w), formed once per block
+            if (!(alive = grid_sum1_div<1>(a, &st, pw_part, st.rr, pw, alpha))) break;
             if (!(pw > 0.0) || !(pw < INFINITY)) { status = FE_ERR_BREAKDOWN; break; }
             // B: r -= alpha w, r.r
-            const double alpha = st.rr / pw;
             const double rr_part = update_r<double>(a.r, a.w, a.g.m, alpha);
             double rr_new;
             if (!(alive = grid_sum1(a, &st, rr_part, rr_new))) break;
