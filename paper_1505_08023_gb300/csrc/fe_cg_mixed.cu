@@ -92,14 +92,181 @@ __device__ __forceinline__ void fold_correction(double *x, float *xs, int m) {
     }
 }
 
-// The inner (low-precision) BCRS3 SpMV issues the loads of all nine slots of a
-// 27-point row in one trip (its step is latency-bound: one trip of independent
-// loads instead of three dependent ones), at three blocks per SM (80
-// registers, no spills): 15 % less time per BF16 inner step, 10 % per FP32
-// one, than three slots per trip at four blocks per SM.
-constexpr int kMixInnerUnroll = 9;
+// The inner (low-precision) BCRS3 SpMV is latency-bound, not bandwidth-bound:
+// with its loads issued by the threads it puts all nine slots of a 27-point
+// row in flight in one trip and the next slice's indices with them
+// (bcrs3_slices_prefetch), at three blocks per SM (80 registers, no spills).
 
-template <int FL, class VL, int FH>
+// ------------------------------------------- inner BCRS3 SpMV staged by bulk copies
+// Each warp owns kRing stages of shared memory.  Lane 0 streams the column
+// indices and values of the warp's slices into them with cp.async.bulk (the
+// bytes counted on the stage's mbarrier), kRing slices ahead of the slice the
+// warp computes, so the matrix stream stays in flight while the warp gathers
+// the operands and multiplies; the warp itself only waits on the gathers.
+// A stage: a 16-byte header (the slice's first slot and its width, written by
+// lane 0 before its arrive), the 9 x 32 column indices, the 27 x 32 values.
+// Slices wider than nine slots are not staged (the header says so) and go
+// through slice_spmv_bcrs3 from global memory.
+template <class VT> struct MixStage {
+    // stages per warp (three BF16 stages measured 3 % slower than two)
+    static constexpr int kRing = 2;
+    static_assert((kRing & (kRing - 1)) == 0, "the fill count maps to stage and parity by kRing | 2^32");
+    static constexpr int kIdx = 16;
+    static constexpr int kVal = kIdx + 9 * kSlice * 4;
+    static constexpr int kBytes = kVal + 27 * kSlice * (int)sizeof(VT);
+    static constexpr size_t kBlockBytes = (size_t)kCgWarps * kRing * kBytes + (size_t)kCgWarps * kRing * 8;
+};
+
+__device__ __forceinline__ uint32_t mix_smem(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ long long mix_now() {
+    long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait for phase `parity` of a stage's mbarrier; false after 1 s.
+__device__ __forceinline__ bool mix_stage_wait(uint32_t bar, uint32_t parity) {
+    uint32_t done = 0;
+    long long t0 = 0;
+    for (unsigned it = 0; it < (1u << 26); ++it) {
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(done)
+                     : "r"(bar), "r"(parity)
+                     : "memory");
+        if (done) return true;
+        if (it == 0) t0 = mix_now();
+        else if ((it & 255u) == 0 && mix_now() - t0 > 1000000000LL) return false;
+    }
+    return false;
+}
+
+// Lane 0: fill stage `st` of the warp's ring with slice (b, w) (slot offset,
+// width); every fill completes the stage's mbarrier phase exactly once.
+template <class VT>
+__device__ __forceinline__ void mix_stage_fill(const fe_matrix &A, unsigned char *ring, uint32_t bars, int st,
+                                               int64_t b, int w, uint64_t policy) {
+    unsigned char *dst = ring + (size_t)st * MixStage<VT>::kBytes;
+    const uint32_t bar = bars + 8u * (uint32_t)st;
+    *reinterpret_cast<int64_t *>(dst) = b;
+    *reinterpret_cast<int *>(dst + 8) = w;
+    if (w > 0 && w <= 9) {
+        const uint32_t ib = (uint32_t)w * kSlice * 4u, vb = (uint32_t)w * 3u * kSlice * (uint32_t)sizeof(VT);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(ib + vb)
+                     : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;"
+            ::"r"(mix_smem(dst + MixStage<VT>::kIdx)), "l"(A.d_cols + b), "r"(ib), "r"(bar), "l"(policy)
+            : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;"
+            ::"r"(mix_smem(dst + MixStage<VT>::kVal)), "l"(reinterpret_cast<const VT *>(A.d_vals) + 3 * b), "r"(vb),
+              "r"(bar), "l"(policy)
+            : "memory");
+    } else {
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+    }
+}
+
+// The warp's grid-stride walk over slices s0, s0 + stride, ... of the inner
+// matrix through its ring.  `fills` counts the ring's fills over the kernel's
+// life: fill f goes to stage f mod kRing and completes that stage's mbarrier
+// phase of parity (f / kRing) mod 2 (kRing a power of two, so both stay right
+// when the 32-bit count wraps).  The FMA order is slice_spmv_bcrs3's, so
+// results are bitwise the same.  Returns false if a stage never completed
+// (after a bounded drain of the fills still in flight).
+template <class VT, class F>
+__device__ __forceinline__ bool bcrs3_slices_staged(const fe_matrix &A, int64_t s0, int64_t stride, int lane,
+                                                    const float *x, unsigned char *ring, uint32_t bars,
+                                                    uint32_t &fills, F &&out) {
+    constexpr int kRing = MixStage<VT>::kRing;
+    const int64_t ns = A.n_slices;
+    const int64_t n = s0 < ns ? (ns - 1 - s0) / stride + 1 : 0;
+    if (n == 0) return true;
+    const int64_t *sp = A.d_slice_ptr;
+    uint64_t policy = 0;
+    int64_t nb = 0;   // lane 0: bounds of the next slice to fill
+    int nw = 0;
+    if (lane == 0) {
+        asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(policy));
+        const int64_t q0 = n < kRing ? n : kRing;
+        for (int64_t q = 0; q < q0; ++q) {
+            const int64_t s = s0 + q * stride;
+            const int64_t b = sp[s];
+            mix_stage_fill<VT>(A, ring, bars, (int)((fills + q) % kRing), b, (int)((sp[s + 1] - b) >> 5),
+                               policy);
+        }
+        if (n > kRing) {
+            const int64_t s = s0 + kRing * stride;
+            nb = sp[s];
+            nw = (int)((sp[s + 1] - nb) >> 5);
+        }
+    }
+    bool ok = true;
+    int64_t q = 0;
+    for (; q < n; ++q) {
+        const uint32_t f = fills + (uint32_t)q;
+        const int st = (int)(f % kRing);
+        if (!__all_sync(0xffffffffu, mix_stage_wait(bars + 8u * (uint32_t)st, (f / kRing) & 1u))) {
+            ok = false;
+            break;
+        }
+        const unsigned char *stage = ring + (size_t)st * MixStage<VT>::kBytes;
+        const int w = *reinterpret_cast<const int *>(stage + 8);
+        const int64_t s = s0 + q * stride;
+        float acc = 0.0f;
+        if (w == 9) {
+            const int32_t *si = reinterpret_cast<const int32_t *>(stage + MixStage<VT>::kIdx) + lane;
+            const VT *sv = reinterpret_cast<const VT *>(stage + MixStage<VT>::kVal) + lane;
+            float xx[9][3];
+#pragma unroll
+            for (int u = 0; u < 9; ++u) {
+                const int64_t j = si[32 * u];
+#pragma unroll
+                for (int t = 0; t < 3; ++t) xx[u][t] = x[j + t];
+            }
+#pragma unroll
+            for (int u = 0; u < 9; ++u)
+#pragma unroll
+                for (int t = 0; t < 3; ++t) acc = fmaf(to_acc<float>(sv[96 * u + 32 * t]), xx[u][t], acc);
+        } else if (w > 0 && w < 9) {
+            const int32_t *si = reinterpret_cast<const int32_t *>(stage + MixStage<VT>::kIdx) + lane;
+            const VT *sv = reinterpret_cast<const VT *>(stage + MixStage<VT>::kVal) + lane;
+            for (int k = 0; k < w; ++k) {
+                const int64_t j = si[32 * k];
+#pragma unroll
+                for (int t = 0; t < 3; ++t) acc = fmaf(to_acc<float>(sv[96 * k + 32 * t]), x[j + t], acc);
+            }
+        } else if (w > 9) {
+            acc = slice_spmv_bcrs3<VT, float, float, 9>(A, s, lane, PtrGather<false, float>{x});
+        }
+        __syncwarp();
+        // every lane has consumed the stage: lane 0 refills it kRing slices ahead
+        if (lane == 0 && q + kRing < n) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mix_stage_fill<VT>(A, ring, bars, st, nb, nw, policy);
+            if (q + kRing + 1 < n) {
+                const int64_t sn = s0 + (q + kRing + 1) * stride;
+                nb = sp[sn];
+                nw = (int)((sp[sn + 1] - nb) >> 5);
+            }
+        }
+        out(s, acc);
+    }
+    if (!ok) {
+        // drain: wait (bounded) for every fill issued but not consumed
+        const int64_t issued = n < q + kRing ? n : q + kRing;
+        for (int64_t d = q; d < issued; ++d) {
+            const uint32_t f = fills + (uint32_t)d;
+            mix_stage_wait(bars + 8u * (f % kRing), (f / kRing) & 1u);
+        }
+    }
+    fills += (uint32_t)n;
+    return ok;
+}
+
+template <int FL, class VL, int FH, bool STAGED = false>
 __global__ void __launch_bounds__(kCgThreads,
                                   (FL == FE_FMT_CSR || FH == FE_FMT_CSR || FL == FE_FMT_BCRS3) ? 3 : kCgBlocksPerSm)
 k_cg_reliable(const MixArgs a) {
@@ -112,6 +279,19 @@ k_cg_reliable(const MixArgs a) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int m = (int)a.A_lo.n_rows, ns = (int)a.A_lo.n_slices;
     const int tw = gridDim.x * kCgWarps;
+    unsigned char *ring = nullptr;   // STAGED: this warp's stages and mbarriers
+    uint32_t bars = 0, fills = 0;
+    if constexpr (STAGED) {
+        extern __shared__ __align__(128) unsigned char mix_dyn[];
+        constexpr int kRing = MixStage<VL>::kRing;
+        ring = mix_dyn + (size_t)warp * kRing * MixStage<VL>::kBytes;
+        bars = mix_smem(mix_dyn + (size_t)kCgWarps * kRing * MixStage<VL>::kBytes) + 8u * kRing * (uint32_t)warp;
+        if (lane == 0) {
+            for (int i = 0; i < kRing; ++i)
+                asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bars + 8u * i), "r"(1));
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+    }
     if (threadIdx.x == 0) {
         st.target = 0;
         st.round = 0;
@@ -145,14 +325,24 @@ k_cg_reliable(const MixArgs a) {
         while (alive) {
             // A: w = A_lo p (FP32), p.w
             float pw_part = 0.0f;
-            for (int s = blockIdx.x * kCgWarps + warp; s < ns; s += tw) {
-                const float y = slice_spmv<FL, VL, float, float, false, FL == FE_FMT_BCRS3 ? kMixInnerUnroll : 0>(
-                    a.A_lo, s, lane, a.p);
-                const int row = s * kSlice + lane;
+            auto out = [&](int64_t s, float y) {
+                const int row = (int)s * kSlice + lane;
                 if (row < m) {
                     a.w[row] = y;
                     pw_part = fmaf(a.p[row], y, pw_part);
                 }
+            };
+            if constexpr (STAGED) {
+                const bool ok = bcrs3_slices_staged<VL>(a.A_lo, blockIdx.x * kCgWarps + warp, tw, lane, a.p,
+                                                        ring, bars, fills, out);
+                if (!ok && lane == 0) atomicExch(&a.ctrl->abort, 1);  // the other blocks leave at their barrier
+                if (__syncthreads_or(!ok)) { alive = false; break; }
+            } else if constexpr (FL == FE_FMT_BCRS3) {
+                bcrs3_slices_prefetch<VL, float, float>(a.A_lo, blockIdx.x * kCgWarps + warp, tw, lane,
+                                                        PtrGather<false, float>{a.p}, out);
+            } else {
+                for (int s = blockIdx.x * kCgWarps + warp; s < ns; s += tw)
+                    out(s, slice_spmv<FL, VL, float, float, false>(a.A_lo, s, lane, a.p));
             }
             double pw, alpha;                // alpha = rr / (p.w), formed once per block
             if (!(alive = grid_sum1_div<1>(a, &st, (double)pw_part, st.rr, pw, alpha))) break;
@@ -208,11 +398,13 @@ k_cg_reliable(const MixArgs a) {
     }
 }
 
-template <int FL, class VL, int FH>
+template <int FL, class VL, int FH, bool STAGED = false>
 static fe_status launch_reliable(const MixArgs &args, cudaStream_t s) {
-    auto kern = k_cg_reliable<FL, VL, FH>;
+    auto kern = k_cg_reliable<FL, VL, FH, STAGED>;
+    const size_t dyn = STAGED ? MixStage<VL>::kBlockBytes : 0;
+    if (STAGED) FE_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
     int per_sm = 0;
-    FE_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kCgThreads, 0));
+    FE_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kCgThreads, dyn));
     if (per_sm < 1) return FE_ERR_CUDA;
     int64_t blocks = (int64_t)sm_count() * per_sm;
     const int64_t need = (args.A_lo.n_slices + kCgWarps - 1) / kCgWarps;
@@ -221,18 +413,28 @@ static fe_status launch_reliable(const MixArgs &args, cudaStream_t s) {
     if (blocks < 1) blocks = 1;
     void *params[] = {(void *)&args};
     FE_TRY_CUDA(cudaLaunchCooperativeKernel((const void *)kern, dim3((unsigned)blocks), dim3(kCgThreads),
-                                            params, 0, s));
+                                            params, dyn, s));
     return FE_OK;
 }
 
-template <int FL, class VL>
+template <int FL, class VL, bool STAGED = false>
 static fe_status dispatch_reliable_hi(const MixArgs &a, cudaStream_t s) {
     switch (a.A_hi.format) {
-        case FE_FMT_CSR: return launch_reliable<FL, VL, FE_FMT_CSR>(a, s);
-        case FE_FMT_SELL: return launch_reliable<FL, VL, FE_FMT_SELL>(a, s);
-        case FE_FMT_BCRS3: return launch_reliable<FL, VL, FE_FMT_BCRS3>(a, s);
+        case FE_FMT_CSR: return launch_reliable<FL, VL, FE_FMT_CSR, STAGED>(a, s);
+        case FE_FMT_SELL: return launch_reliable<FL, VL, FE_FMT_SELL, STAGED>(a, s);
+        case FE_FMT_BCRS3: return launch_reliable<FL, VL, FE_FMT_BCRS3, STAGED>(a, s);
         default: return FE_ERR_ARG;
     }
+}
+
+// BCRS3 inner matrices stream through the bulk-copy ring when both arrays
+// start on a 16-byte boundary (every slice's block of indices and values then
+// does too: a slice starts at a multiple of 32 slots).
+template <class VL>
+static fe_status dispatch_reliable_bcrs3(const MixArgs &a, cudaStream_t s) {
+    if (aligned(a.A_lo.d_cols, 16) && aligned(a.A_lo.d_vals, 16))
+        return dispatch_reliable_hi<FE_FMT_BCRS3, VL, true>(a, s);
+    return dispatch_reliable_hi<FE_FMT_BCRS3, VL>(a, s);
 }
 
 static fe_status dispatch_reliable(const MixArgs &a, cudaStream_t s) {
@@ -241,8 +443,8 @@ static fe_status dispatch_reliable(const MixArgs &a, cudaStream_t s) {
         case FE_FMT_CSR * 3 + FE_VAL_BF16: return dispatch_reliable_hi<FE_FMT_CSR, __nv_bfloat16>(a, s);
         case FE_FMT_SELL * 3 + FE_VAL_F32: return dispatch_reliable_hi<FE_FMT_SELL, float>(a, s);
         case FE_FMT_SELL * 3 + FE_VAL_BF16: return dispatch_reliable_hi<FE_FMT_SELL, __nv_bfloat16>(a, s);
-        case FE_FMT_BCRS3 * 3 + FE_VAL_F32: return dispatch_reliable_hi<FE_FMT_BCRS3, float>(a, s);
-        case FE_FMT_BCRS3 * 3 + FE_VAL_BF16: return dispatch_reliable_hi<FE_FMT_BCRS3, __nv_bfloat16>(a, s);
+        case FE_FMT_BCRS3 * 3 + FE_VAL_F32: return dispatch_reliable_bcrs3<float>(a, s);
+        case FE_FMT_BCRS3 * 3 + FE_VAL_BF16: return dispatch_reliable_bcrs3<__nv_bfloat16>(a, s);
         default: return FE_ERR_ARG;  // FP64 inner values: use fe_cg_solve
     }
 }

@@ -163,6 +163,67 @@ __device__ __forceinline__ AT slice_spmv_bcrs3(const fe_matrix &A, int64_t s, in
     return acc;
 }
 
+// A warp's grid-stride walk over BCRS3 slices s0, s0 + stride, ... in which
+// the column indices of the next slice are loaded during the current slice's
+// trip.  A slice of nine slots (every 27-point row) then puts its value loads
+// and its operand gathers in flight together: one round of memory latency
+// per slice, not two (indices, then the gathers that depend on them).  Slices
+// of another width take slice_spmv_bcrs3.  The FMA order is
+// slice_spmv_bcrs3's, so results are bitwise the same.  out(s, y) receives
+// lane's row sum of slice s.
+template <class VT, class XT, class AT, class G, class F>
+__device__ __forceinline__ void bcrs3_slices_prefetch(const fe_matrix &A, int64_t s0, int64_t stride,
+                                                      int lane, const G &x, F &&out) {
+    constexpr int W = 9;
+    const int64_t ns = A.n_slices;
+    if (s0 >= ns) return;
+    const int64_t *sp = A.d_slice_ptr;
+    const int32_t *cols = A.d_cols + lane;
+    const VT *vals = reinterpret_cast<const VT *>(A.d_vals) + lane;
+    int64_t b = sp[s0];
+    int w = (int)((sp[s0 + 1] - b) >> 5);
+    int32_t jj[W];
+#pragma unroll
+    for (int u = 0; u < W; ++u) jj[u] = (w == W) ? ld_stream(cols + b + 32 * u) : 0;
+    for (int64_t s = s0; s < ns; s += stride) {
+        // the next slice's bounds (their latency runs under this trip's loads)
+        const int64_t sn = s + stride;
+        int64_t bn = 0;
+        int wn = 0;
+        if (sn < ns) {
+            bn = sp[sn];
+            wn = (int)((sp[sn + 1] - bn) >> 5);
+        }
+        AT acc = AT(0);
+        if (w == W) {
+            const VT *v = vals + 3 * b;
+            VT vv[W][3];
+            XT xx[W][3];
+#pragma unroll
+            for (int u = 0; u < W; ++u)
+#pragma unroll
+                for (int t = 0; t < 3; ++t) vv[u][t] = ld_stream(v + 96 * u + 32 * t);
+#pragma unroll
+            for (int u = 0; u < W; ++u)
+#pragma unroll
+                for (int t = 0; t < 3; ++t) xx[u][t] = x((int64_t)jj[u] + t);
+#pragma unroll
+            for (int u = 0; u < W; ++u) jj[u] = (wn == W) ? ld_stream(cols + bn + 32 * u) : 0;
+#pragma unroll
+            for (int u = 0; u < W; ++u)
+#pragma unroll
+                for (int t = 0; t < 3; ++t) acc = fma(to_acc<AT>(vv[u][t]), (AT)xx[u][t], acc);
+        } else {
+#pragma unroll
+            for (int u = 0; u < W; ++u) jj[u] = (wn == W) ? ld_stream(cols + bn + 32 * u) : 0;
+            acc = slice_spmv_bcrs3<VT, XT, AT, W>(A, s, lane, x);
+        }
+        out(s, acc);
+        b = bn;
+        w = wn;
+    }
+}
+
 // CSR: four lanes per row, eight rows per pass, four passes per slice.  Lane
 // j of group g runs entries lo + j, lo + j + 4, ... of row 8p + g (one FMA
 // per entry slot; the four lanes read 32 contiguous bytes of values per step;

@@ -263,3 +263,103 @@ def test_full_size_n400_mixed(fe):
         assert em <= (trm * bnorm + rs) / lam_min, v
         assert em <= 20.0 * e64 + 1e-12 * float(torch.linalg.norm(xs)), (v, em / e64)
         del Alo, xm
+
+
+# ---------------------------------------------------------------------------
+# The BCRS3 inner matrix streams through a shared-memory ring filled by bulk
+# copies when its column and value arrays start on 16-byte boundaries, and
+# through thread loads otherwise.  Both walk the slots in the same order, so
+# the solves must agree bit for bit.
+
+def _shifted(t: torch.Tensor) -> torch.Tensor:
+    """A copy of t whose storage starts one element past a 16-byte boundary."""
+    buf = torch.empty(t.numel() + 16, dtype=t.dtype, device=t.device)
+    assert buf.data_ptr() % 16 == 0
+    out = buf[1:1 + t.numel()]
+    out.copy_(t)
+    assert out.data_ptr() % 16 != 0
+    return out
+
+
+def _with_arrays(fe, dm, cols, vals):
+    d = dm.desc
+    return fe.fe_matrix(d.format, d.value_type, d.n_rows, d.n_cols, d.n_slices, d.n_stored, None,
+                        d.d_slice_ptr, cols.data_ptr(), vals.data_ptr())
+
+
+def _bcrs3_from_csr(fe, row_ptr, cols, vals, m, value):
+    """BCRS3 copy (values rounded to `value`) of an FP64 CSR matrix on the device."""
+    ns = (m + 31) // 32
+    csr = fe.fe_matrix(fe.FE_FMT_CSR, fe.FE_VAL_F64, m, m, ns, int(cols.numel()), row_ptr.data_ptr(), None,
+                       cols.data_ptr(), vals.data_ptr())
+    sp = torch.empty(ns + 1, dtype=torch.int64, device="cuda")
+    n_stored = fe.fe_sliced_plan(fe.FE_FMT_BCRS3, m, m, row_ptr, cols, sp)
+    c = torch.empty(n_stored, dtype=torch.int32, device="cuda")
+    v = torch.empty(3 * n_stored, dtype=fe.TORCH_VALUE[fe.VALUE_TYPES[value]], device="cuda")
+    d = fe.fe_matrix(fe.FE_FMT_BCRS3, fe.VALUE_TYPES[value], m, m, ns, n_stored, None, sp.data_ptr(),
+                     c.data_ptr(), v.data_ptr())
+    fe.fe_convert(csr, d)
+    return csr, fe.DeviceMatrix(d, {"slice_ptr": sp, "cols": c, "vals": v})
+
+
+def _solve_pair(fe, A64_desc, lo, b, m):
+    """Reliable mixed solves with the aligned and the shifted inner arrays."""
+    shifted = (_shifted(lo.tensors["cols"]), _shifted(lo.tensors["vals"]))
+    lo_u = _with_arrays(fe, lo, *shifted)
+    work = fe.mixed_workspace(lo)
+    out = []
+    for desc in (lo.desc, lo_u):
+        x = torch.zeros(m, dtype=torch.float64, device="cuda")
+        res = fe.fe_cg_solve_mixed(A64_desc, desc, b, x, 1e-10, MODES["reliable"], 60, 0.1, 5000, work,
+                                   check=False)
+        out.append((x, res))
+    return out
+
+
+@pytest.mark.parametrize("value", ["f32", "bf16"])
+def test_reliable_staged_and_thread_load_paths_agree(fe, value):
+    """70^3 elements (357,911 rows, 11,185 slices): every warp walks several
+    slices per pass, so the ring is refilled and its parity turns over."""
+    s = fe.System(70).build()
+    (xa, ra), (xb, rb) = _solve_pair(fe, s.matrix("bcrs3", "f64").desc, s.matrix("bcrs3", value), s.b, s.m)
+    assert ra.status == fe.FE_OK and rb.status == fe.FE_OK
+    assert ra.inner_iterations == rb.inner_iterations and ra.outer_iterations == rb.outer_iterations
+    assert torch.equal(xa, xb)
+
+
+@pytest.mark.parametrize("value", ["f32", "bf16"])
+@pytest.mark.parametrize("reach", [4, 12])
+def test_reliable_staged_wide_and_narrow_slices(fe, value, reach):
+    """A symmetric, strictly diagonally dominant matrix with couplings i +- 7k,
+    k = 1..reach: every entry its own BCRS3 slot, so interior slices are nine
+    slots wide (reach 4) or 25 (reach 12, the slices the ring passes to the
+    global-memory walk), and the rows near both ends are narrower.  300,007
+    rows.  The aligned and shifted solves agree bit for bit and reach the
+    FP64 residual test, checked on the host."""
+    m = 300_007
+    i = np.arange(m, dtype=np.int64)
+    offs = np.concatenate([-7 * np.arange(reach, 0, -1), [0], 7 * np.arange(1, reach + 1)])
+    rows, cols, vals = [], [], []
+    for o in offs:
+        j = i + o
+        keep = (j >= 0) & (j < m)
+        rows.append(i[keep])
+        cols.append(j[keep])
+        vals.append(np.full(keep.sum(), 4.0 * reach + 1.0 if o == 0 else -1.0))
+    rows, cols, vals = (np.concatenate(a) for a in (rows, cols, vals))
+    order = np.lexsort((cols, rows))
+    rows, cols, vals = rows[order], cols[order], vals[order]
+    row_ptr = np.concatenate([[0], np.cumsum(np.bincount(rows, minlength=m))])
+    b = np.cos(0.001 * i)
+    d_rp = torch.from_numpy(row_ptr.astype(np.int32)).cuda()
+    d_c = torch.from_numpy(cols.astype(np.int32)).cuda()
+    d_v = torch.from_numpy(vals).cuda()
+    d_b = torch.from_numpy(b).cuda()
+    csr, lo = _bcrs3_from_csr(fe, d_rp, d_c, d_v, m, value)
+    (xa, ra), (xb, rb) = _solve_pair(fe, csr, lo, d_b, m)
+    assert ra.status == fe.FE_OK and rb.status == fe.FE_OK
+    assert ra.inner_iterations == rb.inner_iterations
+    assert torch.equal(xa, xb)
+    x = xa.cpu().numpy()
+    ax = np.bincount(rows, weights=vals * x[cols], minlength=m)
+    assert np.linalg.norm(b - ax) <= 1.5e-10 * np.linalg.norm(b)
