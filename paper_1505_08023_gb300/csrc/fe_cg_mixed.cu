@@ -92,10 +92,11 @@ __device__ __forceinline__ void fold_correction(double *x, float *xs, int m) {
     }
 }
 
-// The inner (low-precision) BCRS3 SpMV is latency-bound, not bandwidth-bound:
-// with its loads issued by the threads it puts all nine slots of a 27-point
-// row in flight in one trip and the next slice's indices with them
-// (bcrs3_slices_prefetch), at three blocks per SM (80 registers, no spills).
+// The inner (low-precision) BCRS3 SpMV was latency-bound with its matrix
+// loads issued by the threads.  It streams the matrix through a shared-memory
+// ring filled by bulk copies (below); arrays that are not 16-byte aligned take
+// the thread-load walk, which puts all nine slots of a 27-point row in flight
+// in one trip and the next slice's indices with them (bcrs3_slices_prefetch).
 
 // ------------------------------------------- inner BCRS3 SpMV staged by bulk copies
 // Each warp owns kRing stages of shared memory.  Lane 0 streams the column
@@ -174,8 +175,10 @@ __device__ __forceinline__ void mix_stage_fill(const fe_matrix &A, unsigned char
 // life: fill f goes to stage f mod kRing and completes that stage's mbarrier
 // phase of parity (f / kRing) mod 2 (kRing a power of two, so both stay right
 // when the 32-bit count wraps).  The FMA order is slice_spmv_bcrs3's, so
-// results are bitwise the same.  Returns false if a stage never completed
-// (after a bounded drain of the fills still in flight).
+// results are bitwise the same.  out(s, y, x_row) receives lane's row sum of
+// slice s and, for BF16 values, x at lane's row (0 otherwise).  Returns false
+// if a stage never completed (after a bounded drain of the fills still in
+// flight).
 template <class VT, class F>
 __device__ __forceinline__ bool bcrs3_slices_staged(const fe_matrix &A, int64_t s0, int64_t stride, int lane,
                                                     const float *x, unsigned char *ring, uint32_t bars,
@@ -215,6 +218,14 @@ __device__ __forceinline__ bool bcrs3_slices_staged(const fe_matrix &A, int64_t 
         const unsigned char *stage = ring + (size_t)st * MixStage<VT>::kBytes;
         const int w = *reinterpret_cast<const int *>(stage + 8);
         const int64_t s = s0 + q * stride;
+        // BF16 values: x at lane's row goes out with the gathers (measured 1-3 %
+        // less time per step); FP32 values: out() loads it (the early load
+        // measured 5 % slower there)
+        float xr = 0.0f;
+        if constexpr (sizeof(VT) == 2) {
+            const int64_t row = s * kSlice + lane;
+            xr = row < A.n_rows ? x[row] : 0.0f;
+        }
         float acc = 0.0f;
         if (w == 9) {
             const int32_t *si = reinterpret_cast<const int32_t *>(stage + MixStage<VT>::kIdx) + lane;
@@ -252,7 +263,7 @@ __device__ __forceinline__ bool bcrs3_slices_staged(const fe_matrix &A, int64_t 
                 nw = (int)((sp[sn + 1] - nb) >> 5);
             }
         }
-        out(s, acc);
+        out(s, acc, xr);
     }
     if (!ok) {
         // drain: wait (bounded) for every fill issued but not consumed
@@ -266,9 +277,20 @@ __device__ __forceinline__ bool bcrs3_slices_staged(const fe_matrix &A, int64_t 
     return ok;
 }
 
+// Blocks per SM: four for BF16 BCRS3 values (64 registers; the staged form's
+// 46.5 KB ring per block fits four times; measured 6 % less time per inner
+// step than three), three for FP32 BCRS3 values and the CSR forms (80
+// registers; the FP32 ring's 74 KB per block allows no more).  The staged and
+// thread-load forms of one value type take the same block count, hence the
+// same grid, the same reduction order and bitwise the same solve.
+template <int FL, class VL, int FH>
+constexpr int mix_min_blocks() {
+    if (FL == FE_FMT_BCRS3 && sizeof(VL) == 2) return 4;
+    return (FL == FE_FMT_CSR || FH == FE_FMT_CSR || FL == FE_FMT_BCRS3) ? 3 : kCgBlocksPerSm;
+}
+
 template <int FL, class VL, int FH, bool STAGED = false>
-__global__ void __launch_bounds__(kCgThreads,
-                                  (FL == FE_FMT_CSR || FH == FE_FMT_CSR || FL == FE_FMT_BCRS3) ? 3 : kCgBlocksPerSm)
+__global__ void __launch_bounds__(kCgThreads, mix_min_blocks<FL, VL, FH>())
 k_cg_reliable(const MixArgs a) {
     __shared__ CgBlockState st;
     __shared__ double s_rr_max;
@@ -325,11 +347,11 @@ k_cg_reliable(const MixArgs a) {
         while (alive) {
             // A: w = A_lo p (FP32), p.w
             float pw_part = 0.0f;
-            auto out = [&](int64_t s, float y) {
+            auto out = [&](int64_t s, float y, float p_row) {
                 const int row = (int)s * kSlice + lane;
                 if (row < m) {
                     a.w[row] = y;
-                    pw_part = fmaf(a.p[row], y, pw_part);
+                    pw_part = fmaf(sizeof(VL) == 2 ? p_row : a.p[row], y, pw_part);
                 }
             };
             if constexpr (STAGED) {
@@ -341,8 +363,11 @@ k_cg_reliable(const MixArgs a) {
                 bcrs3_slices_prefetch<VL, float, float>(a.A_lo, blockIdx.x * kCgWarps + warp, tw, lane,
                                                         PtrGather<false, float>{a.p}, out);
             } else {
-                for (int s = blockIdx.x * kCgWarps + warp; s < ns; s += tw)
-                    out(s, slice_spmv<FL, VL, float, float, false>(a.A_lo, s, lane, a.p));
+                for (int s = blockIdx.x * kCgWarps + warp; s < ns; s += tw) {
+                    const int row = s * kSlice + lane;
+                    const float pr = row < m ? a.p[row] : 0.0f;
+                    out(s, slice_spmv<FL, VL, float, float, false>(a.A_lo, s, lane, a.p), pr);
+                }
             }
             double pw, alpha;                // alpha = rr / (p.w), formed once per block
             if (!(alive = grid_sum1_div<1>(a, &st, (double)pw_part, st.rr, pw, alpha))) break;

@@ -169,8 +169,8 @@ __device__ __forceinline__ AT slice_spmv_bcrs3(const fe_matrix &A, int64_t s, in
 // and its operand gathers in flight together: one round of memory latency
 // per slice, not two (indices, then the gathers that depend on them).  Slices
 // of another width take slice_spmv_bcrs3.  The FMA order is
-// slice_spmv_bcrs3's, so results are bitwise the same.  out(s, y) receives
-// lane's row sum of slice s.
+// slice_spmv_bcrs3's, so results are bitwise the same.  out(s, y, x_row)
+// receives lane's row sum of slice s and the operand at lane's row.
 template <class VT, class XT, class AT, class G, class F>
 __device__ __forceinline__ void bcrs3_slices_prefetch(const fe_matrix &A, int64_t s0, int64_t stride,
                                                       int lane, const G &x, F &&out) {
@@ -194,6 +194,8 @@ __device__ __forceinline__ void bcrs3_slices_prefetch(const fe_matrix &A, int64_
             bn = sp[sn];
             wn = (int)((sp[sn + 1] - bn) >> 5);
         }
+        const int64_t row = s * kSlice + lane;
+        const XT xr = row < A.n_rows ? x(row) : XT(0);   // for out(), loaded with the gathers
         AT acc = AT(0);
         if (w == W) {
             const VT *v = vals + 3 * b;
@@ -218,7 +220,7 @@ __device__ __forceinline__ void bcrs3_slices_prefetch(const fe_matrix &A, int64_
             for (int u = 0; u < W; ++u) jj[u] = (wn == W) ? ld_stream(cols + bn + 32 * u) : 0;
             acc = slice_spmv_bcrs3<VT, XT, AT, W>(A, s, lane, x);
         }
-        out(s, acc);
+        out(s, acc, xr);
         b = bn;
         w = wn;
     }
