@@ -21,6 +21,26 @@ def test_bcrs3_step_model_counts_indices_values_and_vectors():
     assert fma == 3 * slots + 5 * m      # one FMA per stored value + p.w, r, r.r, x, p
 
 
+def test_mixed_model_counts_low_and_high_precision_passes():
+    m, ns, slots = 1000, 32, 400
+    ptrs = 8 * (ns + 1)
+    # inner FP32 step: 4 B index + 3 values per slot; vectors in FP32: w = Ap
+    # (p, w: 8 B), r and xs update (xs, r, p, w read, xs, r written: 24 B),
+    # p update (p, r read, p written: 12 B)
+    inner = {"f32": slots * (4 + 3 * 4) + ptrs + 44 * m, "bf16": slots * (4 + 3 * 2) + ptrs + 44 * m}
+    # refinement: the FP64 matrix (28 B per slot) + x += xs (24 B) + r = b - A x (20 B)
+    hi = slots * 28 + ptrs + 44 * m
+    for value in ("f32", "bf16"):
+        assert bench.mixed_bytes_model(m, ns, slots, value, 0, 0) == hi   # the initial FP64 residual
+        assert bench.mixed_bytes_model(m, ns, slots, value, 7, 2) == 7 * inner[value] + 3 * hi
+    # per row at the N = 256 shape (about nine slots per row): 134 B (BF16) and 188 B (FP32)
+    n = 256
+    m = (n + 1) ** 3
+    per_row = {v: (bench.mixed_bytes_model(m, (m + 31) // 32, 9 * m, v, 1, 0)
+                   - bench.mixed_bytes_model(m, (m + 31) // 32, 9 * m, v, 0, 0)) / m for v in ("f32", "bf16")}
+    assert abs(per_row["bf16"] - 134.25) < 0.01 and abs(per_row["f32"] - 188.25) < 0.01
+
+
 def test_matrix_free_operation_model_on_a_tiny_cube():
     # N = 2: 27 nodes, one interior node, 26 boundary nodes
     ops = bench.matrix_free_ops(2)
